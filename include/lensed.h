@@ -1,0 +1,240 @@
+/*
+ * lensed.h -- C ABI of the GB300 (sm_103a) ray-tracing likelihood library.
+ *
+ * The library computes, for parametric lens and source models, the expected
+ * image of a strong-lensing system and its Gaussian log-likelihood, as
+ * defined in Tessore, Bellagamba & Metcalf, "Lensed: a code for the forward
+ * reconstruction of lenses and sources from strong lensing observations":
+ *
+ *   Sec. 2.1, Eq. 1   lens equation            y = x - alpha(x)
+ *   Sec. 2.1, Eq. 2   image-plane brightness   I(x) = I_L(x) + I_S(y(x))
+ *   Sec. 2.1, Eq. 3   pixel luminosity         L_i = integral of I over pixel i
+ *   Sec. 3.1, Eq. 14  quadrature               L_i ~ sum_k w_k I(x_k)
+ *   Sec. 3.1, Eq. 15  PSF                      L*_ij = sum_kl F_{-k,-l} L_{i+k,j+l}
+ *                     (PSF normalised to unit sum, border padded by
+ *                      repeating the nearest pixel)
+ *   Sec. 3.2, Eq. 17  loglike = -1/2 sum_i w_i (d_i - L*_i)^2, w_i = 1/s_i^2,
+ *                     a masked pixel has w_i = 0
+ *   Sec. 3.3, Eq. 21  s_i^2 = (d_i + b_i) / g_i when no variance is given,
+ *                     times an optional multiplicative extra weight
+ *   Sec. 4.1, Eqs. 22-23  elliptical Sersic profile, geometric-mean radius
+ *
+ * Conventions (the paper leaves them open):
+ *   - images are row-major [ny][nx]; row i runs along +y, column j along +x;
+ *     pixel (i, j) is the square of side h centred on
+ *     ((j - (nx-1)/2) h, (i - (ny-1)/2) h) arcsec;
+ *   - a PSF array is row-major [psf_ny][psf_nx] = [2p+1][2q+1], centred on
+ *     its middle element F_{0,0}; both sizes odd;
+ *   - position angles in degrees, counter-clockwise from +x to the major axis;
+ *   - component parameters, in this order:
+ *       LENSED_SIE        x, y, b, q, pa, s      (Einstein radius b in the
+ *                          geometric-mean convention, core radius s)
+ *       LENSED_SHEAR      x, y, gamma, phi       (about the centre x, y)
+ *       LENSED_POINTMASS  x, y, theta_E
+ *       LENSED_SERSIC     x, y, r_e, mag, n, q, pa
+ *       LENSED_DEVAUC     x, y, r_e, mag, q, pa  (Sersic with n = 4)
+ *       LENSED_GAUSS      x, y, sigma, mag, q, pa
+ *     Total flux of a light profile is 10^(-0.4 (mag - zeropoint)).
+ *
+ * Memory and streams: every input array of lensed_create_model is copied
+ * into library-owned device memory, so the caller may free it on return.
+ * Parameter and output arrays of the evaluation calls are caller-owned
+ * device pointers (unless the call name ends in _host); the library never
+ * frees caller memory.  Work is enqueued on the caller's CUDA stream
+ * (NULL = legacy default stream) and the calls return without synchronising,
+ * except lensed_create_model, lensed_autotune and the _host calls.  A model
+ * must not be used from two host threads at once.  Scratch memory is owned
+ * by the model, grown on demand and released by lensed_destroy.
+ *
+ * Errors: every call returns a lensed_status; nothing aborts the process or
+ * traps the GPU.  lensed_last_error() returns a thread-local message for the
+ * last failing call of the calling thread.  A parameter point outside the
+ * model's domain (an axis ratio outside (0, 1], a non-positive radius or
+ * Sersic index, a negative Einstein radius or core) is not an error: its
+ * log-likelihood is -inf.
+ */
+#ifndef LENSED_GB300_H
+#define LENSED_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LENSED_OK = 0,
+    LENSED_E_ARG = -1,         /* invalid argument or descriptor */
+    LENSED_E_NOMEM = -2,       /* device or host allocation failed */
+    LENSED_E_CUDA = -3,        /* a CUDA runtime call failed */
+    LENSED_E_NONFINITE = -4,   /* non-finite data, variance, weight or PSF */
+    LENSED_E_TIMEOUT = -5,     /* a bounded device-side wait expired */
+    LENSED_E_UNSUPPORTED = -6  /* valid request this build cannot serve */
+} lensed_status;
+
+enum {
+    LENSED_SIE = 1,
+    LENSED_SHEAR = 2,
+    LENSED_POINTMASS = 3,
+    LENSED_SERSIC = 4,
+    LENSED_DEVAUC = 5,
+    LENSED_GAUSS = 6
+};
+
+enum {
+    LENSED_PLANE_LENS = 0,        /* mass: contributes to alpha */
+    LENSED_PLANE_FOREGROUND = 1,  /* light evaluated at the image position x */
+    LENSED_PLANE_SOURCE = 2       /* light evaluated at the traced position y */
+};
+
+/* Integration rules (Sec. 3.1, Eq. 14; rule list of Sec. 4.5), each the
+ * Cartesian square of a 1-D rule on the pixel:
+ *   LENSED_RULE_POINT  one ray at the pixel centre (rule_order ignored)
+ *   LENSED_RULE_SUB    rule_order x rule_order uniform sub-sampling
+ *   LENSED_RULE_GL     rule_order x rule_order Gauss-Legendre            */
+enum { LENSED_RULE_POINT = 0, LENSED_RULE_SUB = 1, LENSED_RULE_GL = 2 };
+
+/* Arithmetic of the evaluation:
+ *   LENSED_PREC_FP32   rays, brightness and PSF in FP32; chi^2 summed in FP64
+ *   LENSED_PREC_MIXED  as FP32, but the SIE deflection is evaluated in FP64
+ *                      for axis ratios close to 1 (e = sqrt(1-q^2) < 0.05)
+ *                      and for rays close to the core (psi < 4 s)
+ *   LENSED_PREC_FP64   everything in FP64 (validation mode)              */
+enum { LENSED_PREC_FP32 = 0, LENSED_PREC_MIXED = 1, LENSED_PREC_FP64 = 2 };
+
+enum { LENSED_RENDER_UNCONVOLVED = 0, LENSED_RENDER_CONVOLVED = 1 };
+
+#define LENSED_MAX_COMPONENT_PARAMS 8
+#define LENSED_MAX_COMPONENTS 16
+#define LENSED_MAX_RULE_ORDER 16
+#define LENSED_MAX_PSF_HALF 15     /* PSF sizes up to 31 x 31 */
+#define LENSED_MAX_IMAGE_SIDE 4096
+
+/* One model component.  Parameter k is free when free_index[k] >= 0 (then
+ * it is read from the parameter vector at that index; several components
+ * may share an index, which ties parameters) and fixed to value[k]
+ * otherwise. */
+typedef struct {
+    int type;   /* LENSED_SIE ... LENSED_GAUSS */
+    int plane;  /* LENSED_PLANE_* (mass types must be LENSED_PLANE_LENS) */
+    int free_index[LENSED_MAX_COMPONENT_PARAMS];
+    double value[LENSED_MAX_COMPONENT_PARAMS];
+} lensed_component;
+
+/* One imaging system (Sec. 3, steps (i)-(ii) of the high-level algorithm):
+ * data, variance or gain/offset, mask, PSF, rule and model.  All pointers
+ * are HOST pointers, read during lensed_create_model only. */
+typedef struct {
+    int nx, ny;                    /* image size, 1 .. LENSED_MAX_IMAGE_SIDE */
+    double pixel_scale;            /* h, arcsec per pixel, > 0 */
+    const double *data;            /* [ny*nx] observed d_i; required */
+    const double *variance;        /* [ny*nx] s_i^2, or NULL: use gain/offset */
+    double gain, offset;           /* Eq. 21: s_i^2 = (d_i + offset) / gain */
+    const double *extra_weight;    /* [ny*nx] factor on w_i, or NULL */
+    const unsigned char *mask;     /* [ny*nx], nonzero = excluded, or NULL */
+    const double *psf;             /* [psf_ny*psf_nx] or NULL (no PSF) */
+    int psf_nx, psf_ny;            /* odd, <= 2*LENSED_MAX_PSF_HALF+1 */
+    int rule, rule_order;          /* LENSED_RULE_*, order 1..LENSED_MAX_RULE_ORDER */
+    double zeropoint;              /* magnitude zero point */
+    int n_components;              /* 1 .. LENSED_MAX_COMPONENTS */
+    const lensed_component *components;
+    int n_params;                  /* length of this system's parameter vector */
+} lensed_system_desc;
+
+typedef struct lensed_model lensed_model; /* opaque, library-owned */
+
+typedef struct {
+    int n_systems;
+    int n_params_max;        /* row stride of the parameter arrays */
+    int precision;
+    long long total_pixels;  /* sum over systems of nx*ny */
+    long long rays_per_eval_all;     /* sum over systems of nx*ny*rays/pixel */
+    long long rays_per_eval_traced;  /* rays lensed_loglike_* traces per point
+                                        and system (pixels the masked chi^2
+                                        needs, through the PSF footprint) */
+    long long psf_taps_per_eval;     /* multiply-adds of the PSF per point */
+    double flops_per_ray;    /* algorithmic FP32 operations per traced ray,
+                                counted from the formulas (add, mul, div,
+                                sqrt, transcendental = 1, fused pair = 2),
+                                averaged over the traced rays */
+    double transcendentals_per_ray;  /* of which atan/atanh/exp2/log2/sqrt */
+} lensed_model_info;
+
+/* Build a model of n_systems imaging systems (Sec. 3, steps (i)-(ii)).
+ * Validates every descriptor, computes the weights w_i (Sec. 3.2-3.3),
+ * normalises the PSF (Sec. 3.1), builds the quadrature table (Eq. 14) and
+ * copies everything to the current CUDA device.  Synchronous.
+ * Returns LENSED_E_ARG for a malformed descriptor (sizes, even PSF, unknown
+ * type or plane, free index >= n_params), LENSED_E_NONFINITE for non-finite
+ * data/variance/weights/PSF or a non-positive variance on an unmasked pixel,
+ * LENSED_E_NOMEM/LENSED_E_CUDA on device failures.  *out is set only on
+ * success. */
+int lensed_create_model(const lensed_system_desc *systems, int n_systems, int precision,
+                        lensed_model **out);
+
+/* Free everything the model owns.  NULL-safe.  Synchronises the device
+ * work the model has in flight before freeing. */
+void lensed_destroy(lensed_model *m);
+
+/* Describe the model (sizes and work per evaluation). */
+int lensed_model_info_get(const lensed_model *m, lensed_model_info *info);
+
+/* Expected image of one system at one parameter point (Eqs. 1-3, 14, and
+ * Eq. 15 when flags == LENSED_RENDER_CONVOLVED): writes L or L* for every
+ * pixel into out_image, a DEVICE array of ny*nx floats.  params is a
+ * DEVICE array of the system's n_params doubles.  If the point is outside
+ * the domain the image is filled with NaN.  Asynchronous on stream. */
+int lensed_render(lensed_model *m, int system, const double *params, int flags,
+                  float *out_image, void *stream);
+
+/* Log-likelihood (Eq. 17) of P parameter points for every system, batched:
+ * params is a DEVICE array [n_systems][P][n_params_max] of doubles (entries
+ * beyond a system's n_params are ignored), out_loglike a DEVICE array
+ * [n_systems][P] of doubles.  All points of all systems go through one
+ * CUDA-graph launch whose tile configuration comes from the autotuner (or
+ * a default).  Asynchronous on stream.  P must be >= 1. */
+int lensed_loglike_batch(lensed_model *m, const double *params, int P, double *out_loglike,
+                         void *stream);
+
+/* Same result as lensed_loglike_batch, computed the way the paper's code
+ * schedules it: one parameter point of one system at a time, each with its
+ * own kernel launches and no graph.  Kept as the baseline the batched path
+ * is measured against.  Results are bit-identical to lensed_loglike_batch. */
+int lensed_loglike_plain(lensed_model *m, const double *params, int P, double *out_loglike,
+                         void *stream);
+
+/* lensed_loglike_batch with HOST arrays: copies params to the device,
+ * evaluates, copies the results back and synchronises the stream before
+ * returning.  Pinned host memory gives the fastest copies. */
+int lensed_loglike_batch_host(lensed_model *m, const double *params_host, int P,
+                              double *out_host, void *stream);
+
+/* Time the candidate tile configurations on a batch of P points drawn
+ * inside the given DEVICE parameter array (same layout as
+ * lensed_loglike_batch) and keep the fastest for later batched calls.
+ * Results do not depend on the choice.  Synchronous. */
+int lensed_autotune(lensed_model *m, const double *params, int P, void *stream);
+
+/* Index of the configuration the autotuner picked (-1: default) and its
+ * description, for reports. */
+int lensed_tuned_config(const lensed_model *m, char *buf, int buflen);
+
+/* Launch plan of one lensed_loglike_batch call with P points: number of
+ * kernels it launches (*launches) and the number of points per scratch
+ * chunk (*chunk_points).  Nothing is launched. */
+int lensed_batch_plan(lensed_model *m, int P, int *launches, int *chunk_points);
+
+/* Run the batched schedule of lensed_loglike_batch once without the graph,
+ * with CUDA events around every launch on stream, and report the device
+ * milliseconds spent per stage in stage_ms[4]: prologue, trace (rays,
+ * Eqs. 1-3, 14), PSF + chi^2 (Eqs. 15, 17), finalize; and in
+ * *trace_launches the number of trace launches.  Same results as
+ * lensed_loglike_batch.  Synchronous. */
+int lensed_profile_batch(lensed_model *m, const double *params, int P, double *out_loglike,
+                         void *stream, double *stage_ms, int *trace_launches);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char *lensed_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LENSED_GB300_H */

@@ -1,0 +1,115 @@
+// Internal declarations shared by the translation units of the CUDA library.
+// Nothing here is part of the C ABI (include/lensed.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lensed.h"
+
+namespace lensed {
+
+// Packed per-component constants, FP32 and FP64 copies, kNC values each.
+constexpr int kNC = 16;
+// Tile of the PSF / chi^2 kernel: kTileW columns x kTileH rows of outputs,
+// kPsfThreads threads, each computing kOutPerThread consecutive columns.
+constexpr int kTileW = 64;
+constexpr int kTileH = 32;
+constexpr int kOutPerThread = 8;
+constexpr int kPsfThreads = (kTileW / kOutPerThread) * kTileH;  // 256
+
+// Light-profile kinds inside the packed constants.
+constexpr int kKindPower = 0;  // Sersic / de Vaucouleurs: 2^-(2^(p2 lg2 R^2 + lc))
+constexpr int kKindGauss = 1;  // Gaussian: 2^-(k R^2)
+
+// SIE evaluation in MIXED precision switches to FP64 below these.
+constexpr double kMixedRoundE = 0.05;   // e = sqrt(1 - q^2)
+constexpr double kMixedCoreFactor = 4.0;  // psi < 4 s
+
+// Series in e replaces atan/atanh below this (both precisions).
+constexpr double kSeriesE = 1e-3;
+
+struct SysDev {
+    int nx, ny, npix;
+    float h;
+    double hd;
+    float cx, cy;        // (nx-1)/2, (ny-1)/2
+    int nn;              // 1-D nodes of the rule
+    int node_off;        // into the node tables
+    int psf_p, psf_q;    // PSF half sizes (0, 0 without a PSF)
+    int psf_off;         // into the flipped, normalised PSF table
+    long long pix_off;   // into data / weights / per-point image scratch
+    int comp_off, ncomp; // into the component tables
+    int n_params;
+    long long need_off;  // into the needed-pixel list
+    int tile_off, n_tiles;  // into the active-tile list
+    int tiles_x, tiles_y;   // full tiling of the image
+    double zeropoint;
+};
+
+// Trace-kernel block table entry: system and the range [start, end) of its
+// pixel list (or of its pixel indices when the list is the identity).
+struct TraceBlock {
+    int sys;
+    int start, end;
+};
+
+// 1-D quadrature nodes (offsets t*h from the pixel centre) and weights.
+struct NodeTables {
+    const float *u, *w;
+    const double *ud, *wd;
+};
+
+// PSF-kernel block table entry: system and tile origin.
+struct PsfBlock {
+    int sys;
+    int tile;  // global index into the partial-sum columns
+    int i0, j0;
+};
+
+struct LaunchCfg {
+    int trace_threads;   // 128 or 256
+    int pix_per_thread;  // 1 or 2
+};
+
+// --- kernels launched from the runtime (defined in lensed_kernels.cu) ---
+
+// a1: per (system, point) packed constants and validity.
+// With single_row, params is one row (the render path).
+void launch_prologue(const SysDev *sys, int s0, int nS, const int *comp_type,
+                     const int *comp_free, const double *comp_value, const double *params,
+                     bool single_row, int P, int p0, int nP, int n_par_stride, int C_total,
+                     float *cf, double *cd, unsigned char *valid, cudaStream_t st);
+
+// a2-a5: pixel luminosities of the pixels in the block table, for points
+// p0 .. p0 + nP - 1, into Lbuf[(p - p0) * L_stride + pix_off + pix].
+void launch_trace(int precision, LaunchCfg cfg, const SysDev *sys, const int *comp_type,
+                  const int *comp_plane, const float *cf, const double *cd,
+                  const unsigned char *valid, int P, int C_total, const TraceBlock *blocks,
+                  int n_blocks, const int *need, NodeTables nodes, int p0, int nP, void *Lbuf,
+                  long long L_stride, cudaStream_t st);
+
+// One-time kernel attributes (dynamic shared memory limits); call before
+// any launch or capture.
+void init_kernel_attributes();
+
+// a6-a7: PSF convolution of the tiles in the block table, then either the
+// masked chi^2 partial sums (partial != nullptr) or the convolved image
+// (out != nullptr, one point).
+void launch_psf(int precision, int q, int p_max, const SysDev *sys, const float *psf_f,
+                const double *psf_d, const float *data, const float *weight,
+                const double *data_d, const double *weight_d,
+                const unsigned char *valid, int P, const PsfBlock *blocks, int n_blocks, int p0,
+                int nP, const void *Lbuf, long long L_stride, double *partial, int T_total,
+                float *out, cudaStream_t st);
+
+// a7: loglike = -1/2 sum of the partials of each (system, point).
+void launch_finalize(const SysDev *sys, const unsigned char *valid, int P,
+                     const double *partial, int T_total, double *out, int s0, int p0, int nS,
+                     int nP, cudaStream_t st);
+
+// Copy an unconvolved image out of the scratch buffer (render path).
+void launch_copy_image(int precision, const void *Lbuf, long long off, int npix,
+                       const unsigned char *valid, float *out, cudaStream_t st);
+
+}  // namespace lensed

@@ -1,0 +1,994 @@
+// Host runtime of the ray-tracing likelihood: the C ABI of include/lensed.h.
+//
+// lensed_create_model validates the systems, prepares the per-pixel data,
+// weights and the normalised PSF (Sec. 3.1-3.3), the quadrature tables
+// (Eq. 14) and the work lists, and copies them to the device.  The
+// evaluation calls schedule the kernels of lensed_kernels.cu:
+//
+//   batched:  prologue(all points) -> for each point chunk: trace, psf ->
+//             finalize, captured once per (P, pointers, tile configuration)
+//             into a CUDA graph and replayed with one graph launch;
+//   plain:    for each system and point: prologue, trace, psf, finalize,
+//             each a separate launch (the per-point scheduling of the
+//             paper's code), no graph.
+//
+// Both run the same kernels on the same per-pixel work, so their results
+// are bit-identical.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "lensed_internal.cuh"
+
+using namespace lensed;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CUDA_OK(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? LENSED_E_NOMEM : LENSED_E_CUDA,   \
+                        "%s: %s", #call, cudaGetErrorString(e_));                           \
+    } while (0)
+
+// Algorithmic operation count of one ray through a component, counted from
+// the formulas (add/sub/mul/div/sqrt/transcendental = 1, a multiply-add
+// pair = 2) -- not from the compiled code.  {flops, transcendentals}:
+//   SIE: translate 2, rotate 6, psi 6 (incl. sqrt), two quotients 4, e*z 2,
+//        atan + atanh 2, prefactor 2, rotate back 6, accumulate 2 -> 32, 3
+//   shear / point mass: translate 2, two linear forms 6 / r^2 3 + div 1 +
+//        scale 2, accumulate 2 -> 10, 0
+//   Sersic-type light: translate 2, rotate 6, R^2 5, log2 1, scale+shift 2,
+//        exp2 1, negate+exp2 2, amplitude 1, accumulate 1 -> 21, 3
+//   Gaussian light: translate 2, rotate 6, R^2 5, scale 1, negate+exp2 2,
+//        amplitude 1, accumulate 1 -> 18, 1
+//   per ray: position 2, lens equation 2, weight product + accumulate 2 -> 6
+void component_ops(int type, double &flops, double &transc)
+{
+    switch (type) {
+    case LENSED_SIE: flops += 32; transc += 3; break;
+    case LENSED_SHEAR: flops += 10; break;
+    case LENSED_POINTMASS: flops += 10; break;
+    case LENSED_GAUSS: flops += 18; transc += 1; break;
+    default: flops += 21; transc += 3; break;
+    }
+}
+
+int nparams_of(int type)
+{
+    switch (type) {
+    case LENSED_SIE: return 6;
+    case LENSED_SHEAR: return 4;
+    case LENSED_POINTMASS: return 3;
+    case LENSED_SERSIC: return 7;
+    case LENSED_DEVAUC: return 6;
+    case LENSED_GAUSS: return 6;
+    }
+    return -1;
+}
+
+// Gauss-Legendre nodes on [-1, 1] by Newton's method on P_n with the
+// three-term recurrence, started from the Tricomi estimate; long double.
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        long double z = cosl(pi * (i + 0.75L) / (n + 0.5L)), dp = 0;
+        for (int it = 0; it < 100; ++it) {
+            long double p0 = 1, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = z; p0 = 1; }
+            dp = n * (z * p1 - p0) / (z * z - 1);
+            long double dz = p1 / dp;
+            z -= dz;
+            if (fabsl(dz) < 1e-19L) break;
+        }
+        // recompute the derivative at the converged root
+        long double p0 = 1, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = (n == 1) ? 1.0L : n * (z * p1 - p0) / (z * z - 1);
+        const long double wt = 2 / ((1 - z * z) * dp * dp);
+        x[n - 1 - i] = (double)z;
+        x[i] = (double)-z;
+        w[i] = w[n - 1 - i] = (double)wt;
+    }
+    if (n % 2 == 1) x[n / 2] = 0.0;
+}
+
+// 1-D rule on the unit pixel: offsets t in (-1/2, 1/2), weights summing to 1.
+bool rule_nodes(int rule, int order, std::vector<double> &t, std::vector<double> &wt)
+{
+    if (rule == LENSED_RULE_POINT) {
+        t = {0.0};
+        wt = {1.0};
+        return true;
+    }
+    if (order < 1 || order > LENSED_MAX_RULE_ORDER) return false;
+    if (rule == LENSED_RULE_SUB) {
+        t.resize(order);
+        wt.assign(order, 1.0 / order);
+        for (int a = 0; a < order; ++a) t[a] = (a + 0.5) / order - 0.5;
+        return true;
+    }
+    if (rule == LENSED_RULE_GL) {
+        std::vector<double> x, w;
+        gauss_legendre(order, x, w);
+        t.resize(order);
+        wt.resize(order);
+        for (int a = 0; a < order; ++a) {
+            t[a] = 0.5 * x[a];
+            wt[a] = 0.5 * w[a];
+        }
+        return true;
+    }
+    return false;
+}
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    int alloc(size_t count)
+    {
+        release();
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return fail(LENSED_E_NOMEM, "cudaMalloc(%zu bytes): %s", count * sizeof(T),
+                        cudaGetErrorString(e));
+        }
+        n = count;
+        return LENSED_OK;
+    }
+    int upload(const std::vector<T> &v)
+    {
+        int rc = alloc(v.size());
+        if (rc) return rc;
+        if (!v.empty()) CUDA_OK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return LENSED_OK;
+    }
+};
+
+struct PsfGroup {
+    int q, p_max;
+    int off, count;  // into the PSF block table
+};
+
+struct GraphEntry {
+    int P;
+    const void *params;
+    void *out;
+    int cfg;
+    cudaGraphExec_t exec;
+    unsigned long long age;
+};
+
+struct Candidate {
+    LaunchCfg cfg;
+    const char *name;
+};
+
+const Candidate kCandidates[] = {
+    {{256, 1}, "trace 256 threads x 1 pixel"},
+    {{128, 1}, "trace 128 threads x 1 pixel"},
+    {{256, 2}, "trace 256 threads x 2 pixels"},
+    {{128, 2}, "trace 128 threads x 2 pixels"},
+};
+constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
+
+}  // namespace
+
+struct lensed_model {
+    int device = 0;
+    int precision = LENSED_PREC_MIXED;
+    int n_sys = 0;
+    int n_par_max = 0;
+    int C_total = 0;
+    long long total_pix = 0;
+    int T_total = 0;  // active (chi^2) tiles over all systems
+    size_t scratch_budget = (size_t)1 << 30;  // bytes of per-point image scratch
+
+    std::vector<SysDev> sys_h;
+    std::vector<int> need_count;      // per system
+    std::vector<int> n_nodes;         // per system
+    std::vector<int> psf_p, psf_q;    // per system
+    std::vector<int> tiles_all;       // per system: tiles_x * tiles_y
+    std::vector<double> ray_flops, ray_transc;  // per system, per ray
+
+    // device tables
+    DevBuf<SysDev> sys;
+    DevBuf<int> comp_type, comp_plane, comp_free;
+    DevBuf<double> comp_value;
+    DevBuf<float> data, weight;
+    DevBuf<double> data_d, weight_d;  // FP64 mode
+    DevBuf<float> psf_f;
+    DevBuf<double> psf_d;
+    DevBuf<float> node_u, node_w;
+    DevBuf<double> node_ud, node_wd;
+    DevBuf<int> need;
+
+    // chi^2 PSF blocks (grouped by q, systems contiguous) and render tables
+    std::vector<PsfBlock> psf_blocks_h;
+    DevBuf<PsfBlock> psf_blocks;
+    std::vector<PsfGroup> psf_groups;
+    std::vector<int> psf_sys_off, psf_sys_cnt;  // per system range in psf_blocks
+    std::vector<int> render_psf_off, render_psf_cnt;
+    std::vector<PsfBlock> render_psf_h;
+    DevBuf<PsfBlock> render_psf;
+
+    // trace block tables, rebuilt when the items per block change
+    int trace_items = 0;
+    std::vector<int> trace_sys_off, trace_sys_cnt;
+    DevBuf<TraceBlock> trace_blocks;
+    int n_trace_blocks = 0;
+    std::vector<int> render_trace_off, render_trace_cnt;
+    DevBuf<TraceBlock> render_trace;
+
+    // per-batch buffers
+    int cap_P = 0;
+    DevBuf<float> cf;
+    DevBuf<double> cd;
+    DevBuf<unsigned char> valid;
+    DevBuf<double> partial;
+    DevBuf<unsigned char> Lbuf;
+    int chunk_P = 0;
+    // render buffers (one point)
+    DevBuf<float> rcf;
+    DevBuf<double> rcd;
+    DevBuf<unsigned char> rvalid;
+    DevBuf<unsigned char> rL;
+    // host-API staging
+    DevBuf<double> stage_params, stage_out;
+
+    int cfg_index = -1;  // autotuned candidate, -1 = default
+    cudaStream_t cap_stream = nullptr;
+    std::vector<GraphEntry> graphs;
+    unsigned long long graph_clock = 0;
+
+    LaunchCfg cfg() const { return kCandidates[cfg_index < 0 ? 0 : cfg_index].cfg; }
+    size_t elem() const { return precision == LENSED_PREC_FP64 ? sizeof(double) : sizeof(float); }
+    NodeTables nodes() const { return {node_u.p, node_w.p, node_ud.p, node_wd.p}; }
+
+    void clear_graphs()
+    {
+        for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
+        graphs.clear();
+    }
+    ~lensed_model()
+    {
+        cudaDeviceSynchronize();
+        clear_graphs();
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
+};
+
+namespace {
+
+int build_trace_tables(lensed_model *m, int items)
+{
+    if (m->trace_items == items) return LENSED_OK;
+    std::vector<TraceBlock> tb, rb;
+    m->trace_sys_off.assign(m->n_sys, 0);
+    m->trace_sys_cnt.assign(m->n_sys, 0);
+    m->render_trace_off.assign(m->n_sys, 0);
+    m->render_trace_cnt.assign(m->n_sys, 0);
+    for (int s = 0; s < m->n_sys; ++s) {
+        m->trace_sys_off[s] = (int)tb.size();
+        for (int a = 0; a < m->need_count[s]; a += items)
+            tb.push_back({s, a, std::min(a + items, m->need_count[s])});
+        m->trace_sys_cnt[s] = (int)tb.size() - m->trace_sys_off[s];
+        m->render_trace_off[s] = (int)rb.size();
+        const int npix = m->sys_h[s].npix;
+        for (int a = 0; a < npix; a += items) rb.push_back({s, a, std::min(a + items, npix)});
+        m->render_trace_cnt[s] = (int)rb.size() - m->render_trace_off[s];
+    }
+    int rc = m->trace_blocks.upload(tb);
+    if (rc) return rc;
+    rc = m->render_trace.upload(rb);
+    if (rc) return rc;
+    m->n_trace_blocks = (int)tb.size();
+    m->trace_items = items;
+    m->clear_graphs();
+    return LENSED_OK;
+}
+
+int ensure_capacity(lensed_model *m, int P)
+{
+    if (P <= m->cap_P) return LENSED_OK;
+    cudaDeviceSynchronize();
+    m->clear_graphs();
+    int rc;
+    if ((rc = m->cf.alloc((size_t)P * m->C_total * kNC))) return rc;
+    if ((rc = m->cd.alloc((size_t)P * m->C_total * kNC))) return rc;
+    if ((rc = m->valid.alloc((size_t)P * m->n_sys))) return rc;
+    if ((rc = m->partial.alloc((size_t)P * std::max(m->T_total, 1)))) return rc;
+    const size_t per_point = (size_t)m->total_pix * m->elem();
+    size_t chunk = std::max<size_t>(1, m->scratch_budget / std::max<size_t>(per_point, 1));
+    chunk = std::min<size_t>(chunk, (size_t)P);
+    if ((rc = m->Lbuf.alloc(chunk * per_point))) return rc;
+    m->chunk_P = (int)chunk;
+    m->cap_P = P;
+    return LENSED_OK;
+}
+
+// Optional per-stage timing of enqueue_batch: events recorded around every
+// launch (stage 0 prologue, 1 trace, 2 psf, 3 finalize).
+struct StageTimer {
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+    cudaStream_t st;
+    void begin(int stage)
+    {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, st);
+        marks.push_back({stage, {a, b}});
+    }
+    void end() { cudaEventRecord(marks.back().second.second, st); }
+    ~StageTimer()
+    {
+        for (auto &mk : marks) {
+            cudaEventDestroy(mk.second.first);
+            cudaEventDestroy(mk.second.second);
+        }
+    }
+};
+
+// Enqueue the batched evaluation (no graph) on stream st.
+void enqueue_batch(lensed_model *m, const double *params, int P, double *out, LaunchCfg cfg,
+                   cudaStream_t st, StageTimer *tm = nullptr)
+{
+    if (tm) tm->begin(0);
+    launch_prologue(m->sys.p, 0, m->n_sys, m->comp_type.p, m->comp_free.p, m->comp_value.p,
+                    params, false, P, 0, P, m->n_par_max, m->C_total, m->cf.p, m->cd.p,
+                    m->valid.p, st);
+    if (tm) tm->end();
+    for (int p0 = 0; p0 < P; p0 += m->chunk_P) {
+        const int nP = std::min(m->chunk_P, P - p0);
+        if (tm) tm->begin(1);
+        launch_trace(m->precision, cfg, m->sys.p, m->comp_type.p, m->comp_plane.p, m->cf.p,
+                     m->cd.p, m->valid.p, P, m->C_total, m->trace_blocks.p, m->n_trace_blocks,
+                     m->need.p, m->nodes(), p0, nP, m->Lbuf.p, m->total_pix, st);
+        if (tm) tm->end();
+        if (tm) tm->begin(2);
+        for (const PsfGroup &g : m->psf_groups)
+            launch_psf(m->precision, g.q, g.p_max, m->sys.p, m->psf_f.p, m->psf_d.p, m->data.p,
+                       m->weight.p, m->data_d.p, m->weight_d.p, m->valid.p, P, m->psf_blocks.p + g.off, g.count, p0, nP,
+                       m->Lbuf.p, m->total_pix, m->partial.p, m->T_total, nullptr, st);
+        if (tm) tm->end();
+    }
+    if (tm) tm->begin(3);
+    launch_finalize(m->sys.p, m->valid.p, P, m->partial.p, m->T_total, out, 0, 0, m->n_sys, P,
+                    st);
+    if (tm) tm->end();
+}
+
+int check_model(const lensed_model *m)
+{
+    if (!m) return fail(LENSED_E_ARG, "model is NULL");
+    return LENSED_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+
+extern "C" const char *lensed_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_systems,
+                                   int precision, lensed_model **out)
+{
+    g_last_error.clear();
+    if (!out) return fail(LENSED_E_ARG, "out is NULL");
+    if (!systems || n_systems < 1) return fail(LENSED_E_ARG, "need at least one system");
+    if (precision < LENSED_PREC_FP32 || precision > LENSED_PREC_FP64)
+        return fail(LENSED_E_ARG, "unknown precision %d", precision);
+
+    // ---- validate every descriptor before touching the device
+    int n_par_max = 0, C_total = 0;
+    long long total_pix = 0;
+    for (int s = 0; s < n_systems; ++s) {
+        const lensed_system_desc &d = systems[s];
+        if (d.nx < 1 || d.ny < 1 || d.nx > LENSED_MAX_IMAGE_SIDE || d.ny > LENSED_MAX_IMAGE_SIDE)
+            return fail(LENSED_E_ARG, "system %d: image size %d x %d out of range", s, d.nx, d.ny);
+        if (!(d.pixel_scale > 0.0) || !isfinite(d.pixel_scale))
+            return fail(LENSED_E_ARG, "system %d: pixel_scale must be > 0", s);
+        if (!d.data) return fail(LENSED_E_ARG, "system %d: data is NULL", s);
+        if (!d.variance && !(d.gain > 0.0 && isfinite(d.gain) && isfinite(d.offset)))
+            return fail(LENSED_E_ARG, "system %d: need a variance map or gain > 0", s);
+        if (d.psf) {
+            if (d.psf_nx < 1 || d.psf_ny < 1 || d.psf_nx % 2 == 0 || d.psf_ny % 2 == 0)
+                return fail(LENSED_E_ARG, "system %d: PSF size %d x %d must be odd", s, d.psf_nx,
+                            d.psf_ny);
+            if (d.psf_nx > 2 * LENSED_MAX_PSF_HALF + 1 || d.psf_ny > 2 * LENSED_MAX_PSF_HALF + 1)
+                return fail(LENSED_E_UNSUPPORTED, "system %d: PSF larger than %d x %d", s,
+                            2 * LENSED_MAX_PSF_HALF + 1, 2 * LENSED_MAX_PSF_HALF + 1);
+        }
+        if (d.rule != LENSED_RULE_POINT &&
+            (d.rule_order < 1 || d.rule_order > LENSED_MAX_RULE_ORDER))
+            return fail(LENSED_E_ARG, "system %d: rule order %d out of range", s, d.rule_order);
+        if (d.rule < LENSED_RULE_POINT || d.rule > LENSED_RULE_GL)
+            return fail(LENSED_E_ARG, "system %d: unknown rule %d", s, d.rule);
+        if (d.n_components < 1 || d.n_components > LENSED_MAX_COMPONENTS || !d.components)
+            return fail(LENSED_E_ARG, "system %d: %d components (1..%d)", s, d.n_components,
+                        LENSED_MAX_COMPONENTS);
+        if (d.n_params < 0) return fail(LENSED_E_ARG, "system %d: n_params < 0", s);
+        if (!isfinite(d.zeropoint)) return fail(LENSED_E_ARG, "system %d: zeropoint", s);
+        for (int c = 0; c < d.n_components; ++c) {
+            const lensed_component &cp = d.components[c];
+            const int np = nparams_of(cp.type);
+            if (np < 0) return fail(LENSED_E_ARG, "system %d comp %d: unknown type %d", s, c, cp.type);
+            const bool mass = cp.type <= LENSED_POINTMASS;
+            if (mass && cp.plane != LENSED_PLANE_LENS)
+                return fail(LENSED_E_ARG, "system %d comp %d: mass must be on the lens plane", s, c);
+            if (!mass && cp.plane != LENSED_PLANE_FOREGROUND && cp.plane != LENSED_PLANE_SOURCE)
+                return fail(LENSED_E_ARG, "system %d comp %d: bad plane %d", s, c, cp.plane);
+            for (int k = 0; k < np; ++k) {
+                if (cp.free_index[k] >= d.n_params)
+                    return fail(LENSED_E_ARG, "system %d comp %d: free index %d >= n_params %d",
+                                s, c, cp.free_index[k], d.n_params);
+                if (cp.free_index[k] < 0 && !isfinite(cp.value[k]))
+                    return fail(LENSED_E_NONFINITE, "system %d comp %d: fixed value %d not finite",
+                                s, c, k);
+            }
+        }
+        n_par_max = std::max(n_par_max, d.n_params);
+        C_total += d.n_components;
+        total_pix += (long long)d.nx * d.ny;
+    }
+
+    // ---- host tables
+    std::vector<SysDev> sh(n_systems);
+    std::vector<int> ctype, cplane, cfree;
+    std::vector<double> cval;
+    std::vector<float> data, weight, psf_f, node_u, node_w;
+    std::vector<double> data_d, weight_d, psf_d, node_ud, node_wd;
+    std::vector<int> need;
+    std::vector<std::vector<PsfBlock>> chi_tiles(n_systems);
+    std::vector<int> need_count(n_systems), nn_v(n_systems), pp(n_systems), qq(n_systems),
+        tiles_all(n_systems);
+    long long pix_off = 0;
+    int comp_off = 0, T_total = 0;
+    std::vector<double> ray_flops_v, ray_transc_v;
+    for (int s = 0; s < n_systems; ++s) {
+        const lensed_system_desc &d = systems[s];
+        const int nx = d.nx, ny = d.ny, npix = nx * ny;
+        SysDev &S = sh[s];
+        memset(&S, 0, sizeof(S));
+        S.nx = nx;
+        S.ny = ny;
+        S.npix = npix;
+        S.h = (float)d.pixel_scale;
+        S.hd = d.pixel_scale;
+        S.cx = 0.5f * (nx - 1);
+        S.cy = 0.5f * (ny - 1);
+        S.zeropoint = d.zeropoint;
+        // weights (Sec. 3.2-3.3): w = extra / s^2, zero where masked
+        std::vector<double> w(npix);
+        for (int k = 0; k < npix; ++k) {
+            const bool masked = d.mask && d.mask[k];
+            if (masked) {
+                w[k] = 0.0;
+                data.push_back(0.f);
+                data_d.push_back(0.0);
+                continue;
+            }
+            const double dv = d.data[k];
+            if (!isfinite(dv))
+                return fail(LENSED_E_NONFINITE, "system %d: data[%d] not finite", s, k);
+            const double s2 = d.variance ? d.variance[k] : (dv + d.offset) / d.gain;
+            if (!(s2 > 0.0) || !isfinite(s2))
+                return fail(LENSED_E_NONFINITE, "system %d: variance[%d] = %g not > 0", s, k, s2);
+            const double ex = d.extra_weight ? d.extra_weight[k] : 1.0;
+            if (!isfinite(ex) || ex < 0.0)
+                return fail(LENSED_E_NONFINITE, "system %d: extra_weight[%d] invalid", s, k);
+            w[k] = ex / s2;
+            data.push_back((float)dv);
+            data_d.push_back(dv);
+        }
+        for (int k = 0; k < npix; ++k) {
+            weight.push_back((float)w[k]);
+            weight_d.push_back(w[k]);
+        }
+        // PSF (Sec. 3.1): normalised to unit sum, stored flipped (F_{-k,-l})
+        int P = 0, Q = 0;
+        S.psf_off = (int)psf_f.size();
+        if (d.psf) {
+            P = d.psf_ny / 2;
+            Q = d.psf_nx / 2;
+            double sum = 0.0;
+            for (int k = 0; k < d.psf_nx * d.psf_ny; ++k) {
+                if (!isfinite(d.psf[k]))
+                    return fail(LENSED_E_NONFINITE, "system %d: psf[%d] not finite", s, k);
+                sum += d.psf[k];
+            }
+            if (!(sum != 0.0) || !isfinite(sum))
+                return fail(LENSED_E_NONFINITE, "system %d: PSF sums to %g", s, sum);
+            for (int kk = 0; kk <= 2 * P; ++kk)
+                for (int ll = 0; ll <= 2 * Q; ++ll) {
+                    const double f = d.psf[(2 * P - kk) * d.psf_nx + (2 * Q - ll)] / sum;
+                    psf_d.push_back(f);
+                    psf_f.push_back((float)f);
+                }
+        } else {
+            psf_d.push_back(1.0);
+            psf_f.push_back(1.f);
+        }
+        S.psf_p = P;
+        S.psf_q = Q;
+        pp[s] = P;
+        qq[s] = Q;
+        // quadrature (Eq. 14): offsets t*h and weights
+        std::vector<double> t, wt;
+        rule_nodes(d.rule, d.rule_order, t, wt);
+        S.nn = (int)t.size();
+        S.node_off = (int)node_u.size();
+        nn_v[s] = S.nn;
+        for (size_t a = 0; a < t.size(); ++a) {
+            node_ud.push_back(t[a] * d.pixel_scale);
+            node_wd.push_back(wt[a]);
+            node_u.push_back((float)(t[a] * d.pixel_scale));
+            node_w.push_back((float)wt[a]);
+        }
+        // needed pixels: every pixel an unmasked output reads through the
+        // (clamped) PSF footprint
+        std::vector<unsigned char> nd(npix, 0);
+        for (int i = 0; i < ny; ++i)
+            for (int j = 0; j < nx; ++j) {
+                if (!(w[(size_t)i * nx + j] > 0.0)) continue;
+                for (int k = -P; k <= P; ++k) {
+                    const int ii = std::min(std::max(i + k, 0), ny - 1);
+                    for (int l = -Q; l <= Q; ++l) {
+                        const int jj = std::min(std::max(j + l, 0), nx - 1);
+                        nd[(size_t)ii * nx + jj] = 1;
+                    }
+                }
+            }
+        S.need_off = (long long)need.size();
+        int cnt = 0;
+        for (int k = 0; k < npix; ++k)
+            if (nd[k]) {
+                need.push_back(k);
+                ++cnt;
+            }
+        need_count[s] = cnt;
+        // tiles of the chi^2 pass: those holding an output with w > 0
+        S.tiles_x = (nx + kTileW - 1) / kTileW;
+        S.tiles_y = (ny + kTileH - 1) / kTileH;
+        tiles_all[s] = S.tiles_x * S.tiles_y;
+        S.tile_off = T_total;
+        for (int ty = 0; ty < S.tiles_y; ++ty)
+            for (int tx = 0; tx < S.tiles_x; ++tx) {
+                bool any = false;
+                for (int i = ty * kTileH; i < std::min(ny, (ty + 1) * kTileH) && !any; ++i)
+                    for (int j = tx * kTileW; j < std::min(nx, (tx + 1) * kTileW); ++j)
+                        if (w[(size_t)i * nx + j] > 0.0) {
+                            any = true;
+                            break;
+                        }
+                if (any)
+                    chi_tiles[s].push_back({s, T_total + (int)chi_tiles[s].size(), ty * kTileH,
+                                            tx * kTileW});
+            }
+        S.n_tiles = (int)chi_tiles[s].size();
+        T_total += S.n_tiles;
+        // components
+        S.comp_off = comp_off;
+        S.ncomp = d.n_components;
+        S.n_params = d.n_params;
+        for (int c = 0; c < d.n_components; ++c) {
+            const lensed_component &cp = d.components[c];
+            ctype.push_back(cp.type);
+            cplane.push_back(cp.plane);
+            const int np = nparams_of(cp.type);
+            for (int k = 0; k < LENSED_MAX_COMPONENT_PARAMS; ++k) {
+                cfree.push_back(k < np ? cp.free_index[k] : -1);
+                cval.push_back(k < np && cp.free_index[k] < 0 ? cp.value[k] : 0.0);
+            }
+        }
+        comp_off += d.n_components;
+        {
+            double f = 6.0, tr = 0.0;
+            for (int c = 0; c < d.n_components; ++c) component_ops(d.components[c].type, f, tr);
+            ray_flops_v.push_back(f);
+            ray_transc_v.push_back(tr);
+        }
+        S.pix_off = pix_off;
+        pix_off += npix;
+    }
+
+    lensed_model *m = new lensed_model();
+    m->precision = precision;
+    m->n_sys = n_systems;
+    m->n_par_max = n_par_max;
+    m->C_total = C_total;
+    m->total_pix = total_pix;
+    m->T_total = T_total;
+    m->sys_h = sh;
+    m->need_count = need_count;
+    m->n_nodes = nn_v;
+    m->psf_p = pp;
+    m->psf_q = qq;
+    m->tiles_all = tiles_all;
+    m->ray_flops = ray_flops_v;
+    m->ray_transc = ray_transc_v;
+    cudaGetDevice(&m->device);
+
+    // PSF block tables: chi^2 tiles grouped by q (systems contiguous);
+    // render tiles per system (all tiles)
+    m->psf_sys_off.assign(n_systems, 0);
+    m->psf_sys_cnt.assign(n_systems, 0);
+    for (int q = 0; q <= LENSED_MAX_PSF_HALF; ++q) {
+        PsfGroup g{q, 0, (int)m->psf_blocks_h.size(), 0};
+        for (int s = 0; s < n_systems; ++s) {
+            if (qq[s] != q || chi_tiles[s].empty()) continue;
+            m->psf_sys_off[s] = (int)m->psf_blocks_h.size();
+            m->psf_sys_cnt[s] = (int)chi_tiles[s].size();
+            m->psf_blocks_h.insert(m->psf_blocks_h.end(), chi_tiles[s].begin(), chi_tiles[s].end());
+            g.p_max = std::max(g.p_max, pp[s]);
+        }
+        g.count = (int)m->psf_blocks_h.size() - g.off;
+        if (g.count > 0) m->psf_groups.push_back(g);
+    }
+    m->render_psf_off.assign(n_systems, 0);
+    m->render_psf_cnt.assign(n_systems, 0);
+    for (int s = 0; s < n_systems; ++s) {
+        m->render_psf_off[s] = (int)m->render_psf_h.size();
+        for (int ty = 0; ty < sh[s].tiles_y; ++ty)
+            for (int tx = 0; tx < sh[s].tiles_x; ++tx)
+                m->render_psf_h.push_back({s, 0, ty * kTileH, tx * kTileW});
+        m->render_psf_cnt[s] = (int)m->render_psf_h.size() - m->render_psf_off[s];
+    }
+
+    int rc;
+    init_kernel_attributes();
+    if ((rc = m->sys.upload(sh)) || (rc = m->comp_type.upload(ctype)) ||
+        (rc = m->comp_plane.upload(cplane)) || (rc = m->comp_free.upload(cfree)) ||
+        (rc = m->comp_value.upload(cval)) || (rc = m->data.upload(data)) ||
+        (rc = m->weight.upload(weight)) ||
+        (rc = m->data_d.upload(precision == LENSED_PREC_FP64 ? data_d : std::vector<double>())) ||
+        (rc = m->weight_d.upload(precision == LENSED_PREC_FP64 ? weight_d : std::vector<double>())) || (rc = m->psf_f.upload(psf_f)) ||
+        (rc = m->psf_d.upload(psf_d)) || (rc = m->node_u.upload(node_u)) ||
+        (rc = m->node_w.upload(node_w)) || (rc = m->node_ud.upload(node_ud)) ||
+        (rc = m->node_wd.upload(node_wd)) || (rc = m->need.upload(need)) ||
+        (rc = m->psf_blocks.upload(m->psf_blocks_h)) ||
+        (rc = m->render_psf.upload(m->render_psf_h))) {
+        std::string msg = g_last_error;
+        delete m;
+        g_last_error = msg;
+        return rc;
+    }
+    if ((rc = build_trace_tables(m, m->cfg().trace_threads * m->cfg().pix_per_thread)) ||
+        (rc = m->rcf.alloc((size_t)C_total * kNC)) || (rc = m->rcd.alloc((size_t)C_total * kNC)) ||
+        (rc = m->rvalid.alloc(n_systems))) {
+        std::string msg = g_last_error;
+        delete m;
+        g_last_error = msg;
+        return rc;
+    }
+    size_t max_npix = 0;
+    for (auto &S : sh) max_npix = std::max(max_npix, (size_t)S.npix);
+    if ((rc = m->rL.alloc(total_pix * m->elem()))) {
+        std::string msg = g_last_error;
+        delete m;
+        g_last_error = msg;
+        return rc;
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        delete m;
+        return fail(LENSED_E_CUDA, "create: %s", cudaGetErrorString(e));
+    }
+    *out = m;
+    return LENSED_OK;
+}
+
+extern "C" void lensed_destroy(lensed_model *m) { delete m; }
+
+extern "C" int lensed_model_info_get(const lensed_model *m, lensed_model_info *info)
+{
+    if (check_model(m)) return LENSED_E_ARG;
+    if (!info) return fail(LENSED_E_ARG, "info is NULL");
+    info->n_systems = m->n_sys;
+    info->n_params_max = m->n_par_max;
+    info->precision = m->precision;
+    info->total_pixels = m->total_pix;
+    long long all = 0, traced = 0, taps = 0;
+    double fl = 0.0, tr = 0.0;
+    for (int s = 0; s < m->n_sys; ++s) {
+        const long long rays = (long long)m->n_nodes[s] * m->n_nodes[s];
+        all += (long long)m->sys_h[s].npix * rays;
+        traced += (long long)m->need_count[s] * rays;
+        fl += (double)m->need_count[s] * rays * m->ray_flops[s];
+        tr += (double)m->need_count[s] * rays * m->ray_transc[s];
+        taps += (long long)m->psf_sys_cnt[s] * kTileW * kTileH * (2 * m->psf_p[s] + 1) *
+                (2 * m->psf_q[s] + 1);
+    }
+    info->rays_per_eval_all = all;
+    info->rays_per_eval_traced = traced;
+    info->psf_taps_per_eval = taps;
+    info->flops_per_ray = traced > 0 ? fl / traced : 0.0;
+    info->transcendentals_per_ray = traced > 0 ? tr / traced : 0.0;
+    return LENSED_OK;
+}
+
+extern "C" int lensed_render(lensed_model *m, int system, const double *params, int flags,
+                             float *out_image, void *stream)
+{
+    if (check_model(m)) return LENSED_E_ARG;
+    if (system < 0 || system >= m->n_sys) return fail(LENSED_E_ARG, "system %d out of range", system);
+    if (!params || !out_image) return fail(LENSED_E_ARG, "params/out_image is NULL");
+    if (flags != LENSED_RENDER_CONVOLVED && flags != LENSED_RENDER_UNCONVOLVED)
+        return fail(LENSED_E_ARG, "unknown flags %d", flags);
+    cudaStream_t st = (cudaStream_t)stream;
+    const SysDev &S = m->sys_h[system];
+    // one point: consts at p = 0, valid at index system (P = 1)
+    launch_prologue(m->sys.p, system, 1, m->comp_type.p, m->comp_free.p, m->comp_value.p, params,
+                    true, 1, 0, 1, m->n_par_max, m->C_total, m->rcf.p, m->rcd.p, m->rvalid.p, st);
+    launch_trace(m->precision, m->cfg(), m->sys.p, m->comp_type.p, m->comp_plane.p, m->rcf.p,
+                 m->rcd.p, m->rvalid.p, 1, m->C_total,
+                 m->render_trace.p + m->render_trace_off[system], m->render_trace_cnt[system],
+                 nullptr, m->nodes(), 0, 1, m->rL.p, m->total_pix, st);
+    if (flags == LENSED_RENDER_UNCONVOLVED) {
+        launch_copy_image(m->precision, m->rL.p, S.pix_off, S.npix, m->rvalid.p + system,
+                          out_image, st);
+    } else {
+        launch_psf(m->precision, m->psf_q[system], m->psf_p[system], m->sys.p, m->psf_f.p,
+                   m->psf_d.p, m->data.p, m->weight.p, m->data_d.p, m->weight_d.p, m->rvalid.p, 1,
+                   m->render_psf.p + m->render_psf_off[system], m->render_psf_cnt[system], 0, 1,
+                   m->rL.p, m->total_pix, nullptr, 0, out_image, st);
+    }
+    CUDA_OK(cudaGetLastError());
+    return LENSED_OK;
+}
+
+static int loglike_args(lensed_model *m, const double *params, int P, double *out)
+{
+    if (check_model(m)) return LENSED_E_ARG;
+    if (!params || !out) return fail(LENSED_E_ARG, "params/out is NULL");
+    if (P < 1) return fail(LENSED_E_ARG, "P = %d must be >= 1", P);
+    return LENSED_OK;
+}
+
+static int run_batch(lensed_model *m, const double *params, int P, double *out, cudaStream_t st,
+                     bool use_graph)
+{
+    int rc = ensure_capacity(m, P);
+    if (rc) return rc;
+    LaunchCfg cfg = m->cfg();
+    if ((rc = build_trace_tables(m, cfg.trace_threads * cfg.pix_per_thread))) return rc;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (st) cudaStreamIsCapturing(st, &cs);
+    if (!use_graph || cs != cudaStreamCaptureStatusNone) {
+        enqueue_batch(m, params, P, out, cfg, st);
+        CUDA_OK(cudaGetLastError());
+        return LENSED_OK;
+    }
+    // graph cache keyed by (P, params, out, configuration)
+    GraphEntry *hit = nullptr;
+    for (auto &g : m->graphs)
+        if (g.P == P && g.params == params && g.out == out && g.cfg == m->cfg_index) hit = &g;
+    if (!hit) {
+        if (m->graphs.size() >= 8) {
+            auto old = std::min_element(m->graphs.begin(), m->graphs.end(),
+                                        [](const GraphEntry &a, const GraphEntry &b) {
+                                            return a.age < b.age;
+                                        });
+            cudaGraphExecDestroy(old->exec);
+            m->graphs.erase(old);
+        }
+        cudaGraph_t graph;
+        CUDA_OK(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_batch(m, params, P, out, cfg, m->cap_stream);
+        cudaError_t e1 = cudaGetLastError();
+        cudaError_t e2 = cudaStreamEndCapture(m->cap_stream, &graph);
+        if (e1 != cudaSuccess || e2 != cudaSuccess)
+            return fail(LENSED_E_CUDA, "graph capture: %s / %s", cudaGetErrorString(e1),
+                        cudaGetErrorString(e2));
+        cudaGraphExec_t exec;
+        cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e3 != cudaSuccess)
+            return fail(LENSED_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e3));
+        m->graphs.push_back({P, params, out, m->cfg_index, exec, 0});
+        hit = &m->graphs.back();
+    }
+    hit->age = ++m->graph_clock;
+    CUDA_OK(cudaGraphLaunch(hit->exec, st));
+    return LENSED_OK;
+}
+
+extern "C" int lensed_loglike_batch(lensed_model *m, const double *params, int P,
+                                    double *out_loglike, void *stream)
+{
+    int rc = loglike_args(m, params, P, out_loglike);
+    if (rc) return rc;
+    return run_batch(m, params, P, out_loglike, (cudaStream_t)stream, true);
+}
+
+extern "C" int lensed_loglike_plain(lensed_model *m, const double *params, int P,
+                                    double *out_loglike, void *stream)
+{
+    int rc = loglike_args(m, params, P, out_loglike);
+    if (rc) return rc;
+    if ((rc = ensure_capacity(m, P))) return rc;
+    LaunchCfg cfg = m->cfg();
+    if ((rc = build_trace_tables(m, cfg.trace_threads * cfg.pix_per_thread))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int s = 0; s < m->n_sys; ++s) {
+        for (int p = 0; p < P; ++p) {
+            launch_prologue(m->sys.p, s, 1, m->comp_type.p, m->comp_free.p, m->comp_value.p,
+                            params, false, P, p, 1, m->n_par_max, m->C_total, m->cf.p, m->cd.p,
+                            m->valid.p, st);
+            launch_trace(m->precision, cfg, m->sys.p, m->comp_type.p, m->comp_plane.p, m->cf.p,
+                         m->cd.p, m->valid.p, P, m->C_total,
+                         m->trace_blocks.p + m->trace_sys_off[s], m->trace_sys_cnt[s], m->need.p,
+                         m->nodes(), p, 1, m->Lbuf.p, m->total_pix, st);
+            if (m->psf_sys_cnt[s] > 0)
+                launch_psf(m->precision, m->psf_q[s], m->psf_p[s], m->sys.p, m->psf_f.p,
+                           m->psf_d.p, m->data.p, m->weight.p, m->data_d.p, m->weight_d.p, m->valid.p, P,
+                           m->psf_blocks.p + m->psf_sys_off[s], m->psf_sys_cnt[s], p, 1,
+                           m->Lbuf.p, m->total_pix, m->partial.p, m->T_total, nullptr, st);
+            launch_finalize(m->sys.p, m->valid.p, P, m->partial.p, m->T_total, out_loglike, s,
+                            p, 1, 1, st);
+        }
+    }
+    CUDA_OK(cudaGetLastError());
+    return LENSED_OK;
+}
+
+extern "C" int lensed_loglike_batch_host(lensed_model *m, const double *params_host, int P,
+                                         double *out_host, void *stream)
+{
+    int rc = loglike_args(m, params_host, P, out_host);
+    if (rc) return rc;
+    const size_t np = (size_t)m->n_sys * P * m->n_par_max;
+    const size_t no = (size_t)m->n_sys * P;
+    if (m->stage_params.n < std::max<size_t>(np, 1) || m->stage_out.n < no) {
+        cudaDeviceSynchronize();
+        m->clear_graphs();
+        if ((rc = m->stage_params.alloc(np)) || (rc = m->stage_out.alloc(no))) return rc;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_OK(cudaMemcpyAsync(m->stage_params.p, params_host, np * sizeof(double),
+                            cudaMemcpyHostToDevice, st));
+    if ((rc = run_batch(m, m->stage_params.p, P, m->stage_out.p, st, true))) return rc;
+    CUDA_OK(cudaMemcpyAsync(out_host, m->stage_out.p, no * sizeof(double), cudaMemcpyDeviceToHost,
+                            st));
+    CUDA_OK(cudaStreamSynchronize(st));
+    return LENSED_OK;
+}
+
+extern "C" int lensed_autotune(lensed_model *m, const double *params, int P, void *stream)
+{
+    int rc = loglike_args(m, params, P, (double *)params);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    DevBuf<double> tmp;
+    if ((rc = tmp.alloc((size_t)m->n_sys * P))) return rc;
+    cudaEvent_t e0, e1;
+    CUDA_OK(cudaEventCreate(&e0));
+    CUDA_OK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_i = 0;
+    const int saved = m->cfg_index;
+    for (int i = 0; i < kNumCandidates; ++i) {
+        m->cfg_index = i;
+        float t_min = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            if ((rc = run_batch(m, params, P, tmp.p, st, false))) {
+                m->cfg_index = saved;
+                return rc;
+            }
+            cudaEventRecord(e0, st);
+            run_batch(m, params, P, tmp.p, st, false);
+            cudaEventRecord(e1, st);
+            CUDA_OK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t_min = std::min(t_min, ms);
+        }
+        if (t_min < best) {
+            best = t_min;
+            best_i = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m->cfg_index = best_i;
+    LaunchCfg cfg = m->cfg();
+    if ((rc = build_trace_tables(m, cfg.trace_threads * cfg.pix_per_thread))) return rc;
+    CUDA_OK(cudaStreamSynchronize(st));
+    return LENSED_OK;
+}
+
+extern "C" int lensed_batch_plan(lensed_model *m, int P, int *launches, int *chunk_points)
+{
+    if (check_model(m)) return LENSED_E_ARG;
+    if (P < 1 || !launches || !chunk_points) return fail(LENSED_E_ARG, "bad arguments");
+    int rc = ensure_capacity(m, P);
+    if (rc) return rc;
+    const int chunks = (P + m->chunk_P - 1) / m->chunk_P;
+    *launches = 2 + chunks * (1 + (int)m->psf_groups.size());
+    *chunk_points = m->chunk_P;
+    return LENSED_OK;
+}
+
+extern "C" int lensed_profile_batch(lensed_model *m, const double *params, int P,
+                                    double *out_loglike, void *stream, double *stage_ms,
+                                    int *trace_launches)
+{
+    int rc = loglike_args(m, params, P, out_loglike);
+    if (rc) return rc;
+    if (!stage_ms) return fail(LENSED_E_ARG, "stage_ms is NULL");
+    if ((rc = ensure_capacity(m, P))) return rc;
+    LaunchCfg cfg = m->cfg();
+    if ((rc = build_trace_tables(m, cfg.trace_threads * cfg.pix_per_thread))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    StageTimer tm;
+    tm.st = st;
+    enqueue_batch(m, params, P, out_loglike, cfg, st, &tm);
+    CUDA_OK(cudaGetLastError());
+    CUDA_OK(cudaStreamSynchronize(st));
+    for (int k = 0; k < 4; ++k) stage_ms[k] = 0.0;
+    int nt = 0;
+    for (auto &mk : tm.marks) {
+        float ms = 0.f;
+        CUDA_OK(cudaEventElapsedTime(&ms, mk.second.first, mk.second.second));
+        stage_ms[mk.first] += ms;
+        nt += mk.first == 1;
+    }
+    if (trace_launches) *trace_launches = nt;
+    return LENSED_OK;
+}
+
+extern "C" int lensed_tuned_config(const lensed_model *m, char *buf, int buflen)
+{
+    if (check_model(m)) return -1;
+    if (buf && buflen > 0) {
+        const char *name = kCandidates[m->cfg_index < 0 ? 0 : m->cfg_index].name;
+        snprintf(buf, (size_t)buflen, "%s%s", name, m->cfg_index < 0 ? " (default)" : "");
+    }
+    return m->cfg_index;
+}
