@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp32", "mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--points", type=int, default=POINTS,
+                    help="points per step (profiling of small cases only; the benchmark "
+                         "workload is 4096)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain per-point pass")
     return ap.parse_args()
 
 
@@ -196,16 +200,17 @@ def main():
     probe.close()
     obs = W.add_noise(spec, noiseless, spec["seed"])
     m = LZ.Model(spec, obs, precision=args.precision)
-    pts = W.draw_points(spec, POINTS, 4242 + rank)
+    npts = args.points
+    pts = W.draw_points(spec, npts, 4242 + rank)
     params = m.pack_params(pts)
-    out = torch.empty((1, POINTS), dtype=torch.float64, device="cuda")
+    out = torch.empty((1, npts), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     with torch.cuda.stream(stream):
         m.autotune(params, stream=stream)
         tuned = m.tuned_config()
-        launches, chunk = m.batch_plan(POINTS)
+        launches, chunk = m.batch_plan(npts)
         for _ in range(max(3, args.warmup)):
             m.loglike_batch(params, out=out, stream=stream)
         stream.synchronize()
@@ -250,23 +255,25 @@ def main():
         trace_launches //= n_prof
 
         # ---- plain per-point path, same points (paper-style scheduling)
-        plain_out = torch.empty_like(out)
-        m.loglike_plain(params, out=plain_out, stream=stream)
-        stream.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        e0.record(stream)
-        m.loglike_plain(params, out=plain_out, stream=stream)
-        e1.record(stream)
-        stream.synchronize()
-        plain_ms = e0.elapsed_time(e1)
-        bit_equal = bool(torch.equal(plain_out, out))
+        plain_ms, bit_equal = None, None
+        if not args.no_plain:
+            plain_out = torch.empty_like(out)
+            m.loglike_plain(params, out=plain_out, stream=stream)
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            e0.record(stream)
+            m.loglike_plain(params, out=plain_out, stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            plain_ms = e0.elapsed_time(e1)
+            bit_equal = bool(torch.equal(plain_out, out))
 
     # ---- end to end through the host-buffer C call (copies inside)
     host_params = torch.empty(params.shape, dtype=torch.float64).pin_memory()
     host_params.copy_(params.cpu())
-    host_out = torch.empty((1, POINTS), dtype=torch.float64).pin_memory()
+    host_out = torch.empty((1, npts), dtype=torch.float64).pin_memory()
     for _ in range(3):
         m.loglike_batch_host(host_params, host_out, stream=stream)
     k_e2e = max(10, args.steps // 2)
@@ -284,14 +291,14 @@ def main():
         return 0
 
     ms_step = dev_ms / args.steps
-    evals_s = world * POINTS / (ms_step * 1e-3)
+    evals_s = world * npts / (ms_step * 1e-3)
     rays_traced = m.rays_per_eval_traced
     grays = evals_s * rays_traced / 1e9
     pk, pk_src = peaks()
     sm_mhz_peak = float(pk.get("sm_max_mhz", FALLBACK_SM_MHZ))
     fp32_peak = SMS * 128 * 2 * sm_mhz_peak * 1e6 / 1e12  # TFLOP/s, FMA = 2
     trace_ms = stage_ms["trace"] / max(trace_launches, 1)
-    pts_per_launch = POINTS / max(trace_launches, 1)
+    pts_per_launch = npts / max(trace_launches, 1)
     flops_launch = pts_per_launch * rays_traced * m.flops_per_ray
     achieved = flops_launch / (trace_ms * 1e-3) / 1e12
     line = {
@@ -300,19 +307,21 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "points_per_step": POINTS, "image": "200x200",
+        "config": {"workload": WORKLOAD if npts == POINTS else f"{WORKLOAD} (profiling case: {npts} points)",
+                   "points_per_step": npts, "image": "200x200",
                    "rule": "gauss-legendre 5x5", "psf": "21x21", "precision_mode": args.precision,
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"independent points per rank x{world}",
                    "tuned": tuned[1], "chunk_points": chunk},
         "grays_per_s": grays,
         "rays_per_eval_traced": rays_traced,
-        "plain": {"evals_per_s": world * POINTS / (plain_ms * 1e-3),
-                  "grays_per_s": world * POINTS / (plain_ms * 1e-3) * rays_traced / 1e9,
-                  "speedup_batched_vs_plain": plain_ms / ms_step,
-                  "bit_identical_to_batched": bit_equal},
+        "plain": None if plain_ms is None else {
+            "evals_per_s": world * npts / (plain_ms * 1e-3),
+            "grays_per_s": world * npts / (plain_ms * 1e-3) * rays_traced / 1e9,
+            "speedup_batched_vs_plain": plain_ms / ms_step,
+            "bit_identical_to_batched": bit_equal},
         "stage_ms": stage_ms,
-        "e2e": {"value": world * POINTS / e2e_s, "unit": "evals/s",
+        "e2e": {"value": world * npts / e2e_s, "unit": "evals/s",
                 "h2d_bytes_per_step": int(host_params.numel() * 8),
                 "d2h_bytes_per_step": int(host_out.numel() * 8)},
         "gpu_launches": launches * args.steps,

@@ -10,7 +10,12 @@
 namespace lensed {
 
 // Packed per-component constants, FP32 and FP64 copies, kNC values each.
-constexpr int kNC = 16;
+// The FP32 copy carries, for the constants a coherent rounding error would
+// bias (the SIE prefactor, axis ratio, eccentricity and orientation; the
+// light profiles' scale, exponent and amplitude), a second float with the
+// rounding residual (value - (float)value), used in compensated multiply-
+// adds; the FP64 copy has zeros there.
+constexpr int kNC = 24;
 // Tile of the PSF / chi^2 kernel: kTileW columns x kTileH rows of outputs,
 // kPsfThreads threads, each computing kOutPerThread consecutive columns.
 constexpr int kTileW = 64;
@@ -31,11 +36,12 @@ constexpr double kSeriesE = 1e-3;
 
 struct SysDev {
     int nx, ny, npix;
-    float h;
+    float h, h_lo;       // pixel side as a float pair (h ~ h + h_lo)
     double hd;
     float cx, cy;        // (nx-1)/2, (ny-1)/2
     int nn;              // 1-D nodes of the rule
-    int node_off;        // into the node tables
+    int node_off;        // into the 1-D node tables
+    int w2_off;          // into the 2-D weight tables (nn * nn)
     int psf_p, psf_q;    // PSF half sizes (0, 0 without a PSF)
     int psf_off;         // into the flipped, normalised PSF table
     long long pix_off;   // into data / weights / per-point image scratch
@@ -54,7 +60,8 @@ struct TraceBlock {
     int start, end;
 };
 
-// 1-D quadrature nodes (offsets t*h from the pixel centre) and weights.
+// Quadrature nodes: 1-D offsets t*h from the pixel centre, and the 2-D
+// weights W_a W_b (float copy adjusted so that it sums to one).
 struct NodeTables {
     const float *u, *w;
     const double *ud, *wd;
@@ -75,11 +82,14 @@ struct LaunchCfg {
 // --- kernels launched from the runtime (defined in lensed_kernels.cu) ---
 
 // a1: per (system, point) packed constants and validity.
-// With single_row, params is one row (the render path).
-void launch_prologue(const SysDev *sys, int s0, int nS, const int *comp_type,
-                     const int *comp_free, const double *comp_value, const double *params,
-                     bool single_row, int P, int p0, int nP, int n_par_stride, int C_total,
-                     float *cf, double *cd, unsigned char *valid, cudaStream_t st);
+// a1 for components c0 .. c0+nC-1 (global indices, belonging to systems
+// s0 .. s0+nS-1) and points p0 .. p0+nP-1; with single_row, params is one
+// row (the render path).  cvalid: [P][C_total] scratch bytes.
+void launch_prologue(const SysDev *sys, const int *comp_sys, int s0, int nS, int c0, int nC,
+                     const int *comp_type, const int *comp_free, const double *comp_value,
+                     const double *params, bool single_row, int P, int p0, int nP,
+                     int n_par_stride, int C_total, float *cf, double *cd, unsigned char *cvalid,
+                     unsigned char *valid, cudaStream_t st);
 
 // a2-a5: pixel luminosities of the pixels in the block table, for points
 // p0 .. p0 + nP - 1, into Lbuf[(p - p0) * L_stride + pix_off + pix].

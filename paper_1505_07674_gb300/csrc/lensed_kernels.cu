@@ -41,25 +41,6 @@ __device__ __forceinline__ float lg2f(float x)
     return y;
 }
 
-template <typename T>
-struct Math;
-template <>
-struct Math<float> {
-    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
-    static __device__ __forceinline__ float atan_(float x) { return atanf(x); }
-    static __device__ __forceinline__ float atanh_(float x) { return atanhf(x); }
-    static __device__ __forceinline__ float exp2_(float x) { return ex2f(x); }
-    static __device__ __forceinline__ float log2_(float x) { return lg2f(x); }
-};
-template <>
-struct Math<double> {
-    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-    static __device__ __forceinline__ double atan_(double x) { return atan(x); }
-    static __device__ __forceinline__ double atanh_(double x) { return atanh(x); }
-    static __device__ __forceinline__ double exp2_(double x) { return exp2(x); }
-    static __device__ __forceinline__ double log2_(double x) { return log2(x); }
-};
-
 // ---------------------------------------------------------------------------
 // a1: parameter prologue
 
@@ -83,7 +64,7 @@ __device__ double sersic_b(double n)
     const double a = 2.0 * n;
     double lo = 0.0, hi = a;
     double b = a - 1.0 / 3.0 + 4.0 / (405.0 * n) + 46.0 / (25515.0 * n * n) +
-               131.0 / (1148175.0 * n * n * n);
+               131.0 / (1148175.0 * n * n * n) - 2194697.0 / (30690717750.0 * n * n * n * n);
     if (!(b > lo && b < hi)) b = 0.5 * (lo + hi);
     const double lga = lgamma(a);
     for (int it = 0; it < 200; ++it) {
@@ -100,163 +81,251 @@ __device__ double sersic_b(double n)
     return b;
 }
 
-__global__ void k_prologue(const SysDev *__restrict__ sys, int s0, int nS,
-                           const int *__restrict__ comp_type, const int *__restrict__ comp_free,
-                           const double *__restrict__ comp_value,
-                           const double *__restrict__ params, int single_row, int P, int p0,
-                           int nP,
-                           int n_par_stride, int C_total, float *__restrict__ cf,
-                           double *__restrict__ cd, unsigned char *__restrict__ valid)
+// One thread per (point, component): resolve the component's parameters,
+// check its domain and write its packed constants and a validity byte.
+__global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__restrict__ comp_sys,
+                                int c0, int nC, const int *__restrict__ comp_type,
+                                const int *__restrict__ comp_free,
+                                const double *__restrict__ comp_value,
+                                const double *__restrict__ params, int single_row, int P, int p0,
+                                int nP, int n_par_stride, int C_total, float *__restrict__ cf,
+                                double *__restrict__ cd, unsigned char *__restrict__ cvalid)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (long long)nC * nP) return;
+    const int gc = c0 + (int)(tid % nC);
+    const int p = p0 + (int)(tid / nC);
+    const int s = comp_sys[gc];
+    const double zeropoint = sys[s].zeropoint;
+    const double hd = sys[s].hd;
+    const double *row = single_row ? params : params + ((size_t)s * P + p) * n_par_stride;
+    const int type = comp_type[gc];
+    double v[LENSED_MAX_COMPONENT_PARAMS];
+#pragma unroll
+    for (int k = 0; k < LENSED_MAX_COMPONENT_PARAMS; ++k) {
+        const int fi = comp_free[gc * LENSED_MAX_COMPONENT_PARAMS + k];
+        v[k] = fi >= 0 ? row[fi] : comp_value[gc * LENSED_MAX_COMPONENT_PARAMS + k];
+    }
+    double o[kNC];
+#pragma unroll
+    for (int k = 0; k < kNC; ++k) o[k] = 0.0;
+    // slots whose FP32 copy gets a residual partner: lo[k] = partner of k
+    int lo[kNC];
+#pragma unroll
+    for (int k = 0; k < kNC; ++k) lo[k] = -1;
+    const int np = type == LENSED_SIE ? 6 : type == LENSED_SHEAR ? 4
+                 : type == LENSED_POINTMASS ? 3 : type == LENSED_SERSIC ? 7 : 6;
+    bool ok = true;
+    for (int k = 0; k < np; ++k) ok = ok && isfinite(v[k]);
+    o[0] = v[0];
+    o[1] = v[1];
+    if (type == LENSED_SIE) {
+        // 0 x0, 1 y0, 2 cos, 3 sin, 4 q^2, 5 s^2, 6 s, 7 q^2 s, 8 e, 9 pref,
+        // 10 series flag, 11 e^2, 12 FP64 flag (MIXED), 13 4s;
+        // residuals: 14 q^2, 15 e, 16 pref, 17 cos, 18 sin
+        const double b = v[2], q = v[3], sc = v[5];
+        ok = ok && q > 0.0 && q <= 1.0 && b >= 0.0 && sc >= 0.0;
+        double sn, cs;
+        sincospi(v[4] / 180.0, &sn, &cs);
+        const double e = sqrt((1.0 - q) * (1.0 + q));
+        const bool series = e < kSeriesE;
+        o[2] = cs;
+        o[3] = sn;
+        o[4] = q * q;
+        o[5] = sc * sc;
+        o[6] = sc;
+        o[7] = q * q * sc;
+        o[8] = e;
+        o[9] = series ? b * sqrt(q) : b * sqrt(q) / e;
+        o[10] = series ? 1.0 : 0.0;
+        o[11] = e * e;
+        o[12] = e < kMixedRoundE ? 1.0 : 0.0;
+        o[13] = kMixedCoreFactor * sc;
+        lo[4] = 14;
+        lo[8] = 15;
+        lo[9] = 16;
+        lo[2] = 17;
+        lo[3] = 18;
+    } else if (type == LENSED_SHEAR) {
+        double sn, cs;
+        sincospi(v[3] / 90.0, &sn, &cs);  // 2 phi
+        o[2] = v[2] * cs;
+        o[3] = v[2] * sn;
+    } else if (type == LENSED_POINTMASS) {
+        ok = ok && v[2] >= 0.0;
+        o[2] = v[2] * v[2];
+    } else {
+        // light: Sersic (x y r mag n q pa), de Vaucouleurs (x y r mag q pa),
+        // Gaussian (x y sigma mag q pa).
+        // 0 x0, 1 y0, 2 cos, 3 sin, 4 q/r^2, 5 1/(q r^2), 6 p2, 7 B, 8 A,
+        // 9 kind; residuals: 10 A, 11 cos, 12 sin, 13 B, 14 q/r^2, 15 1/(q r^2).
+        // rho^2 = (q u^2 + v^2/q)/r^2; Sersic t = B rho^(2 p2) with B = b_n
+        // log2(e), p2 = 1/(2n); Gaussian (r = sqrt(2) sigma) t = B rho^2 with
+        // B = log2(e); I = A 2^-t with A = I_0 h^2.
+        const double r = v[2];
+        const double F = pow(10.0, -0.4 * (v[3] - zeropoint));
+        double n = 4.0, q, pa;
+        if (type == LENSED_SERSIC) { n = v[4]; q = v[5]; pa = v[6]; }
+        else { q = v[4]; pa = v[5]; }
+        ok = ok && r > 0.0 && n > 0.0 && q > 0.0 && q <= 1.0;
+        double sn, cs;
+        sincospi(pa / 180.0, &sn, &cs);
+        o[2] = cs;
+        o[3] = sn;
+        lo[8] = 10;
+        lo[2] = 11;
+        lo[3] = 12;
+        lo[7] = 13;
+        lo[4] = 14;
+        lo[5] = 15;
+        if (ok && type == LENSED_GAUSS) {
+            const double r2 = 2.0 * r * r;
+            o[4] = q / r2;
+            o[5] = 1.0 / (q * r2);
+            o[6] = 1.0;
+            o[7] = 1.4426950408889634;  // log2(e)
+            o[8] = F / (M_PI * r2) * hd * hd;
+            o[9] = kKindGauss;
+        } else if (ok) {
+            const double bn = sersic_b(n);
+            // I_0 = F b^(2n) / (2 pi n r^2 Gamma(2n)), in logs
+            const double lI0 = log(F) + 2.0 * n * log(bn) - log(2.0 * M_PI * n * r * r) -
+                               lgamma(2.0 * n);
+            o[4] = q / (r * r);
+            o[5] = 1.0 / (q * r * r);
+            o[6] = 0.5 / n;
+            o[7] = bn * 1.4426950408889634;
+            o[8] = exp(lI0) * hd * hd;
+            o[9] = kKindPower;
+        }
+    }
+    const size_t base = ((size_t)p * C_total + gc) * kNC;
+    float f[kNC];
+#pragma unroll
+    for (int k = 0; k < kNC; ++k) f[k] = (float)o[k];
+#pragma unroll
+    for (int k = 0; k < kNC; ++k)
+        if (lo[k] >= 0) f[lo[k]] = (float)(o[k] - (double)f[k]);
+#pragma unroll
+    for (int k = 0; k < kNC; ++k) {
+        cd[base + k] = o[k];
+        cf[base + k] = f[k];
+    }
+    cvalid[(size_t)p * C_total + gc] = ok ? 1 : 0;
+}
+
+// Validity of a (system, point): every component in its domain.
+__global__ void k_prologue_valid(const SysDev *__restrict__ sys, int s0, int nS, int P, int p0,
+                                 int nP, int C_total, const unsigned char *__restrict__ cvalid,
+                                 unsigned char *__restrict__ valid)
 {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= (long long)nS * nP) return;
     const int s = s0 + (int)(tid / nP);
     const int p = p0 + (int)(tid % nP);
-    const SysDev S = sys[s];
-    const double *row = single_row ? params : params + ((size_t)s * P + p) * n_par_stride;
-    bool ok = true;
-    for (int c = 0; c < S.ncomp; ++c) {
-        const int gc = S.comp_off + c;
-        const int type = comp_type[gc];
-        double v[LENSED_MAX_COMPONENT_PARAMS];
-        for (int k = 0; k < LENSED_MAX_COMPONENT_PARAMS; ++k) {
-            const int fi = comp_free[gc * LENSED_MAX_COMPONENT_PARAMS + k];
-            v[k] = fi >= 0 ? row[fi] : comp_value[gc * LENSED_MAX_COMPONENT_PARAMS + k];
-        }
-        double o[kNC];
-        for (int k = 0; k < kNC; ++k) o[k] = 0.0;
-        int np = 0;
-        switch (type) {
-        case LENSED_SIE: np = 6; break;
-        case LENSED_SHEAR: np = 4; break;
-        case LENSED_POINTMASS: np = 3; break;
-        case LENSED_SERSIC: np = 7; break;
-        default: np = 6; break;
-        }
-        for (int k = 0; k < np; ++k) ok = ok && isfinite(v[k]);
-        o[0] = v[0];
-        o[1] = v[1];
-        if (type == LENSED_SIE) {
-            const double b = v[2], q = v[3], sc = v[5];
-            ok = ok && q > 0.0 && q <= 1.0 && b >= 0.0 && sc >= 0.0;
-            double sn, cs;
-            sincospi(v[4] / 180.0, &sn, &cs);
-            const double e = sqrt((1.0 - q) * (1.0 + q));
-            const bool series = e < kSeriesE;
-            o[2] = cs;
-            o[3] = sn;
-            o[4] = q * q;
-            o[5] = sc * sc;
-            o[6] = sc;
-            o[7] = q * q * sc;
-            o[8] = e;
-            o[9] = series ? b * sqrt(q) : b * sqrt(q) / e;
-            o[10] = series ? 1.0 : 0.0;
-            o[11] = e * e;
-            o[12] = e < kMixedRoundE ? 1.0 : 0.0;
-            o[13] = kMixedCoreFactor * sc;
-        } else if (type == LENSED_SHEAR) {
-            double sn, cs;
-            sincospi(v[3] / 90.0, &sn, &cs);  // 2 phi
-            o[2] = v[2] * cs;
-            o[3] = v[2] * sn;
-        } else if (type == LENSED_POINTMASS) {
-            ok = ok && v[2] >= 0.0;
-            o[2] = v[2] * v[2];
-        } else {
-            // light: Sersic (x y r mag n q pa), de Vaucouleurs (x y r mag q pa),
-            // Gaussian (x y sigma mag q pa)
-            const double r = v[2];
-            const double F = pow(10.0, -0.4 * (v[3] - S.zeropoint));
-            double n = 4.0, q, pa;
-            if (type == LENSED_SERSIC) { n = v[4]; q = v[5]; pa = v[6]; }
-            else { q = v[4]; pa = v[5]; }
-            ok = ok && r > 0.0 && n > 0.0 && q > 0.0 && q <= 1.0;
-            double sn, cs;
-            sincospi(pa / 180.0, &sn, &cs);
-            o[2] = cs;
-            o[3] = sn;
-            o[4] = q;
-            o[5] = 1.0 / q;
-            if (ok && type == LENSED_GAUSS) {
-                o[6] = 1.0;
-                o[7] = 1.4426950408889634 / (2.0 * r * r);  // log2(e) / (2 sigma^2)
-                o[8] = F / (2.0 * M_PI * r * r) * S.hd * S.hd;
-                o[9] = kKindGauss;
-            } else if (ok) {
-                const double bn = sersic_b(n);
-                // I_0 = F b^(2n) / (2 pi n r^2 Gamma(2n)), in logs
-                const double lI0 = log(F) + 2.0 * n * log(bn) - log(2.0 * M_PI * n * r * r) -
-                                   lgamma(2.0 * n);
-                o[6] = 0.5 / n;
-                o[7] = log2(bn) + log2(1.4426950408889634) - log2(r) / n;
-                o[8] = exp(lI0) * S.hd * S.hd;
-                o[9] = kKindPower;
-            }
-        }
-        const size_t base = ((size_t)p * C_total + gc) * kNC;
-        for (int k = 0; k < kNC; ++k) {
-            cd[base + k] = o[k];
-            cf[base + k] = (float)o[k];
-        }
-    }
-    valid[(size_t)s * P + p] = ok ? 1 : 0;
+    const SysDev &S = sys[s];
+    unsigned char ok = 1;
+    for (int c = 0; c < S.ncomp; ++c) ok &= cvalid[(size_t)p * C_total + S.comp_off + c];
+    valid[(size_t)s * P + p] = ok;
 }
 
-void launch_prologue(const SysDev *sys, int s0, int nS, const int *comp_type,
-                     const int *comp_free, const double *comp_value, const double *params,
-                     bool single_row, int P, int p0, int nP, int n_par_stride, int C_total,
-                     float *cf, double *cd, unsigned char *valid, cudaStream_t st)
+void launch_prologue(const SysDev *sys, const int *comp_sys, int s0, int nS, int c0, int nC,
+                     const int *comp_type, const int *comp_free, const double *comp_value,
+                     const double *params, bool single_row, int P, int p0, int nP,
+                     int n_par_stride, int C_total, float *cf, double *cd, unsigned char *cvalid,
+                     unsigned char *valid, cudaStream_t st)
 {
-    const long long n = (long long)nS * nP;
-    const int threads = 128;
-    const unsigned blocks = (unsigned)((n + threads - 1) / threads);
-    k_prologue<<<blocks, threads, 0, st>>>(sys, s0, nS, comp_type, comp_free, comp_value, params,
-                                           single_row ? 1 : 0, P, p0, nP, n_par_stride, C_total,
-                                           cf, cd, valid);
+    const long long n = (long long)nC * nP;
+    const int threads = 64;
+    k_prologue_comp<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
+        sys, comp_sys, c0, nC, comp_type, comp_free, comp_value, params, single_row ? 1 : 0, P,
+        p0, nP, n_par_stride, C_total, cf, cd, cvalid);
+    const long long n2 = (long long)nS * nP;
+    k_prologue_valid<<<(unsigned)((n2 + 127) / 128), 128, 0, st>>>(sys, s0, nS, P, p0, nP,
+                                                                    C_total, cvalid, valid);
 }
 
 // ---------------------------------------------------------------------------
 // a3: deflection; a4: brightness
 
-// SIE with core (geometric-mean convention) in precision T.  c: packed
-// constants x0 y0 cos sin q^2 s^2 s q^2s e pref series e^2.
-template <typename T>
-__device__ __forceinline__ void sie_deflect(T x, T y, const T *c, T &ax, T &ay)
+// SIE with core (geometric-mean convention), FP64: constants as above.
+__device__ __forceinline__ void sie_deflect_f64(double x, double y, const double *c, double &ax,
+                                                double &ay)
 {
-    const T dx = x - c[0], dy = y - c[1];
-    const T u = dx * c[2] + dy * c[3];
-    const T v = dy * c[2] - dx * c[3];
-    const T psi = Math<T>::sqrt_(c[4] * (c[5] + u * u) + v * v);
-    const T zu = u / (psi + c[6]);
-    const T zv = v / (psi + c[7]);
-    T au, av;
-    if (c[10] != T(0)) {
+    const double dx = x - c[0], dy = y - c[1];
+    const double u = dx * c[2] + dy * c[3];
+    const double v = dy * c[2] - dx * c[3];
+    const double psi = sqrt(c[4] * (c[5] + u * u) + v * v);
+    const double zu = u / (psi + c[6]);
+    const double zv = v / (psi + c[7]);
+    double au, av;
+    if (c[10] != 0.0) {
         // atan(e z)/e and atanh(e z)/e to O(e^4)
-        const T e2 = c[11];
-        const T zu2 = zu * zu, zv2 = zv * zv;
-        au = c[9] * zu * (T(1) - e2 * zu2 * (T(1) / T(3)) + e2 * e2 * zu2 * zu2 * (T(1) / T(5)));
-        av = c[9] * zv * (T(1) + e2 * zv2 * (T(1) / T(3)) + e2 * e2 * zv2 * zv2 * (T(1) / T(5)));
+        const double e2 = c[11], zu2 = zu * zu, zv2 = zv * zv;
+        au = c[9] * zu * (1.0 - e2 * zu2 / 3.0 + e2 * e2 * zu2 * zu2 / 5.0);
+        av = c[9] * zv * (1.0 + e2 * zv2 / 3.0 + e2 * e2 * zv2 * zv2 / 5.0);
     } else {
-        au = c[9] * Math<T>::atan_(c[8] * zu);
-        av = c[9] * Math<T>::atanh_(c[8] * zv);
+        au = c[9] * atan(c[8] * zu);
+        av = c[9] * atanh(c[8] * zv);
     }
     ax += au * c[2] - av * c[3];
     ay += au * c[3] + av * c[2];
 }
 
-// Light profile in precision T.  c: x0 y0 cos sin q 1/q p2 lc|k A kind.
-template <typename T>
-__device__ __forceinline__ T light(T x, T y, const T *c)
+// The same in FP32 with compensated constants: every product with a
+// constant that carries a residual partner is a float pair multiply-add, so
+// the float rounding of the constant does not bias the deflection field.
+__device__ __forceinline__ void sie_deflect_f32(float x, float y, const float *c, float &ax,
+                                                float &ay)
 {
-    const T dx = x - c[0], dy = y - c[1];
-    const T u = dx * c[2] + dy * c[3];
-    const T v = dy * c[2] - dx * c[3];
-    const T R2 = c[4] * u * u + c[5] * v * v;
-    T t;
-    if (c[9] == T(kKindGauss)) t = c[7] * R2;
-    else t = Math<T>::exp2_(c[6] * Math<T>::log2_(R2) + c[7]);
-    return c[8] * Math<T>::exp2_(-t);
+    const float cs = c[2], sn = c[3], cs_l = c[17], sn_l = c[18];
+    const float dx = x - c[0], dy = y - c[1];
+    const float u = fmaf(dx, cs, fmaf(dy, sn, fmaf(dx, cs_l, dy * sn_l)));
+    const float v = fmaf(dy, cs, fmaf(-dx, sn, fmaf(dy, cs_l, -dx * sn_l)));
+    const float w = fmaf(u, u, c[5]);
+    const float psi = sqrtf(fmaf(c[4], w, fmaf(c[14], w, v * v)));
+    const float zu = u / (psi + c[6]);
+    const float zv = v / (psi + c[7]);
+    float A1, A2;
+    if (c[10] != 0.f) {
+        const float e2 = c[11], zu2 = zu * zu, zv2 = zv * zv;
+        A1 = zu * (1.f - e2 * zu2 * (1.f / 3.f) + e2 * e2 * zu2 * zu2 * 0.2f);
+        A2 = zv * (1.f + e2 * zv2 * (1.f / 3.f) + e2 * e2 * zv2 * zv2 * 0.2f);
+    } else {
+        A1 = atanf(fmaf(c[8], zu, c[15] * zu));
+        A2 = atanhf(fmaf(c[8], zv, c[15] * zv));
+    }
+    const float au = fmaf(c[9], A1, c[16] * A1);
+    const float av = fmaf(c[9], A2, c[16] * A2);
+    ax += fmaf(au, cs, fmaf(-av, sn, fmaf(au, cs_l, -av * sn_l)));
+    ay += fmaf(au, sn, fmaf(av, cs, fmaf(au, sn_l, av * cs_l)));
+}
+
+// Light profile, FP64.
+__device__ __forceinline__ double light_f64(double x, double y, const double *c)
+{
+    const double dx = x - c[0], dy = y - c[1];
+    const double u = dx * c[2] + dy * c[3];
+    const double v = dy * c[2] - dx * c[3];
+    const double rho2 = c[4] * u * u + c[5] * v * v;
+    const double t = (c[9] == (double)kKindGauss) ? c[7] * rho2
+                                                   : c[7] * exp2(c[6] * log2(rho2));
+    return c[8] * exp2(-t);
+}
+
+// Light profile, FP32 with compensated constants; MUFU lg2 / ex2.
+__device__ __forceinline__ float light_f32(float x, float y, const float *c)
+{
+    const float cs = c[2], sn = c[3], cs_l = c[11], sn_l = c[12];
+    const float dx = x - c[0], dy = y - c[1];
+    const float u = fmaf(dx, cs, fmaf(dy, sn, fmaf(dx, cs_l, dy * sn_l)));
+    const float v = fmaf(dy, cs, fmaf(-dx, sn, fmaf(dy, cs_l, -dx * sn_l)));
+    const float uu = u * u, vv = v * v;
+    const float rho2 = fmaf(c[4], uu, fmaf(c[5], vv, fmaf(c[14], uu, c[15] * vv)));
+    const float f = (c[9] == (float)kKindGauss) ? rho2 : ex2f(c[6] * lg2f(rho2));
+    const float t = fmaf(c[7], f, c[13] * f);
+    const float g = ex2f(-t);
+    return fmaf(c[8], g, c[10] * g);
 }
 
 // Total image-plane brightness at one ray (Eqs. 1-2).  MODE selects the
@@ -281,30 +350,30 @@ __device__ __forceinline__ float brightness_f32(float x, float y, const RayCtx &
         const int pl = R.plane[c];
         const float *cc = R.cf + c * kNC;
         if (pl == LENSED_PLANE_FOREGROUND) {
-            I += light<float>(x, y, cc);
+            I += light_f32(x, y, cc);
         } else if (pl == LENSED_PLANE_LENS) {
             const int t = R.type[c];
             if (t == LENSED_SIE) {
                 if (MODE == LENSED_PREC_MIXED) {
                     bool use64 = cc[12] != 0.f;
                     if (!use64) {
+                        // psi < 4 s, tested on squares: near the core
                         const float dx = x - cc[0], dy = y - cc[1];
                         const float u = dx * cc[2] + dy * cc[3];
                         const float v = dy * cc[2] - dx * cc[3];
-                        const float psi = sqrtf(cc[4] * (cc[5] + u * u) + v * v);
-                        use64 = psi < cc[13];
+                        use64 = cc[4] * (cc[5] + u * u) + v * v < cc[13] * cc[13];
                     }
                     if (use64) {
                         const double xd = ((double)j - cxd) * hd + ud;
                         const double yd = ((double)i - cyd) * hd + vd;
                         double dax = 0.0, day = 0.0;
-                        sie_deflect<double>(xd, yd, R.cd + c * kNC, dax, day);
+                        sie_deflect_f64(xd, yd, R.cd + c * kNC, dax, day);
                         ax += (float)dax;
                         ay += (float)day;
                         continue;
                     }
                 }
-                sie_deflect<float>(x, y, cc, ax, ay);
+                sie_deflect_f32(x, y, cc, ax, ay);
             } else if (t == LENSED_SHEAR) {
                 const float dx = x - cc[0], dy = y - cc[1];
                 ax += cc[2] * dx + cc[3] * dy;
@@ -320,7 +389,7 @@ __device__ __forceinline__ float brightness_f32(float x, float y, const RayCtx &
     }
     const float sx = x - ax, sy = y - ay;
     for (int c = 0; c < R.ncomp; ++c)
-        if (R.plane[c] == LENSED_PLANE_SOURCE) I += light<float>(sx, sy, R.cf + c * kNC);
+        if (R.plane[c] == LENSED_PLANE_SOURCE) I += light_f32(sx, sy, R.cf + c * kNC);
     return I;
 }
 
@@ -331,11 +400,11 @@ __device__ __forceinline__ double brightness_f64(double x, double y, const RayCt
         const int pl = R.plane[c];
         const double *cc = R.cd + c * kNC;
         if (pl == LENSED_PLANE_FOREGROUND) {
-            I += light<double>(x, y, cc);
+            I += light_f64(x, y, cc);
         } else if (pl == LENSED_PLANE_LENS) {
             const int t = R.type[c];
             if (t == LENSED_SIE) {
-                sie_deflect<double>(x, y, cc, ax, ay);
+                sie_deflect_f64(x, y, cc, ax, ay);
             } else if (t == LENSED_SHEAR) {
                 const double dx = x - cc[0], dy = y - cc[1];
                 ax += cc[2] * dx + cc[3] * dy;
@@ -351,7 +420,7 @@ __device__ __forceinline__ double brightness_f64(double x, double y, const RayCt
     }
     const double sx = x - ax, sy = y - ay;
     for (int c = 0; c < R.ncomp; ++c)
-        if (R.plane[c] == LENSED_PLANE_SOURCE) I += light<double>(sx, sy, R.cd + c * kNC);
+        if (R.plane[c] == LENSED_PLANE_SOURCE) I += light_f64(sx, sy, R.cd + c * kNC);
     return I;
 }
 
@@ -371,8 +440,10 @@ __global__ void __launch_bounds__(256)
     __shared__ __align__(16) float s_cf[LENSED_MAX_COMPONENTS * kNC];
     __shared__ __align__(16) double s_cd[(MODE == LENSED_PREC_FP32) ? 1 : LENSED_MAX_COMPONENTS * kNC];
     __shared__ int s_type[LENSED_MAX_COMPONENTS], s_plane[LENSED_MAX_COMPONENTS];
-    __shared__ float s_u[LENSED_MAX_RULE_ORDER], s_w[LENSED_MAX_RULE_ORDER];
-    __shared__ double s_ud[LENSED_MAX_RULE_ORDER], s_wd[LENSED_MAX_RULE_ORDER];
+    __shared__ float s_u[LENSED_MAX_RULE_ORDER];
+    __shared__ double s_ud[LENSED_MAX_RULE_ORDER];
+    __shared__ float s_w[LENSED_MAX_RULE_ORDER * LENSED_MAX_RULE_ORDER];
+    __shared__ double s_wd[(MODE == LENSED_PREC_FP64) ? LENSED_MAX_RULE_ORDER * LENSED_MAX_RULE_ORDER : 1];
 
     const TraceBlock tb = blocks[blockIdx.x];
     const int p = p0 + blockIdx.y;
@@ -390,9 +461,11 @@ __global__ void __launch_bounds__(256)
     }
     for (int k = threadIdx.x; k < nn; k += blockDim.x) {
         s_u[k] = node_u[S.node_off + k];
-        s_w[k] = node_w[S.node_off + k];
         s_ud[k] = node_ud[S.node_off + k];
-        s_wd[k] = node_wd[S.node_off + k];
+    }
+    for (int k = threadIdx.x; k < nn * nn; k += blockDim.x) {
+        if (MODE == LENSED_PREC_FP64) s_wd[k] = node_wd[S.w2_off + k];
+        else s_w[k] = node_w[S.w2_off + k];
     }
     __syncthreads();
 
@@ -417,23 +490,24 @@ __global__ void __launch_bounds__(256)
             double acc = 0.0;
             for (int b = 0; b < nn; ++b) {
                 const double y = yc + s_ud[b];
-                double row = 0.0;
-                for (int a = 0; a < nn; ++a) row += s_wd[a] * brightness_f64(xc + s_ud[a], y, R);
-                acc += s_wd[b] * row;
+                for (int a = 0; a < nn; ++a)
+                    acc += s_wd[b * nn + a] * brightness_f64(xc + s_ud[a], y, R);
             }
             ((double *)Lbuf)[lbase + pix] = acc;
         } else {
-            const float xc = ((float)j - S.cx) * S.h;
-            const float yc = ((float)i - S.cy) * S.h;
+            // pixel centre (j - cx) h with h as a float pair: one rounding,
+            // no coherent scale error
+            const float jc = (float)j - S.cx, ic = (float)i - S.cy;
+            const float xc = fmaf(jc, S.h, jc * S.h_lo);
+            const float yc = fmaf(ic, S.h, ic * S.h_lo);
             float acc = 0.f;
             for (int b = 0; b < nn; ++b) {
                 const float y = yc + s_u[b];
-                float row = 0.f;
                 for (int a = 0; a < nn; ++a)
-                    row += s_w[a] * brightness_f32<MODE>(xc + s_u[a], y, R, j, i, s_ud[a],
-                                                         s_ud[b], (double)S.cx, (double)S.cy,
-                                                         S.hd);
-                acc += s_w[b] * row;
+                    acc = fmaf(s_w[b * nn + a],
+                               brightness_f32<MODE>(xc + s_u[a], y, R, j, i, s_ud[a], s_ud[b],
+                                                    (double)S.cx, (double)S.cy, S.hd),
+                               acc);
             }
             ((float *)Lbuf)[lbase + pix] = acc;
         }

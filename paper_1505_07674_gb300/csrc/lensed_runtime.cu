@@ -236,7 +236,7 @@ struct lensed_model {
 
     // device tables
     DevBuf<SysDev> sys;
-    DevBuf<int> comp_type, comp_plane, comp_free;
+    DevBuf<int> comp_type, comp_plane, comp_free, comp_sys;
     DevBuf<double> comp_value;
     DevBuf<float> data, weight;
     DevBuf<double> data_d, weight_d;  // FP64 mode
@@ -267,14 +267,14 @@ struct lensed_model {
     int cap_P = 0;
     DevBuf<float> cf;
     DevBuf<double> cd;
-    DevBuf<unsigned char> valid;
+    DevBuf<unsigned char> valid, cvalid;
     DevBuf<double> partial;
     DevBuf<unsigned char> Lbuf;
     int chunk_P = 0;
     // render buffers (one point)
     DevBuf<float> rcf;
     DevBuf<double> rcd;
-    DevBuf<unsigned char> rvalid;
+    DevBuf<unsigned char> rvalid, rcvalid;
     DevBuf<unsigned char> rL;
     // host-API staging
     DevBuf<double> stage_params, stage_out;
@@ -340,6 +340,7 @@ int ensure_capacity(lensed_model *m, int P)
     if ((rc = m->cf.alloc((size_t)P * m->C_total * kNC))) return rc;
     if ((rc = m->cd.alloc((size_t)P * m->C_total * kNC))) return rc;
     if ((rc = m->valid.alloc((size_t)P * m->n_sys))) return rc;
+    if ((rc = m->cvalid.alloc((size_t)P * m->C_total))) return rc;
     if ((rc = m->partial.alloc((size_t)P * std::max(m->T_total, 1)))) return rc;
     const size_t per_point = (size_t)m->total_pix * m->elem();
     size_t chunk = std::max<size_t>(1, m->scratch_budget / std::max<size_t>(per_point, 1));
@@ -378,9 +379,9 @@ void enqueue_batch(lensed_model *m, const double *params, int P, double *out, La
                    cudaStream_t st, StageTimer *tm = nullptr)
 {
     if (tm) tm->begin(0);
-    launch_prologue(m->sys.p, 0, m->n_sys, m->comp_type.p, m->comp_free.p, m->comp_value.p,
-                    params, false, P, 0, P, m->n_par_max, m->C_total, m->cf.p, m->cd.p,
-                    m->valid.p, st);
+    launch_prologue(m->sys.p, m->comp_sys.p, 0, m->n_sys, 0, m->C_total, m->comp_type.p,
+                    m->comp_free.p, m->comp_value.p, params, false, P, 0, P, m->n_par_max,
+                    m->C_total, m->cf.p, m->cd.p, m->cvalid.p, m->valid.p, st);
     if (tm) tm->end();
     for (int p0 = 0; p0 < P; p0 += m->chunk_P) {
         const int nP = std::min(m->chunk_P, P - p0);
@@ -479,7 +480,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
 
     // ---- host tables
     std::vector<SysDev> sh(n_systems);
-    std::vector<int> ctype, cplane, cfree;
+    std::vector<int> ctype, cplane, cfree, csys;
     std::vector<double> cval;
     std::vector<float> data, weight, psf_f, node_u, node_w;
     std::vector<double> data_d, weight_d, psf_d, node_ud, node_wd;
@@ -499,6 +500,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         S.ny = ny;
         S.npix = npix;
         S.h = (float)d.pixel_scale;
+        S.h_lo = (float)(d.pixel_scale - (double)S.h);
         S.hd = d.pixel_scale;
         S.cx = 0.5f * (nx - 1);
         S.cy = 0.5f * (ny - 1);
@@ -544,12 +546,21 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
             }
             if (!(sum != 0.0) || !isfinite(sum))
                 return fail(LENSED_E_NONFINITE, "system %d: PSF sums to %g", s, sum);
+            // normalised, flipped; the float copy is adjusted at its largest tap
+            // so that it sums to one in exact arithmetic
+            const size_t f0 = psf_f.size();
+            size_t imax = f0;
             for (int kk = 0; kk <= 2 * P; ++kk)
                 for (int ll = 0; ll <= 2 * Q; ++ll) {
                     const double f = d.psf[(2 * P - kk) * d.psf_nx + (2 * Q - ll)] / sum;
                     psf_d.push_back(f);
                     psf_f.push_back((float)f);
+                    if (fabs(f) > fabs(psf_d[imax])) imax = psf_f.size() - 1;
                 }
+            double rest = 0.0;
+            for (size_t k = f0; k < psf_f.size(); ++k)
+                if (k != imax) rest += (double)psf_f[k];
+            psf_f[imax] = (float)(1.0 - rest);
         } else {
             psf_d.push_back(1.0);
             psf_f.push_back(1.f);
@@ -558,17 +569,35 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         S.psf_q = Q;
         pp[s] = P;
         qq[s] = Q;
-        // quadrature (Eq. 14): offsets t*h and weights
+        // quadrature (Eq. 14): 1-D offsets t*h, 2-D weights W_a W_b; the float
+        // weights are adjusted at the largest one so they sum to one in exact
+        // arithmetic, leaving no coherent scale error
         std::vector<double> t, wt;
         rule_nodes(d.rule, d.rule_order, t, wt);
-        S.nn = (int)t.size();
+        const int nn = (int)t.size();
+        S.nn = nn;
         S.node_off = (int)node_u.size();
-        nn_v[s] = S.nn;
-        for (size_t a = 0; a < t.size(); ++a) {
+        S.w2_off = (int)node_w.size();
+        nn_v[s] = nn;
+        for (int a = 0; a < nn; ++a) {
             node_ud.push_back(t[a] * d.pixel_scale);
-            node_wd.push_back(wt[a]);
             node_u.push_back((float)(t[a] * d.pixel_scale));
-            node_w.push_back((float)wt[a]);
+        }
+        {
+            std::vector<float> w2f(nn * nn);
+            int kmax = 0;
+            for (int b = 0; b < nn; ++b)
+                for (int a = 0; a < nn; ++a) {
+                    const double v = wt[a] * wt[b];
+                    node_wd.push_back(v);
+                    w2f[b * nn + a] = (float)v;
+                    if (v > wt[kmax % nn] * wt[kmax / nn]) kmax = b * nn + a;
+                }
+            double rest = 0.0;
+            for (int k = 0; k < nn * nn; ++k)
+                if (k != kmax) rest += (double)w2f[k];
+            w2f[kmax] = (float)(1.0 - rest);
+            node_w.insert(node_w.end(), w2f.begin(), w2f.end());
         }
         // needed pixels: every pixel an unmasked output reads through the
         // (clamped) PSF footprint
@@ -620,6 +649,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
             const lensed_component &cp = d.components[c];
             ctype.push_back(cp.type);
             cplane.push_back(cp.plane);
+            csys.push_back(s);
             const int np = nparams_of(cp.type);
             for (int k = 0; k < LENSED_MAX_COMPONENT_PARAMS; ++k) {
                 cfree.push_back(k < np ? cp.free_index[k] : -1);
@@ -683,7 +713,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
     int rc;
     init_kernel_attributes();
     if ((rc = m->sys.upload(sh)) || (rc = m->comp_type.upload(ctype)) ||
-        (rc = m->comp_plane.upload(cplane)) || (rc = m->comp_free.upload(cfree)) ||
+        (rc = m->comp_plane.upload(cplane)) || (rc = m->comp_free.upload(cfree)) || (rc = m->comp_sys.upload(csys)) ||
         (rc = m->comp_value.upload(cval)) || (rc = m->data.upload(data)) ||
         (rc = m->weight.upload(weight)) ||
         (rc = m->data_d.upload(precision == LENSED_PREC_FP64 ? data_d : std::vector<double>())) ||
@@ -700,7 +730,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
     }
     if ((rc = build_trace_tables(m, m->cfg().trace_threads * m->cfg().pix_per_thread)) ||
         (rc = m->rcf.alloc((size_t)C_total * kNC)) || (rc = m->rcd.alloc((size_t)C_total * kNC)) ||
-        (rc = m->rvalid.alloc(n_systems))) {
+        (rc = m->rvalid.alloc(n_systems)) || (rc = m->rcvalid.alloc((size_t)C_total))) {
         std::string msg = g_last_error;
         delete m;
         g_last_error = msg;
@@ -764,8 +794,9 @@ extern "C" int lensed_render(lensed_model *m, int system, const double *params, 
     cudaStream_t st = (cudaStream_t)stream;
     const SysDev &S = m->sys_h[system];
     // one point: consts at p = 0, valid at index system (P = 1)
-    launch_prologue(m->sys.p, system, 1, m->comp_type.p, m->comp_free.p, m->comp_value.p, params,
-                    true, 1, 0, 1, m->n_par_max, m->C_total, m->rcf.p, m->rcd.p, m->rvalid.p, st);
+    launch_prologue(m->sys.p, m->comp_sys.p, system, 1, S.comp_off, S.ncomp, m->comp_type.p,
+                    m->comp_free.p, m->comp_value.p, params, true, 1, 0, 1, m->n_par_max,
+                    m->C_total, m->rcf.p, m->rcd.p, m->rcvalid.p, m->rvalid.p, st);
     launch_trace(m->precision, m->cfg(), m->sys.p, m->comp_type.p, m->comp_plane.p, m->rcf.p,
                  m->rcd.p, m->rvalid.p, 1, m->C_total,
                  m->render_trace.p + m->render_trace_off[system], m->render_trace_cnt[system],
@@ -858,9 +889,10 @@ extern "C" int lensed_loglike_plain(lensed_model *m, const double *params, int P
     cudaStream_t st = (cudaStream_t)stream;
     for (int s = 0; s < m->n_sys; ++s) {
         for (int p = 0; p < P; ++p) {
-            launch_prologue(m->sys.p, s, 1, m->comp_type.p, m->comp_free.p, m->comp_value.p,
+            launch_prologue(m->sys.p, m->comp_sys.p, s, 1, m->sys_h[s].comp_off,
+                            m->sys_h[s].ncomp, m->comp_type.p, m->comp_free.p, m->comp_value.p,
                             params, false, P, p, 1, m->n_par_max, m->C_total, m->cf.p, m->cd.p,
-                            m->valid.p, st);
+                            m->cvalid.p, m->valid.p, st);
             launch_trace(m->precision, cfg, m->sys.p, m->comp_type.p, m->comp_plane.p, m->cf.p,
                          m->cd.p, m->valid.p, P, m->C_total,
                          m->trace_blocks.p + m->trace_sys_off[s], m->trace_sys_cnt[s], m->need.p,
@@ -950,7 +982,7 @@ extern "C" int lensed_batch_plan(lensed_model *m, int P, int *launches, int *chu
     int rc = ensure_capacity(m, P);
     if (rc) return rc;
     const int chunks = (P + m->chunk_P - 1) / m->chunk_P;
-    *launches = 2 + chunks * (1 + (int)m->psf_groups.size());
+    *launches = 3 + chunks * (1 + (int)m->psf_groups.size());
     *chunk_points = m->chunk_P;
     return LENSED_OK;
 }
