@@ -36,6 +36,7 @@
  *   - external shear alpha = (g1 dx + g2 dy, g2 dx - g1 dy), g1 = g cos 2phi,
  *     g2 = g sin 2phi, about its centre;
  *   - point mass alpha = thetaE^2 d / |d|^2, and alpha = 0 exactly at d = 0;
+ *     likewise alpha = 0 exactly at the centre of a coreless SIE (s = 0);
  *   - Sersic b_n solves P(2n, b_n) = 1/2 exactly (regularised lower
  *     incomplete gamma); total flux F = 10^(-0.4 (mag - zp)) gives
  *     I_0 = F b_n^(2n) / (2 pi n r^2 Gamma(2n)); de Vaucouleurs is n = 4;
@@ -287,6 +288,7 @@ void ora_deflection_one(int type, const double *p, double x, double y,
         double v = -dx * sn + dy * c;
         double e = sqrt((1.0 - q) * (1.0 + q));
         double psi = sqrt(q * q * (s * s + u * u) + v * v);
+        if (psi + s == 0.0) return; /* exact centre of a coreless SIE: alpha = 0 */
         double zu = u / (psi + s), zv = v / (psi + q * q * s);
         double au, av;
         if (e < 1e-3) {

@@ -75,8 +75,7 @@ struct PsfBlock {
 };
 
 struct LaunchCfg {
-    int trace_threads;   // 128 or 256
-    int pix_per_thread;  // 1 or 2
+    int trace_threads;  // threads per trace block, one pixel each
 };
 
 // --- kernels launched from the runtime (defined in lensed_kernels.cu) ---
@@ -92,8 +91,9 @@ void launch_prologue(const SysDev *sys, const int *comp_sys, int s0, int nS, int
                      unsigned char *valid, cudaStream_t st);
 
 // a2-a5: pixel luminosities of the pixels in the block table, for points
-// p0 .. p0 + nP - 1, into Lbuf[(p - p0) * L_stride + pix_off + pix].
-void launch_trace(int precision, LaunchCfg cfg, const SysDev *sys, const int *comp_type,
+// p0 .. p0 + nP - 1, into Lbuf[(p - p0) * L_stride + pix_off + pix].  Every
+// system in the table has nn nodes per row of its rule.
+void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const int *comp_type,
                   const int *comp_plane, const float *cf, const double *cd,
                   const unsigned char *valid, int P, int C_total, const TraceBlock *blocks,
                   int n_blocks, const int *need, NodeTables nodes, int p0, int nP, void *Lbuf,

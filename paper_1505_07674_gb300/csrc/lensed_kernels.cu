@@ -120,9 +120,11 @@ __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__res
     o[0] = v[0];
     o[1] = v[1];
     if (type == LENSED_SIE) {
-        // 0 x0, 1 y0, 2 cos, 3 sin, 4 q^2, 5 s^2, 6 s, 7 q^2 s, 8 e, 9 pref,
-        // 10 series flag, 11 e^2, 12 FP64 flag (MIXED), 13 4s;
-        // residuals: 14 q^2, 15 e, 16 pref, 17 cos, 18 sin
+        // 0 x0, 1 y0, 2 cos, 3 sin, 4 cos_lo, 5 sin_lo, 6 q^2, 7 q^2_lo,
+        // 8 s^2, 9 s, 10 q^2 s, 11 e, 12 e_lo, 13 pref, 14 pref_lo,
+        // 15 series flag, 16 e^2, 17 FP64 flag (MIXED, e < 0.05),
+        // 18 (4 s / q + h / sqrt 2)^2: pixels whose centre lies inside this
+        // radius of the lens centre take the FP64 branch in MIXED
         const double b = v[2], q = v[3], sc = v[5];
         ok = ok && q > 0.0 && q <= 1.0 && b >= 0.0 && sc >= 0.0;
         double sn, cs;
@@ -131,37 +133,40 @@ __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__res
         const bool series = e < kSeriesE;
         o[2] = cs;
         o[3] = sn;
-        o[4] = q * q;
-        o[5] = sc * sc;
-        o[6] = sc;
-        o[7] = q * q * sc;
-        o[8] = e;
-        o[9] = series ? b * sqrt(q) : b * sqrt(q) / e;
-        o[10] = series ? 1.0 : 0.0;
-        o[11] = e * e;
-        o[12] = e < kMixedRoundE ? 1.0 : 0.0;
-        o[13] = kMixedCoreFactor * sc;
-        lo[4] = 14;
-        lo[8] = 15;
-        lo[9] = 16;
-        lo[2] = 17;
-        lo[3] = 18;
+        o[6] = q * q;
+        o[8] = sc * sc;
+        o[9] = sc;
+        o[10] = q * q * sc;
+        o[11] = e;
+        o[13] = series ? b * sqrt(q) : b * sqrt(q) / e;
+        o[15] = series ? 1.0 : 0.0;
+        o[16] = e * e;
+        o[17] = e < kMixedRoundE ? 1.0 : 0.0;
+        const double rc = ok ? kMixedCoreFactor * sc / q + 0.7071067811865476 * hd : 0.0;
+        o[18] = rc * rc;
+        lo[2] = 4;
+        lo[3] = 5;
+        lo[6] = 7;
+        lo[11] = 12;
+        lo[13] = 14;
     } else if (type == LENSED_SHEAR) {
+        // 0 x0, 1 y0, 2 gamma_1, 3 gamma_2
         double sn, cs;
         sincospi(v[3] / 90.0, &sn, &cs);  // 2 phi
         o[2] = v[2] * cs;
         o[3] = v[2] * sn;
     } else if (type == LENSED_POINTMASS) {
+        // 0 x0, 1 y0, 2 theta_E^2
         ok = ok && v[2] >= 0.0;
         o[2] = v[2] * v[2];
     } else {
         // light: Sersic (x y r mag n q pa), de Vaucouleurs (x y r mag q pa),
         // Gaussian (x y sigma mag q pa).
-        // 0 x0, 1 y0, 2 cos, 3 sin, 4 q/r^2, 5 1/(q r^2), 6 p2, 7 B, 8 A,
-        // 9 kind; residuals: 10 A, 11 cos, 12 sin, 13 B, 14 q/r^2, 15 1/(q r^2).
-        // rho^2 = (q u^2 + v^2/q)/r^2; Sersic t = B rho^(2 p2) with B = b_n
-        // log2(e), p2 = 1/(2n); Gaussian (r = sqrt(2) sigma) t = B rho^2 with
-        // B = log2(e); I = A 2^-t with A = I_0 h^2.
+        // 0 x0, 1 y0, 2 cos, 3 sin, 4 cos_lo, 5 sin_lo, 6 q/r^2, 7 1/(q r^2),
+        // 8 q/r^2 lo, 9 1/(q r^2) lo, 10 p2, 11 B, 12 B_lo, 13 A, 14 A_lo,
+        // 15 kind.  rho^2 = (q u^2 + v^2/q)/r^2; Sersic t = B rho^(2 p2) with
+        // B = b_n log2(e), p2 = 1/(2n); Gaussian (r = sqrt(2) sigma) t =
+        // B rho^2 with B = log2(e); I = A 2^-t with A = I_0 h^2.
         const double r = v[2];
         const double F = pow(10.0, -0.4 * (v[3] - zeropoint));
         double n = 4.0, q, pa;
@@ -172,31 +177,31 @@ __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__res
         sincospi(pa / 180.0, &sn, &cs);
         o[2] = cs;
         o[3] = sn;
-        lo[8] = 10;
-        lo[2] = 11;
-        lo[3] = 12;
-        lo[7] = 13;
-        lo[4] = 14;
-        lo[5] = 15;
+        lo[2] = 4;
+        lo[3] = 5;
+        lo[6] = 8;
+        lo[7] = 9;
+        lo[11] = 12;
+        lo[13] = 14;
         if (ok && type == LENSED_GAUSS) {
             const double r2 = 2.0 * r * r;
-            o[4] = q / r2;
-            o[5] = 1.0 / (q * r2);
-            o[6] = 1.0;
-            o[7] = 1.4426950408889634;  // log2(e)
-            o[8] = F / (M_PI * r2) * hd * hd;
-            o[9] = kKindGauss;
+            o[6] = q / r2;
+            o[7] = 1.0 / (q * r2);
+            o[10] = 1.0;
+            o[11] = 1.4426950408889634;  // log2(e)
+            o[13] = F / (M_PI * r2) * hd * hd;
+            o[15] = kKindGauss;
         } else if (ok) {
             const double bn = sersic_b(n);
             // I_0 = F b^(2n) / (2 pi n r^2 Gamma(2n)), in logs
             const double lI0 = log(F) + 2.0 * n * log(bn) - log(2.0 * M_PI * n * r * r) -
                                lgamma(2.0 * n);
-            o[4] = q / (r * r);
-            o[5] = 1.0 / (q * r * r);
-            o[6] = 0.5 / n;
-            o[7] = bn * 1.4426950408889634;
-            o[8] = exp(lI0) * hd * hd;
-            o[9] = kKindPower;
+            o[6] = q / (r * r);
+            o[7] = 1.0 / (q * r * r);
+            o[10] = 0.5 / n;
+            o[11] = bn * 1.4426950408889634;
+            o[13] = exp(lI0) * hd * hd;
+            o[15] = kKindPower;
         }
     }
     const size_t base = ((size_t)p * C_total + gc) * kNC;
@@ -248,150 +253,147 @@ void launch_prologue(const SysDev *sys, const int *comp_sys, int s0, int nS, int
 // ---------------------------------------------------------------------------
 // a3: deflection; a4: brightness
 
-// SIE with core (geometric-mean convention), FP64: constants as above.
+// SIE with core (geometric-mean convention) in FP64 (constants as packed by
+// the prologue; residual slots are zero in the FP64 copy).  A ray exactly at
+// the centre of a coreless SIE gets no deflection.
 __device__ __forceinline__ void sie_deflect_f64(double x, double y, const double *c, double &ax,
                                                 double &ay)
 {
     const double dx = x - c[0], dy = y - c[1];
     const double u = dx * c[2] + dy * c[3];
     const double v = dy * c[2] - dx * c[3];
-    const double psi = sqrt(c[4] * (c[5] + u * u) + v * v);
-    const double zu = u / (psi + c[6]);
-    const double zv = v / (psi + c[7]);
+    const double psi = sqrt(c[6] * (c[8] + u * u) + v * v);
+    const double du = psi + c[9], dv = psi + c[10];
+    if (!(du > 0.0)) return;
+    const double zu = u / du;
+    const double zv = v / dv;
     double au, av;
-    if (c[10] != 0.0) {
+    if (c[15] != 0.0) {
         // atan(e z)/e and atanh(e z)/e to O(e^4)
-        const double e2 = c[11], zu2 = zu * zu, zv2 = zv * zv;
-        au = c[9] * zu * (1.0 - e2 * zu2 / 3.0 + e2 * e2 * zu2 * zu2 / 5.0);
-        av = c[9] * zv * (1.0 + e2 * zv2 / 3.0 + e2 * e2 * zv2 * zv2 / 5.0);
+        const double e2 = c[16], zu2 = zu * zu, zv2 = zv * zv;
+        au = c[13] * zu * (1.0 - e2 * zu2 / 3.0 + e2 * e2 * zu2 * zu2 / 5.0);
+        av = c[13] * zv * (1.0 + e2 * zv2 / 3.0 + e2 * e2 * zv2 * zv2 / 5.0);
     } else {
-        au = c[9] * atan(c[8] * zu);
-        av = c[9] * atanh(c[8] * zv);
+        au = c[13] * atan(c[11] * zu);
+        av = c[13] * atanh(c[11] * zv);
     }
     ax += au * c[2] - av * c[3];
     ay += au * c[3] + av * c[2];
 }
 
-// The same in FP32 with compensated constants: every product with a
-// constant that carries a residual partner is a float pair multiply-add, so
-// the float rounding of the constant does not bias the deflection field.
-__device__ __forceinline__ void sie_deflect_f32(float x, float y, const float *c, float &ax,
-                                                float &ay)
-{
-    const float cs = c[2], sn = c[3], cs_l = c[17], sn_l = c[18];
-    const float dx = x - c[0], dy = y - c[1];
-    const float u = fmaf(dx, cs, fmaf(dy, sn, fmaf(dx, cs_l, dy * sn_l)));
-    const float v = fmaf(dy, cs, fmaf(-dx, sn, fmaf(dy, cs_l, -dx * sn_l)));
-    const float w = fmaf(u, u, c[5]);
-    const float psi = sqrtf(fmaf(c[4], w, fmaf(c[14], w, v * v)));
-    const float zu = u / (psi + c[6]);
-    const float zv = v / (psi + c[7]);
-    float A1, A2;
-    if (c[10] != 0.f) {
-        const float e2 = c[11], zu2 = zu * zu, zv2 = zv * zv;
-        A1 = zu * (1.f - e2 * zu2 * (1.f / 3.f) + e2 * e2 * zu2 * zu2 * 0.2f);
-        A2 = zv * (1.f + e2 * zv2 * (1.f / 3.f) + e2 * e2 * zv2 * zv2 * 0.2f);
-    } else {
-        A1 = atanf(fmaf(c[8], zu, c[15] * zu));
-        A2 = atanhf(fmaf(c[8], zv, c[15] * zv));
-    }
-    const float au = fmaf(c[9], A1, c[16] * A1);
-    const float av = fmaf(c[9], A2, c[16] * A2);
-    ax += fmaf(au, cs, fmaf(-av, sn, fmaf(au, cs_l, -av * sn_l)));
-    ay += fmaf(au, sn, fmaf(av, cs, fmaf(au, sn_l, av * cs_l)));
-}
-
-// Light profile, FP64.
+// Light profile in FP64.
 __device__ __forceinline__ double light_f64(double x, double y, const double *c)
 {
     const double dx = x - c[0], dy = y - c[1];
     const double u = dx * c[2] + dy * c[3];
     const double v = dy * c[2] - dx * c[3];
-    const double rho2 = c[4] * u * u + c[5] * v * v;
-    const double t = (c[9] == (double)kKindGauss) ? c[7] * rho2
-                                                   : c[7] * exp2(c[6] * log2(rho2));
-    return c[8] * exp2(-t);
+    const double rho2 = c[6] * u * u + c[7] * v * v;
+    const double t = (c[15] == (double)kKindGauss) ? c[11] * rho2
+                                                    : c[11] * exp2(c[10] * log2(rho2));
+    return c[13] * exp2(-t);
 }
 
-// Light profile, FP32 with compensated constants; MUFU lg2 / ex2.
-__device__ __forceinline__ float light_f32(float x, float y, const float *c)
+// FP32 constants of one component held in registers for a row of rays.
+struct SieF {
+    float x0, y0, cs, sn, csl, snl, q2, q2l, s2, s, q2s, e, el, pref, prefl, series, e2;
+};
+struct LightF {
+    float x0, y0, cs, sn, csl, snl, qr, iqr, qrl, iqrl, p2, B, Bl, A, Al, kind;
+};
+
+__device__ __forceinline__ SieF load_sie(const float *c)
 {
-    const float cs = c[2], sn = c[3], cs_l = c[11], sn_l = c[12];
-    const float dx = x - c[0], dy = y - c[1];
-    const float u = fmaf(dx, cs, fmaf(dy, sn, fmaf(dx, cs_l, dy * sn_l)));
-    const float v = fmaf(dy, cs, fmaf(-dx, sn, fmaf(dy, cs_l, -dx * sn_l)));
-    const float uu = u * u, vv = v * v;
-    const float rho2 = fmaf(c[4], uu, fmaf(c[5], vv, fmaf(c[14], uu, c[15] * vv)));
-    const float f = (c[9] == (float)kKindGauss) ? rho2 : ex2f(c[6] * lg2f(rho2));
-    const float t = fmaf(c[7], f, c[13] * f);
-    const float g = ex2f(-t);
-    return fmaf(c[8], g, c[10] * g);
+    const float4 a = reinterpret_cast<const float4 *>(c)[0];
+    const float4 b = reinterpret_cast<const float4 *>(c)[1];
+    const float4 d = reinterpret_cast<const float4 *>(c)[2];
+    const float4 f = reinterpret_cast<const float4 *>(c)[3];
+    SieF k;
+    k.x0 = a.x; k.y0 = a.y; k.cs = a.z; k.sn = a.w;
+    k.csl = b.x; k.snl = b.y; k.q2 = b.z; k.q2l = b.w;
+    k.s2 = d.x; k.s = d.y; k.q2s = d.z; k.e = d.w;
+    k.el = f.x; k.pref = f.y; k.prefl = f.z; k.series = f.w;
+    k.e2 = c[16];
+    return k;
 }
 
-// Total image-plane brightness at one ray (Eqs. 1-2).  MODE selects the
-// precision; in MIXED the SIE switches to FP64 near q = 1 and near its core,
-// with the FP64 ray position rebuilt from the pixel and node indices.
+__device__ __forceinline__ LightF load_light(const float *c)
+{
+    const float4 a = reinterpret_cast<const float4 *>(c)[0];
+    const float4 b = reinterpret_cast<const float4 *>(c)[1];
+    const float4 d = reinterpret_cast<const float4 *>(c)[2];
+    const float4 f = reinterpret_cast<const float4 *>(c)[3];
+    LightF k;
+    k.x0 = a.x; k.y0 = a.y; k.cs = a.z; k.sn = a.w;
+    k.csl = b.x; k.snl = b.y; k.qr = b.z; k.iqr = b.w;
+    k.qrl = d.x; k.iqrl = d.y; k.p2 = d.z; k.B = d.w;
+    k.Bl = f.x; k.A = f.y; k.Al = f.z; k.kind = f.w;
+    return k;
+}
+
+// SIE in FP32 with compensated constants: every product with a constant
+// that carries a residual partner is a float-pair multiply-add, so the
+// float rounding of the constants does not bias the deflection field.
+// Quotients and the square root use the fast forms (a few ulp, random in
+// sign from ray to ray).
+__device__ __forceinline__ void sie_f32(const SieF &k, float x, float y, float &ax, float &ay)
+{
+    const float dx = x - k.x0, dy = y - k.y0;
+    const float u = fmaf(dx, k.cs, fmaf(dy, k.sn, fmaf(dx, k.csl, dy * k.snl)));
+    const float v = fmaf(dy, k.cs, fmaf(-dx, k.sn, fmaf(dy, k.csl, -dx * k.snl)));
+    const float w = fmaf(u, u, k.s2);
+    const float psi2 = fmaf(k.q2, w, fmaf(k.q2l, w, v * v));
+    const float psi = psi2 > 0.f ? psi2 * rsqrtf(psi2) : 0.f;
+    const float du = psi + k.s, dv = psi + k.q2s;
+    const float zu = du > 0.f ? __fdividef(u, du) : 0.f;
+    const float zv = du > 0.f ? __fdividef(v, dv) : 0.f;
+    float A1, A2;
+    if (k.series != 0.f) {
+        const float zu2 = zu * zu, zv2 = zv * zv;
+        A1 = zu * (1.f - k.e2 * zu2 * (1.f / 3.f) + k.e2 * k.e2 * zu2 * zu2 * 0.2f);
+        A2 = zv * (1.f + k.e2 * zv2 * (1.f / 3.f) + k.e2 * k.e2 * zv2 * zv2 * 0.2f);
+    } else {
+        A1 = atanf(fmaf(k.e, zu, k.el * zu));
+        A2 = atanhf(fmaf(k.e, zv, k.el * zv));
+    }
+    const float au = fmaf(k.pref, A1, k.prefl * A1);
+    const float av = fmaf(k.pref, A2, k.prefl * A2);
+    ax += fmaf(au, k.cs, fmaf(-av, k.sn, fmaf(au, k.csl, -av * k.snl)));
+    ay += fmaf(au, k.sn, fmaf(av, k.cs, fmaf(au, k.snl, av * k.csl)));
+}
+
+// Light profile in FP32 with compensated constants; MUFU lg2 / ex2.
+__device__ __forceinline__ float light_f32(const LightF &k, float x, float y)
+{
+    const float dx = x - k.x0, dy = y - k.y0;
+    const float u = fmaf(dx, k.cs, fmaf(dy, k.sn, fmaf(dx, k.csl, dy * k.snl)));
+    const float v = fmaf(dy, k.cs, fmaf(-dx, k.sn, fmaf(dy, k.csl, -dx * k.snl)));
+    const float uu = u * u, vv = v * v;
+    const float rho2 = fmaf(k.qr, uu, fmaf(k.iqr, vv, fmaf(k.qrl, uu, k.iqrl * vv)));
+    const float f = (k.kind == (float)kKindGauss) ? rho2 : ex2f(k.p2 * lg2f(rho2));
+    const float t = fmaf(k.B, f, k.Bl * f);
+    const float g = ex2f(-t);
+    return fmaf(k.A, g, k.Al * g);
+}
+
+// FP64 SIE of one ray in a MIXED evaluation.  Out of line, so that none of
+// its double-precision arithmetic is scheduled on the FP32 path; the ray
+// position is rebuilt in FP64 from the pixel index and the FP64 node offsets.
+__device__ __noinline__ void sie_ray_f64(float jc, float ic, double hd, double ua, double vb,
+                                         const double *c, float &ax, float &ay)
+{
+    double dax = 0.0, day = 0.0;
+    sie_deflect_f64((double)jc * hd + ua, (double)ic * hd + vb, c, dax, day);
+    ax += (float)dax;
+    ay += (float)day;
+}
+
+// Total image-plane brightness at one ray in FP64 (Eqs. 1-2).
 struct RayCtx {
     int ncomp;
     const int *type;
     const int *plane;
-    const float *cf;
     const double *cd;
-    double xd, yd;  // FP64 ray position (MIXED branch only; filled lazily)
 };
-
-template <int MODE>
-__device__ __forceinline__ float brightness_f32(float x, float y, const RayCtx &R, int j, int i,
-                                                double ud, double vd, double cxd, double cyd,
-                                                double hd)
-{
-    float I = 0.f, ax = 0.f, ay = 0.f;
-    for (int c = 0; c < R.ncomp; ++c) {
-        const int pl = R.plane[c];
-        const float *cc = R.cf + c * kNC;
-        if (pl == LENSED_PLANE_FOREGROUND) {
-            I += light_f32(x, y, cc);
-        } else if (pl == LENSED_PLANE_LENS) {
-            const int t = R.type[c];
-            if (t == LENSED_SIE) {
-                if (MODE == LENSED_PREC_MIXED) {
-                    bool use64 = cc[12] != 0.f;
-                    if (!use64) {
-                        // psi < 4 s, tested on squares: near the core
-                        const float dx = x - cc[0], dy = y - cc[1];
-                        const float u = dx * cc[2] + dy * cc[3];
-                        const float v = dy * cc[2] - dx * cc[3];
-                        use64 = cc[4] * (cc[5] + u * u) + v * v < cc[13] * cc[13];
-                    }
-                    if (use64) {
-                        const double xd = ((double)j - cxd) * hd + ud;
-                        const double yd = ((double)i - cyd) * hd + vd;
-                        double dax = 0.0, day = 0.0;
-                        sie_deflect_f64(xd, yd, R.cd + c * kNC, dax, day);
-                        ax += (float)dax;
-                        ay += (float)day;
-                        continue;
-                    }
-                }
-                sie_deflect_f32(x, y, cc, ax, ay);
-            } else if (t == LENSED_SHEAR) {
-                const float dx = x - cc[0], dy = y - cc[1];
-                ax += cc[2] * dx + cc[3] * dy;
-                ay += cc[3] * dx - cc[2] * dy;
-            } else {  // point mass
-                const float dx = x - cc[0], dy = y - cc[1];
-                const float r2 = dx * dx + dy * dy;
-                const float f = r2 > 0.f ? cc[2] / r2 : 0.f;
-                ax += f * dx;
-                ay += f * dy;
-            }
-        }
-    }
-    const float sx = x - ax, sy = y - ay;
-    for (int c = 0; c < R.ncomp; ++c)
-        if (R.plane[c] == LENSED_PLANE_SOURCE) I += light_f32(sx, sy, R.cf + c * kNC);
-    return I;
-}
 
 __device__ __forceinline__ double brightness_f64(double x, double y, const RayCtx &R)
 {
@@ -427,127 +429,244 @@ __device__ __forceinline__ double brightness_f64(double x, double y, const RayCt
 // ---------------------------------------------------------------------------
 // a2-a5: ray tracing and pixel integration
 
-template <int MODE, int PPT>
-__global__ void __launch_bounds__(256)
-    k_trace(const SysDev *__restrict__ sys, const int *__restrict__ comp_type,
-            const int *__restrict__ comp_plane, const float *__restrict__ cf,
-            const double *__restrict__ cd, const unsigned char *__restrict__ valid, int P,
-            int C_total, const TraceBlock *__restrict__ blocks, const int *__restrict__ need,
-            const float *__restrict__ node_u, const float *__restrict__ node_w,
-            const double *__restrict__ node_ud, const double *__restrict__ node_wd, int p0,
-            void *__restrict__ Lbuf, long long L_stride)
-{
-    __shared__ __align__(16) float s_cf[LENSED_MAX_COMPONENTS * kNC];
-    __shared__ __align__(16) double s_cd[(MODE == LENSED_PREC_FP32) ? 1 : LENSED_MAX_COMPONENTS * kNC];
-    __shared__ int s_type[LENSED_MAX_COMPONENTS], s_plane[LENSED_MAX_COMPONENTS];
-    __shared__ float s_u[LENSED_MAX_RULE_ORDER];
-    __shared__ double s_ud[LENSED_MAX_RULE_ORDER];
-    __shared__ float s_w[LENSED_MAX_RULE_ORDER * LENSED_MAX_RULE_ORDER];
-    __shared__ double s_wd[(MODE == LENSED_PREC_FP64) ? LENSED_MAX_RULE_ORDER * LENSED_MAX_RULE_ORDER : 1];
+// Shared-memory staging common to the trace kernels: the point's packed
+// constants, component types and planes, node offsets and 2-D weights.
+struct TraceSmem {
+    float cf[LENSED_MAX_COMPONENTS * kNC];
+    double cd[LENSED_MAX_COMPONENTS * kNC];
+    int type[LENSED_MAX_COMPONENTS], plane[LENSED_MAX_COMPONENTS];
+    float u[LENSED_MAX_RULE_ORDER];
+    double ud[LENSED_MAX_RULE_ORDER];
+    float w[LENSED_MAX_RULE_ORDER * LENSED_MAX_RULE_ORDER];
+    double wd[LENSED_MAX_RULE_ORDER * LENSED_MAX_RULE_ORDER];
+};
 
+__device__ __forceinline__ void stage_point(TraceSmem &sm, const SysDev &S, const int *comp_type,
+                                            const int *comp_plane, const float *cf,
+                                            const double *cd, size_t cbase, bool need_f64,
+                                            bool w_f64, const NodeTables &nodes)
+{
+    const int ncomp = S.ncomp, nn = S.nn;
+    for (int k = threadIdx.x; k < ncomp * kNC; k += blockDim.x) {
+        sm.cf[k] = cf[cbase + k];
+        if (need_f64) sm.cd[k] = cd[cbase + k];
+    }
+    for (int k = threadIdx.x; k < ncomp; k += blockDim.x) {
+        sm.type[k] = comp_type[S.comp_off + k];
+        sm.plane[k] = comp_plane[S.comp_off + k];
+    }
+    for (int k = threadIdx.x; k < nn; k += blockDim.x) {
+        sm.u[k] = nodes.u[S.node_off + k];
+        sm.ud[k] = nodes.ud[S.node_off + k];
+    }
+    for (int k = threadIdx.x; k < nn * nn; k += blockDim.x) {
+        if (w_f64) sm.wd[k] = nodes.wd[S.w2_off + k];
+        else sm.w[k] = nodes.w[S.w2_off + k];
+    }
+}
+
+// a2-a5 in FP32 / MIXED: one thread per pixel; for every row of the rule's
+// node grid, G rays are traced together component by component, so each
+// component's constants are read into registers once per G rays and the G
+// independent rays give the scheduler instruction-level parallelism.
+// EXACT: the rule has exactly G nodes per row (no guards).
+template <int MODE, int G, bool EXACT>
+__global__ void __launch_bounds__(256)
+    k_trace_rows(const SysDev *__restrict__ sys, const int *__restrict__ comp_type,
+                 const int *__restrict__ comp_plane, const float *__restrict__ cf,
+                 const double *__restrict__ cd, const unsigned char *__restrict__ valid, int P,
+                 int C_total, const TraceBlock *__restrict__ blocks, const int *__restrict__ need,
+                 NodeTables nodes, int p0, float *__restrict__ Lbuf, long long L_stride)
+{
+    __shared__ __align__(16) TraceSmem sm;
     const TraceBlock tb = blocks[blockIdx.x];
     const int p = p0 + blockIdx.y;
     if (!valid[(size_t)tb.sys * P + p]) return;
     const SysDev &S = sys[tb.sys];
-    const int ncomp = S.ncomp, nn = S.nn;
     const size_t cbase = ((size_t)p * C_total + S.comp_off) * kNC;
-    for (int k = threadIdx.x; k < ncomp * kNC; k += blockDim.x) {
-        s_cf[k] = cf[cbase + k];
-        if (MODE != LENSED_PREC_FP32) s_cd[k] = cd[cbase + k];
-    }
-    for (int k = threadIdx.x; k < ncomp; k += blockDim.x) {
-        s_type[k] = comp_type[S.comp_off + k];
-        s_plane[k] = comp_plane[S.comp_off + k];
-    }
-    for (int k = threadIdx.x; k < nn; k += blockDim.x) {
-        s_u[k] = node_u[S.node_off + k];
-        s_ud[k] = node_ud[S.node_off + k];
-    }
-    for (int k = threadIdx.x; k < nn * nn; k += blockDim.x) {
-        if (MODE == LENSED_PREC_FP64) s_wd[k] = node_wd[S.w2_off + k];
-        else s_w[k] = node_w[S.w2_off + k];
-    }
+    stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, MODE == LENSED_PREC_MIXED, false,
+                nodes);
     __syncthreads();
 
-    RayCtx R;
-    R.ncomp = ncomp;
-    R.type = s_type;
-    R.plane = s_plane;
-    R.cf = s_cf;
-    R.cd = s_cd;
+    const int idx = tb.start + threadIdx.x;
+    if (idx >= tb.end) return;
+    const int ncomp = S.ncomp;
+    const int nn = EXACT ? G : S.nn;
     const int nx = S.nx;
-    const size_t lbase = (size_t)(p - p0) * L_stride + S.pix_off;
+    const int pix = need ? need[S.need_off + idx] : idx;
+    const int i = pix / nx, j = pix - (pix / nx) * nx;
+    // pixel centre (j - cx) h with h as a float pair: one rounding, no
+    // coherent scale error
+    const float jc = (float)j - S.cx, ic = (float)i - S.cy;
+    const float xc = fmaf(jc, S.h, jc * S.h_lo);
+    const float yc = fmaf(ic, S.h, ic * S.h_lo);
 
+    float acc = 0.f;
+    for (int b = 0; b < nn; ++b) {
+        const float y = yc + sm.u[b];
+        for (int a0 = 0; a0 < nn; a0 += G) {
+            float xk[G], ax[G], ay[G], I[G];
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-        const int idx = tb.start + threadIdx.x + k * blockDim.x;
-        if (idx >= tb.end) break;
-        const int pix = need ? need[S.need_off + idx] : idx;
-        const int i = pix / nx, j = pix - (pix / nx) * nx;
-        if (MODE == LENSED_PREC_FP64) {
-            const double xc = ((double)j - (double)S.cx) * S.hd;
-            const double yc = ((double)i - (double)S.cy) * S.hd;
-            double acc = 0.0;
-            for (int b = 0; b < nn; ++b) {
-                const double y = yc + s_ud[b];
-                for (int a = 0; a < nn; ++a)
-                    acc += s_wd[b * nn + a] * brightness_f64(xc + s_ud[a], y, R);
+            for (int k = 0; k < G; ++k) {
+                const int a = EXACT ? k : min(a0 + k, nn - 1);
+                xk[k] = xc + sm.u[a];
+                ax[k] = 0.f;
+                ay[k] = 0.f;
+                I[k] = 0.f;
             }
-            ((double *)Lbuf)[lbase + pix] = acc;
-        } else {
-            // pixel centre (j - cx) h with h as a float pair: one rounding,
-            // no coherent scale error
-            const float jc = (float)j - S.cx, ic = (float)i - S.cy;
-            const float xc = fmaf(jc, S.h, jc * S.h_lo);
-            const float yc = fmaf(ic, S.h, ic * S.h_lo);
-            float acc = 0.f;
-            for (int b = 0; b < nn; ++b) {
-                const float y = yc + s_u[b];
-                for (int a = 0; a < nn; ++a)
-                    acc = fmaf(s_w[b * nn + a],
-                               brightness_f32<MODE>(xc + s_u[a], y, R, j, i, s_ud[a], s_ud[b],
-                                                    (double)S.cx, (double)S.cy, S.hd),
-                               acc);
+            for (int c = 0; c < ncomp; ++c) {
+                const int pl = sm.plane[c];
+                const float *cc = sm.cf + c * kNC;
+                if (pl == LENSED_PLANE_FOREGROUND) {
+                    const LightF L = load_light(cc);
+#pragma unroll
+                    for (int k = 0; k < G; ++k) I[k] += light_f32(L, xk[k], y);
+                } else if (pl == LENSED_PLANE_LENS) {
+                    const int t = sm.type[c];
+                    if (t == LENSED_SIE) {
+                        bool use64 = false;
+                        if (MODE == LENSED_PREC_MIXED) {
+                            const float ex = xc - cc[0], ey = yc - cc[1];
+                            use64 = cc[17] != 0.f || ex * ex + ey * ey < cc[18];
+                        }
+                        if (use64) {
+#pragma unroll
+                            for (int k = 0; k < G; ++k) {
+                                const int a = EXACT ? k : min(a0 + k, nn - 1);
+                                sie_ray_f64(jc, ic, S.hd, sm.ud[a], sm.ud[b], sm.cd + c * kNC,
+                                            ax[k], ay[k]);
+                            }
+                        } else {
+                            const SieF K = load_sie(cc);
+#pragma unroll
+                            for (int k = 0; k < G; ++k) sie_f32(K, xk[k], y, ax[k], ay[k]);
+                        }
+                    } else if (t == LENSED_SHEAR) {
+                        const float x0 = cc[0], y0 = cc[1], g1 = cc[2], g2 = cc[3];
+#pragma unroll
+                        for (int k = 0; k < G; ++k) {
+                            const float dx = xk[k] - x0, dy = y - y0;
+                            ax[k] += fmaf(g1, dx, g2 * dy);
+                            ay[k] += fmaf(g2, dx, -g1 * dy);
+                        }
+                    } else {  // point mass
+                        const float x0 = cc[0], y0 = cc[1], te2 = cc[2];
+#pragma unroll
+                        for (int k = 0; k < G; ++k) {
+                            const float dx = xk[k] - x0, dy = y - y0;
+                            const float r2 = fmaf(dx, dx, dy * dy);
+                            const float f = r2 > 0.f ? __fdividef(te2, r2) : 0.f;
+                            ax[k] = fmaf(f, dx, ax[k]);
+                            ay[k] = fmaf(f, dy, ay[k]);
+                        }
+                    }
+                }
             }
-            ((float *)Lbuf)[lbase + pix] = acc;
+            for (int c = 0; c < ncomp; ++c) {
+                if (sm.plane[c] != LENSED_PLANE_SOURCE) continue;
+                const LightF L = load_light(sm.cf + c * kNC);
+#pragma unroll
+                for (int k = 0; k < G; ++k) I[k] += light_f32(L, xk[k] - ax[k], y - ay[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+                if (EXACT || a0 + k < nn) acc = fmaf(sm.w[b * nn + a0 + k], I[k], acc);
         }
     }
+    Lbuf[(size_t)(p - p0) * L_stride + S.pix_off + pix] = acc;
 }
 
-template <int MODE, int PPT>
-static void trace_launch_t(int threads, const SysDev *sys, const int *comp_type,
-                           const int *comp_plane, const float *cf, const double *cd,
-                           const unsigned char *valid, int P, int C_total,
-                           const TraceBlock *blocks, int n_blocks, const int *need,
-                           NodeTables nodes, int p0, int nP, void *Lbuf, long long L_stride,
-                           cudaStream_t st)
+// a2-a5 in FP64 (validation mode): plain per-ray loop.
+__global__ void __launch_bounds__(256)
+    k_trace_f64(const SysDev *__restrict__ sys, const int *__restrict__ comp_type,
+                const int *__restrict__ comp_plane, const float *__restrict__ cf,
+                const double *__restrict__ cd, const unsigned char *__restrict__ valid, int P,
+                int C_total, const TraceBlock *__restrict__ blocks, const int *__restrict__ need,
+                NodeTables nodes, int p0, double *__restrict__ Lbuf, long long L_stride)
+{
+    __shared__ __align__(16) TraceSmem sm;
+    const TraceBlock tb = blocks[blockIdx.x];
+    const int p = p0 + blockIdx.y;
+    if (!valid[(size_t)tb.sys * P + p]) return;
+    const SysDev &S = sys[tb.sys];
+    const size_t cbase = ((size_t)p * C_total + S.comp_off) * kNC;
+    stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, true, true, nodes);
+    __syncthreads();
+    const int idx = tb.start + threadIdx.x;
+    if (idx >= tb.end) return;
+    RayCtx R{S.ncomp, sm.type, sm.plane, sm.cd};
+    const int nn = S.nn, nx = S.nx;
+    const int pix = need ? need[S.need_off + idx] : idx;
+    const int i = pix / nx, j = pix - (pix / nx) * nx;
+    const double xc = ((double)j - (double)S.cx) * S.hd;
+    const double yc = ((double)i - (double)S.cy) * S.hd;
+    double acc = 0.0;
+    for (int b = 0; b < nn; ++b) {
+        const double y = yc + sm.ud[b];
+        for (int a = 0; a < nn; ++a) acc += sm.wd[b * nn + a] * brightness_f64(xc + sm.ud[a], y, R);
+    }
+    Lbuf[(size_t)(p - p0) * L_stride + S.pix_off + pix] = acc;
+}
+
+template <int MODE, int G, bool EXACT>
+static void trace_rows_t(int threads, const SysDev *sys, const int *comp_type,
+                         const int *comp_plane, const float *cf, const double *cd,
+                         const unsigned char *valid, int P, int C_total, const TraceBlock *blocks,
+                         int n_blocks, const int *need, NodeTables nodes, int p0, int nP,
+                         void *Lbuf, long long L_stride, cudaStream_t st)
 {
     dim3 grid((unsigned)n_blocks, (unsigned)nP);
-    k_trace<MODE, PPT><<<grid, threads, 0, st>>>(sys, comp_type, comp_plane, cf, cd, valid, P,
-                                                 C_total, blocks, need, nodes.u, nodes.w,
-                                                 nodes.ud, nodes.wd, p0, Lbuf, L_stride);
+    k_trace_rows<MODE, G, EXACT><<<grid, threads, 0, st>>>(sys, comp_type, comp_plane, cf, cd,
+                                                           valid, P, C_total, blocks, need, nodes,
+                                                           p0, (float *)Lbuf, L_stride);
 }
 
-void launch_trace(int precision, LaunchCfg cfg, const SysDev *sys, const int *comp_type,
+template <int MODE>
+static void trace_rows_dispatch(int nn, int threads, const SysDev *sys, const int *comp_type,
+                                const int *comp_plane, const float *cf, const double *cd,
+                                const unsigned char *valid, int P, int C_total,
+                                const TraceBlock *blocks, int n_blocks, const int *need,
+                                NodeTables nodes, int p0, int nP, void *Lbuf, long long L_stride,
+                                cudaStream_t st)
+{
+#define LENSED_ROWS(GG, EX)                                                                  \
+    trace_rows_t<MODE, GG, EX>(threads, sys, comp_type, comp_plane, cf, cd, valid, P, C_total, \
+                               blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st)
+    switch (nn) {
+    case 1: LENSED_ROWS(1, true); break;
+    case 2: LENSED_ROWS(2, true); break;
+    case 3: LENSED_ROWS(3, true); break;
+    case 4: LENSED_ROWS(4, true); break;
+    case 5: LENSED_ROWS(5, true); break;
+    case 6: LENSED_ROWS(6, true); break;
+    case 7: LENSED_ROWS(7, true); break;
+    case 8: LENSED_ROWS(8, true); break;
+    default: LENSED_ROWS(4, false); break;
+    }
+#undef LENSED_ROWS
+}
+
+void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const int *comp_type,
                   const int *comp_plane, const float *cf, const double *cd,
                   const unsigned char *valid, int P, int C_total, const TraceBlock *blocks,
                   int n_blocks, const int *need, NodeTables nodes, int p0, int nP, void *Lbuf,
                   long long L_stride, cudaStream_t st)
 {
     if (n_blocks <= 0 || nP <= 0) return;
-#define LENSED_TRACE(M, K)                                                                    \
-    trace_launch_t<M, K>(cfg.trace_threads, sys, comp_type, comp_plane, cf, cd, valid, P,    \
-                         C_total, blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st)
     if (precision == LENSED_PREC_FP64) {
-        LENSED_TRACE(LENSED_PREC_FP64, 1);
+        dim3 grid((unsigned)n_blocks, (unsigned)nP);
+        k_trace_f64<<<grid, cfg.trace_threads, 0, st>>>(sys, comp_type, comp_plane, cf, cd,
+                                                         valid, P, C_total, blocks, need, nodes,
+                                                         p0, (double *)Lbuf, L_stride);
     } else if (precision == LENSED_PREC_MIXED) {
-        if (cfg.pix_per_thread == 2) LENSED_TRACE(LENSED_PREC_MIXED, 2);
-        else LENSED_TRACE(LENSED_PREC_MIXED, 1);
+        trace_rows_dispatch<LENSED_PREC_MIXED>(nn, cfg.trace_threads, sys, comp_type, comp_plane,
+                                               cf, cd, valid, P, C_total, blocks, n_blocks, need,
+                                               nodes, p0, nP, Lbuf, L_stride, st);
     } else {
-        if (cfg.pix_per_thread == 2) LENSED_TRACE(LENSED_PREC_FP32, 2);
-        else LENSED_TRACE(LENSED_PREC_FP32, 1);
+        trace_rows_dispatch<LENSED_PREC_FP32>(nn, cfg.trace_threads, sys, comp_type, comp_plane,
+                                              cf, cd, valid, P, C_total, blocks, n_blocks, need,
+                                              nodes, p0, nP, Lbuf, L_stride, st);
     }
-#undef LENSED_TRACE
 }
 
 // ---------------------------------------------------------------------------

@@ -193,6 +193,11 @@ struct PsfGroup {
     int off, count;  // into the PSF block table
 };
 
+struct TraceGroup {
+    int nn;          // nodes per row of the rule of every system in the group
+    int off, count;  // into the trace block table
+};
+
 struct GraphEntry {
     int P;
     const void *params;
@@ -208,10 +213,9 @@ struct Candidate {
 };
 
 const Candidate kCandidates[] = {
-    {{256, 1}, "trace 256 threads x 1 pixel"},
-    {{128, 1}, "trace 128 threads x 1 pixel"},
-    {{256, 2}, "trace 256 threads x 2 pixels"},
-    {{128, 2}, "trace 128 threads x 2 pixels"},
+    {{128}, "trace blocks of 128 pixels"},
+    {{256}, "trace blocks of 256 pixels"},
+    {{64}, "trace blocks of 64 pixels"},
 };
 constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 
@@ -258,6 +262,7 @@ struct lensed_model {
     // trace block tables, rebuilt when the items per block change
     int trace_items = 0;
     std::vector<int> trace_sys_off, trace_sys_cnt;
+    std::vector<TraceGroup> trace_groups;
     DevBuf<TraceBlock> trace_blocks;
     int n_trace_blocks = 0;
     std::vector<int> render_trace_off, render_trace_cnt;
@@ -306,16 +311,27 @@ namespace {
 int build_trace_tables(lensed_model *m, int items)
 {
     if (m->trace_items == items) return LENSED_OK;
+    // systems ordered by nodes per row, so each group is one launch
+    std::vector<int> order(m->n_sys);
+    for (int s = 0; s < m->n_sys; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return m->n_nodes[a] < m->n_nodes[b]; });
     std::vector<TraceBlock> tb, rb;
     m->trace_sys_off.assign(m->n_sys, 0);
     m->trace_sys_cnt.assign(m->n_sys, 0);
     m->render_trace_off.assign(m->n_sys, 0);
     m->render_trace_cnt.assign(m->n_sys, 0);
-    for (int s = 0; s < m->n_sys; ++s) {
+    m->trace_groups.clear();
+    for (int s : order) {
+        if (m->trace_groups.empty() || m->trace_groups.back().nn != m->n_nodes[s])
+            m->trace_groups.push_back({m->n_nodes[s], (int)tb.size(), 0});
         m->trace_sys_off[s] = (int)tb.size();
         for (int a = 0; a < m->need_count[s]; a += items)
             tb.push_back({s, a, std::min(a + items, m->need_count[s])});
         m->trace_sys_cnt[s] = (int)tb.size() - m->trace_sys_off[s];
+        m->trace_groups.back().count = (int)tb.size() - m->trace_groups.back().off;
+    }
+    for (int s = 0; s < m->n_sys; ++s) {
         m->render_trace_off[s] = (int)rb.size();
         const int npix = m->sys_h[s].npix;
         for (int a = 0; a < npix; a += items) rb.push_back({s, a, std::min(a + items, npix)});
@@ -386,9 +402,10 @@ void enqueue_batch(lensed_model *m, const double *params, int P, double *out, La
     for (int p0 = 0; p0 < P; p0 += m->chunk_P) {
         const int nP = std::min(m->chunk_P, P - p0);
         if (tm) tm->begin(1);
-        launch_trace(m->precision, cfg, m->sys.p, m->comp_type.p, m->comp_plane.p, m->cf.p,
-                     m->cd.p, m->valid.p, P, m->C_total, m->trace_blocks.p, m->n_trace_blocks,
-                     m->need.p, m->nodes(), p0, nP, m->Lbuf.p, m->total_pix, st);
+        for (const TraceGroup &g : m->trace_groups)
+            launch_trace(m->precision, cfg, g.nn, m->sys.p, m->comp_type.p, m->comp_plane.p,
+                         m->cf.p, m->cd.p, m->valid.p, P, m->C_total, m->trace_blocks.p + g.off,
+                         g.count, m->need.p, m->nodes(), p0, nP, m->Lbuf.p, m->total_pix, st);
         if (tm) tm->end();
         if (tm) tm->begin(2);
         for (const PsfGroup &g : m->psf_groups)
@@ -728,7 +745,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         g_last_error = msg;
         return rc;
     }
-    if ((rc = build_trace_tables(m, m->cfg().trace_threads * m->cfg().pix_per_thread)) ||
+    if ((rc = build_trace_tables(m, m->cfg().trace_threads)) ||
         (rc = m->rcf.alloc((size_t)C_total * kNC)) || (rc = m->rcd.alloc((size_t)C_total * kNC)) ||
         (rc = m->rvalid.alloc(n_systems)) || (rc = m->rcvalid.alloc((size_t)C_total))) {
         std::string msg = g_last_error;
@@ -797,7 +814,8 @@ extern "C" int lensed_render(lensed_model *m, int system, const double *params, 
     launch_prologue(m->sys.p, m->comp_sys.p, system, 1, S.comp_off, S.ncomp, m->comp_type.p,
                     m->comp_free.p, m->comp_value.p, params, true, 1, 0, 1, m->n_par_max,
                     m->C_total, m->rcf.p, m->rcd.p, m->rcvalid.p, m->rvalid.p, st);
-    launch_trace(m->precision, m->cfg(), m->sys.p, m->comp_type.p, m->comp_plane.p, m->rcf.p,
+    launch_trace(m->precision, m->cfg(), m->n_nodes[system], m->sys.p, m->comp_type.p,
+                 m->comp_plane.p, m->rcf.p,
                  m->rcd.p, m->rvalid.p, 1, m->C_total,
                  m->render_trace.p + m->render_trace_off[system], m->render_trace_cnt[system],
                  nullptr, m->nodes(), 0, 1, m->rL.p, m->total_pix, st);
@@ -828,7 +846,7 @@ static int run_batch(lensed_model *m, const double *params, int P, double *out, 
     int rc = ensure_capacity(m, P);
     if (rc) return rc;
     LaunchCfg cfg = m->cfg();
-    if ((rc = build_trace_tables(m, cfg.trace_threads * cfg.pix_per_thread))) return rc;
+    if ((rc = build_trace_tables(m, cfg.trace_threads))) return rc;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (st) cudaStreamIsCapturing(st, &cs);
     if (!use_graph || cs != cudaStreamCaptureStatusNone) {
@@ -885,7 +903,7 @@ extern "C" int lensed_loglike_plain(lensed_model *m, const double *params, int P
     if (rc) return rc;
     if ((rc = ensure_capacity(m, P))) return rc;
     LaunchCfg cfg = m->cfg();
-    if ((rc = build_trace_tables(m, cfg.trace_threads * cfg.pix_per_thread))) return rc;
+    if ((rc = build_trace_tables(m, cfg.trace_threads))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     for (int s = 0; s < m->n_sys; ++s) {
         for (int p = 0; p < P; ++p) {
@@ -893,7 +911,8 @@ extern "C" int lensed_loglike_plain(lensed_model *m, const double *params, int P
                             m->sys_h[s].ncomp, m->comp_type.p, m->comp_free.p, m->comp_value.p,
                             params, false, P, p, 1, m->n_par_max, m->C_total, m->cf.p, m->cd.p,
                             m->cvalid.p, m->valid.p, st);
-            launch_trace(m->precision, cfg, m->sys.p, m->comp_type.p, m->comp_plane.p, m->cf.p,
+            launch_trace(m->precision, cfg, m->n_nodes[s], m->sys.p, m->comp_type.p,
+                         m->comp_plane.p, m->cf.p,
                          m->cd.p, m->valid.p, P, m->C_total,
                          m->trace_blocks.p + m->trace_sys_off[s], m->trace_sys_cnt[s], m->need.p,
                          m->nodes(), p, 1, m->Lbuf.p, m->total_pix, st);
@@ -970,7 +989,7 @@ extern "C" int lensed_autotune(lensed_model *m, const double *params, int P, voi
     cudaEventDestroy(e1);
     m->cfg_index = best_i;
     LaunchCfg cfg = m->cfg();
-    if ((rc = build_trace_tables(m, cfg.trace_threads * cfg.pix_per_thread))) return rc;
+    if ((rc = build_trace_tables(m, cfg.trace_threads))) return rc;
     CUDA_OK(cudaStreamSynchronize(st));
     return LENSED_OK;
 }
@@ -982,7 +1001,7 @@ extern "C" int lensed_batch_plan(lensed_model *m, int P, int *launches, int *chu
     int rc = ensure_capacity(m, P);
     if (rc) return rc;
     const int chunks = (P + m->chunk_P - 1) / m->chunk_P;
-    *launches = 3 + chunks * (1 + (int)m->psf_groups.size());
+    *launches = 3 + chunks * ((int)m->trace_groups.size() + (int)m->psf_groups.size());
     *chunk_points = m->chunk_P;
     return LENSED_OK;
 }
@@ -996,7 +1015,7 @@ extern "C" int lensed_profile_batch(lensed_model *m, const double *params, int P
     if (!stage_ms) return fail(LENSED_E_ARG, "stage_ms is NULL");
     if ((rc = ensure_capacity(m, P))) return rc;
     LaunchCfg cfg = m->cfg();
-    if ((rc = build_trace_tables(m, cfg.trace_threads * cfg.pix_per_thread))) return rc;
+    if ((rc = build_trace_tables(m, cfg.trace_threads))) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     StageTimer tm;
     tm.st = st;

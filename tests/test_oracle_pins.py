@@ -285,6 +285,15 @@ def test_sie_rotation_equivariance():
         assert np.allclose(ar, R @ a, atol=1e-14)
 
 
+def test_singular_centres_have_no_deflection():
+    # reading: alpha = 0 exactly at a point mass and at the centre of a
+    # coreless SIE (the direction is undefined there); a core removes the
+    # singularity and alpha -> 0 continuously
+    assert O.deflection("sie", [0.1, -0.2, 1.0, 0.7, 30.0, 0.0], 0.1, -0.2) == (0.0, 0.0)
+    ax, ay = O.deflection("sie", [0.1, -0.2, 1.0, 0.7, 30.0, 0.05], 0.1 + 1e-9, -0.2)
+    assert math.hypot(ax, ay) < 1e-7
+
+
 def test_point_mass_closed_form():
     te = 0.3
     for x, y in [(0.1, 0.2), (-0.4, 0.05), (0.3, 0.0)]:
