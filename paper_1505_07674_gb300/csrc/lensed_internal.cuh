@@ -27,9 +27,11 @@ constexpr int kPsfThreads = (kTileW / kOutPerThread) * kTileH;  // 256
 constexpr int kKindPower = 0;  // Sersic / de Vaucouleurs: 2^-(2^(p2 lg2 R^2 + lc))
 constexpr int kKindGauss = 1;  // Gaussian: 2^-(k R^2)
 
-// SIE evaluation in MIXED precision switches to FP64 below these.
-constexpr double kMixedRoundE = 0.05;   // e = sqrt(1 - q^2)
-constexpr double kMixedCoreFactor = 4.0;  // psi < 4 s
+// SIE evaluation in MIXED precision switches to FP64 for every pixel when
+// e = sqrt(1 - q^2) < kMixedRoundE, and for the pixels whose square comes
+// within kMixedCoreFactor * s / q of the lens centre.
+constexpr double kMixedRoundE = 0.05;
+constexpr double kMixedCoreFactor = 2.0;
 
 // Series in e replaces atan/atanh below this (both precisions).
 constexpr double kSeriesE = 1e-3;
@@ -48,6 +50,7 @@ struct SysDev {
     int comp_off, ncomp; // into the component tables
     int n_params;
     long long need_off;  // into the needed-pixel list
+    int n_need;          // length of the needed-pixel list
     int tile_off, n_tiles;  // into the active-tile list
     int tiles_x, tiles_y;   // full tiling of the image
     double zeropoint;
@@ -102,6 +105,15 @@ void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const
 // One-time kernel attributes (dynamic shared memory limits); call before
 // any launch or capture.
 void init_kernel_attributes();
+
+// MIXED only: recompute, with the FP64 SIE, the pixels of each (system,
+// point) that the MIXED rule assigns to FP64 (after launch_trace wrote
+// their FP32 values).  need == nullptr: every pixel of the systems (render).
+void launch_fix64(LaunchCfg cfg, const SysDev *sys, int s0, int nS, const int *comp_type,
+                  const int *comp_plane, const float *cf, const double *cd,
+                  const unsigned char *valid, int P, int C_total, const int *need,
+                  NodeTables nodes, int p0, int nP, void *Lbuf, long long L_stride,
+                  cudaStream_t st);
 
 // a6-a7: PSF convolution of the tiles in the block table, then either the
 // masked chi^2 partial sums (partial != nullptr) or the convolved image

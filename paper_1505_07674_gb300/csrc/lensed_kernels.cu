@@ -44,17 +44,27 @@ __device__ __forceinline__ float lg2f(float x)
 // ---------------------------------------------------------------------------
 // a1: parameter prologue
 
-// Regularised lower incomplete gamma P(a, x) by its power series.
-__device__ double lower_gamma_p(double a, double x)
+// Regularised lower incomplete gamma P(a, x) by its power series
+//   P(a, x) = x^a e^-x / Gamma(a+1) * sum_k x^k / ((a+1)...(a+k)),
+// summed as one fraction N / D (D the running product of (a+j), N the
+// matching numerator) so the loop has no division; lg_a1 = lgamma(a + 1).
+__device__ double lower_gamma_p(double a, double x, double lg_a1)
 {
     if (x <= 0.0) return 0.0;
-    double term = 1.0, sum = 1.0;
-    for (int k = 1; k < 5000; ++k) {
-        term *= x / (a + k);
-        sum += term;
-        if (term < 1e-17 * sum) break;
+    double N = 1.0, D = 1.0, xk = 1.0;
+    for (int k = 1; k < 400; ++k) {
+        const double f = a + k;
+        xk *= x;
+        N = N * f + xk;
+        D *= f;
+        if (xk < 1e-17 * N) break;
+        if (D > 1e250) {  // rescale before the product overflows
+            N *= 1e-250;
+            D *= 1e-250;
+            xk *= 1e-250;
+        }
     }
-    return exp(a * log(x) - x - lgamma(a + 1.0)) * sum;
+    return exp(a * log(x) - x - lg_a1) * (N / D);
 }
 
 // Sersic b_n: root of P(2n, b) = 1/2.  Newton from the Ciotti & Bertin
@@ -66,9 +76,9 @@ __device__ double sersic_b(double n)
     double b = a - 1.0 / 3.0 + 4.0 / (405.0 * n) + 46.0 / (25515.0 * n * n) +
                131.0 / (1148175.0 * n * n * n) - 2194697.0 / (30690717750.0 * n * n * n * n);
     if (!(b > lo && b < hi)) b = 0.5 * (lo + hi);
-    const double lga = lgamma(a);
-    for (int it = 0; it < 200; ++it) {
-        double f = lower_gamma_p(a, b) - 0.5;
+    const double lga = lgamma(a), lga1 = lga + log(a);
+    for (int it = 0; it < 100; ++it) {
+        double f = lower_gamma_p(a, b, lga1) - 0.5;
         if (f == 0.0) break;
         if (f < 0.0) lo = b;
         else hi = b;
@@ -123,8 +133,8 @@ __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__res
         // 0 x0, 1 y0, 2 cos, 3 sin, 4 cos_lo, 5 sin_lo, 6 q^2, 7 q^2_lo,
         // 8 s^2, 9 s, 10 q^2 s, 11 e, 12 e_lo, 13 pref, 14 pref_lo,
         // 15 series flag, 16 e^2, 17 FP64 flag (MIXED, e < 0.05),
-        // 18 (4 s / q + h / sqrt 2)^2: pixels whose centre lies inside this
-        // radius of the lens centre take the FP64 branch in MIXED
+        // 18 (2 s / q)^2: pixels whose square comes inside this radius of
+        // the lens centre take the FP64 branch in MIXED
         const double b = v[2], q = v[3], sc = v[5];
         ok = ok && q > 0.0 && q <= 1.0 && b >= 0.0 && sc >= 0.0;
         double sn, cs;
@@ -142,7 +152,7 @@ __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__res
         o[15] = series ? 1.0 : 0.0;
         o[16] = e * e;
         o[17] = e < kMixedRoundE ? 1.0 : 0.0;
-        const double rc = ok ? kMixedCoreFactor * sc / q + 0.7071067811865476 * hd : 0.0;
+        const double rc = ok ? kMixedCoreFactor * sc / q : 0.0;
         o[18] = rc * rc;
         lo[2] = 4;
         lo[3] = 5;
@@ -465,11 +475,11 @@ __device__ __forceinline__ void stage_point(TraceSmem &sm, const SysDev &S, cons
     }
 }
 
-// a2-a5 in FP32 / MIXED: one thread per pixel; for every row of the rule's
-// node grid, G rays are traced together component by component, so each
-// component's constants are read into registers once per G rays and the G
-// independent rays give the scheduler instruction-level parallelism.
-// EXACT: the rule has exactly G nodes per row (no guards).
+// a2-a5 in FP32 (also the first pass of MIXED): one thread per pixel; for
+// every row of the rule's node grid, G rays are traced together component by
+// component, so each component's constants are read into registers once per
+// G rays and the G independent rays give the scheduler instruction-level
+// parallelism.  EXACT: the rule has exactly G nodes per row (no guards).
 template <int MODE, int G, bool EXACT>
 __global__ void __launch_bounds__(256)
     k_trace_rows(const SysDev *__restrict__ sys, const int *__restrict__ comp_type,
@@ -484,8 +494,7 @@ __global__ void __launch_bounds__(256)
     if (!valid[(size_t)tb.sys * P + p]) return;
     const SysDev &S = sys[tb.sys];
     const size_t cbase = ((size_t)p * C_total + S.comp_off) * kNC;
-    stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, MODE == LENSED_PREC_MIXED, false,
-                nodes);
+    stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, false, false, nodes);
     __syncthreads();
 
     const int idx = tb.start + threadIdx.x;
@@ -524,23 +533,9 @@ __global__ void __launch_bounds__(256)
                 } else if (pl == LENSED_PLANE_LENS) {
                     const int t = sm.type[c];
                     if (t == LENSED_SIE) {
-                        bool use64 = false;
-                        if (MODE == LENSED_PREC_MIXED) {
-                            const float ex = xc - cc[0], ey = yc - cc[1];
-                            use64 = cc[17] != 0.f || ex * ex + ey * ey < cc[18];
-                        }
-                        if (use64) {
+                        const SieF K = load_sie(cc);
 #pragma unroll
-                            for (int k = 0; k < G; ++k) {
-                                const int a = EXACT ? k : min(a0 + k, nn - 1);
-                                sie_ray_f64(jc, ic, S.hd, sm.ud[a], sm.ud[b], sm.cd + c * kNC,
-                                            ax[k], ay[k]);
-                            }
-                        } else {
-                            const SieF K = load_sie(cc);
-#pragma unroll
-                            for (int k = 0; k < G; ++k) sie_f32(K, xk[k], y, ax[k], ay[k]);
-                        }
+                        for (int k = 0; k < G; ++k) sie_f32(K, xk[k], y, ax[k], ay[k]);
                     } else if (t == LENSED_SHEAR) {
                         const float x0 = cc[0], y0 = cc[1], g1 = cc[2], g2 = cc[3];
 #pragma unroll
@@ -658,15 +653,151 @@ void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const
         k_trace_f64<<<grid, cfg.trace_threads, 0, st>>>(sys, comp_type, comp_plane, cf, cd,
                                                          valid, P, C_total, blocks, need, nodes,
                                                          p0, (double *)Lbuf, L_stride);
-    } else if (precision == LENSED_PREC_MIXED) {
-        trace_rows_dispatch<LENSED_PREC_MIXED>(nn, cfg.trace_threads, sys, comp_type, comp_plane,
-                                               cf, cd, valid, P, C_total, blocks, n_blocks, need,
-                                               nodes, p0, nP, Lbuf, L_stride, st);
     } else {
         trace_rows_dispatch<LENSED_PREC_FP32>(nn, cfg.trace_threads, sys, comp_type, comp_plane,
                                               cf, cd, valid, P, C_total, blocks, n_blocks, need,
                                               nodes, p0, nP, Lbuf, L_stride, st);
     }
+}
+
+// MIXED second pass.  One block per (system, point).  The pixels the MIXED
+// rule assigns to FP64 -- every listed pixel when an SIE of the point is
+// nearly round (e < 0.05), else the pixels whose square reaches within
+// 2 s / q of an SIE centre -- are recomputed ray by ray with that SIE in FP64
+// and every other component in FP32, overwriting the first pass.
+__device__ float pixel_mixed(const TraceSmem &sm, const SysDev &S, int pix, const bool *sie64)
+{
+    const int nn = S.nn, nx = S.nx, ncomp = S.ncomp;
+    const int i = pix / nx, j = pix - (pix / nx) * nx;
+    const float jc = (float)j - S.cx, ic = (float)i - S.cy;
+    const float xc = fmaf(jc, S.h, jc * S.h_lo);
+    const float yc = fmaf(ic, S.h, ic * S.h_lo);
+    float acc = 0.f;
+    for (int b = 0; b < nn; ++b) {
+        const float y = yc + sm.u[b];
+        for (int a = 0; a < nn; ++a) {
+            const float x = xc + sm.u[a];
+            float I = 0.f, ax = 0.f, ay = 0.f;
+            for (int c = 0; c < ncomp; ++c) {
+                const int pl = sm.plane[c];
+                const float *cc = sm.cf + c * kNC;
+                if (pl == LENSED_PLANE_FOREGROUND) {
+                    I += light_f32(load_light(cc), x, y);
+                } else if (pl == LENSED_PLANE_LENS) {
+                    const int t = sm.type[c];
+                    if (t == LENSED_SIE) {
+                        if (sie64[c]) sie_ray_f64(jc, ic, S.hd, sm.ud[a], sm.ud[b], sm.cd + c * kNC, ax, ay);
+                        else sie_f32(load_sie(cc), x, y, ax, ay);
+                    } else if (t == LENSED_SHEAR) {
+                        const float dx = x - cc[0], dy = y - cc[1];
+                        ax += fmaf(cc[2], dx, cc[3] * dy);
+                        ay += fmaf(cc[3], dx, -cc[2] * dy);
+                    } else {
+                        const float dx = x - cc[0], dy = y - cc[1];
+                        const float r2 = fmaf(dx, dx, dy * dy);
+                        const float f = r2 > 0.f ? __fdividef(cc[2], r2) : 0.f;
+                        ax = fmaf(f, dx, ax);
+                        ay = fmaf(f, dy, ay);
+                    }
+                }
+            }
+            for (int c = 0; c < ncomp; ++c)
+                if (sm.plane[c] == LENSED_PLANE_SOURCE)
+                    I += light_f32(load_light(sm.cf + c * kNC), x - ax, y - ay);
+            acc = fmaf(sm.w[b * nn + a], I, acc);
+        }
+    }
+    return acc;
+}
+
+// Does pixel (i, j)'s square reach within sqrt(r2) of (x0, y0)?
+__device__ __forceinline__ bool pixel_near(const SysDev &S, int i, int j, double x0, double y0,
+                                           double r2)
+{
+    const double xc = ((double)j - (double)S.cx) * S.hd, yc = ((double)i - (double)S.cy) * S.hd;
+    const double dx = fmax(fabs(xc - x0) - 0.5 * S.hd, 0.0);
+    const double dy = fmax(fabs(yc - y0) - 0.5 * S.hd, 0.0);
+    return dx * dx + dy * dy < r2;
+}
+
+__global__ void __launch_bounds__(128)
+    k_trace_fix64(const SysDev *__restrict__ sys, int s0, const int *__restrict__ comp_type,
+                  const int *__restrict__ comp_plane, const float *__restrict__ cf,
+                  const double *__restrict__ cd, const unsigned char *__restrict__ valid, int P,
+                  int C_total, const int *__restrict__ need, NodeTables nodes, int p0,
+                  float *__restrict__ Lbuf, long long L_stride)
+{
+    __shared__ __align__(16) TraceSmem sm;
+    const int s = s0 + blockIdx.x;
+    const int p = p0 + blockIdx.y;
+    if (!valid[(size_t)s * P + p]) return;
+    const SysDev &S = sys[s];
+    const size_t cbase = ((size_t)p * C_total + S.comp_off) * kNC;
+    stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, true, false, nodes);
+    __syncthreads();
+    const int ncomp = S.ncomp, nx = S.nx, ny = S.ny;
+    float *L = Lbuf + (size_t)(p - p0) * L_stride + S.pix_off;
+    bool whole = false;
+    for (int c = 0; c < ncomp; ++c)
+        if (sm.type[c] == LENSED_SIE && sm.cd[c * kNC + 17] != 0.0) whole = true;
+    bool sie64[LENSED_MAX_COMPONENTS];
+    if (whole) {
+        const int n = need ? S.n_need : S.npix;
+        for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+            const int pix = need ? need[S.need_off + idx] : idx;
+            const int i = pix / nx, j = pix - (pix / nx) * nx;
+            for (int c = 0; c < ncomp; ++c) {
+                const double *cc = sm.cd + c * kNC;
+                sie64[c] = sm.type[c] == LENSED_SIE &&
+                           (cc[17] != 0.0 || pixel_near(S, i, j, cc[0], cc[1], cc[18]));
+            }
+            L[pix] = pixel_mixed(sm, S, pix, sie64);
+        }
+        return;
+    }
+    // core boxes, one SIE after the other; a pixel already covered by an
+    // earlier SIE's box is skipped so every pixel is written once
+    for (int c = 0; c < ncomp; ++c) {
+        if (sm.type[c] != LENSED_SIE) continue;
+        const double *cc = sm.cd + c * kNC;
+        const double r = sqrt(cc[18]);
+        if (!(r > 0.0)) continue;
+        const int j0 = max(0, (int)floor((cc[0] - r) / S.hd + S.cx - 1.0));
+        const int j1 = min(nx - 1, (int)ceil((cc[0] + r) / S.hd + S.cx + 1.0));
+        const int i0 = max(0, (int)floor((cc[1] - r) / S.hd + S.cy - 1.0));
+        const int i1 = min(ny - 1, (int)ceil((cc[1] + r) / S.hd + S.cy + 1.0));
+        if (j1 < j0 || i1 < i0) continue;
+        const int bw = j1 - j0 + 1, n = bw * (i1 - i0 + 1);
+        for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+            const int i = i0 + idx / bw, j = j0 + idx % bw;
+            if (!pixel_near(S, i, j, cc[0], cc[1], cc[18])) continue;
+            bool earlier = false;
+            for (int c2 = 0; c2 < c; ++c2) {
+                const double *c2c = sm.cd + c2 * kNC;
+                if (sm.type[c2] == LENSED_SIE && pixel_near(S, i, j, c2c[0], c2c[1], c2c[18]))
+                    earlier = true;
+            }
+            if (earlier) continue;
+            for (int c3 = 0; c3 < ncomp; ++c3) {
+                const double *c3c = sm.cd + c3 * kNC;
+                sie64[c3] = sm.type[c3] == LENSED_SIE && pixel_near(S, i, j, c3c[0], c3c[1], c3c[18]);
+            }
+            L[i * nx + j] = pixel_mixed(sm, S, i * nx + j, sie64);
+        }
+    }
+}
+
+void launch_fix64(LaunchCfg cfg, const SysDev *sys, int s0, int nS, const int *comp_type,
+                  const int *comp_plane, const float *cf, const double *cd,
+                  const unsigned char *valid, int P, int C_total, const int *need,
+                  NodeTables nodes, int p0, int nP, void *Lbuf, long long L_stride,
+                  cudaStream_t st)
+{
+    (void)cfg;
+    if (nS <= 0 || nP <= 0) return;
+    dim3 grid((unsigned)nS, (unsigned)nP);
+    k_trace_fix64<<<grid, 128, 0, st>>>(sys, s0, comp_type, comp_plane, cf, cd, valid, P, C_total,
+                                         need, nodes, p0, (float *)Lbuf, L_stride);
 }
 
 // ---------------------------------------------------------------------------
@@ -731,10 +862,22 @@ __global__ void __launch_bounds__(kPsfThreads)
 
     const int tc = threadIdx.x % (kTileW / kOutPerThread);
     const int tr = threadIdx.x / (kTileW / kOutPerThread);
+    const int i = pb.i0 + tr;
+    const int jb = pb.j0 + tc * kOutPerThread;
+    // chi^2 mode: a warp none of whose outputs carries weight skips the
+    // convolution (its partial is zero)
+    bool live = true;
+    if (partial) {
+        bool any = false;
+        if (i < ny)
+            for (int o = 0; o < kOutPerThread; ++o)
+                if (jb + o < nx && weight[S.pix_off + (size_t)i * nx + jb + o] > T(0)) any = true;
+        live = __any_sync(0xffffffffu, any);
+    }
     T acc[kOutPerThread];
 #pragma unroll
     for (int o = 0; o < kOutPerThread; ++o) acc[o] = T(0);
-    for (int kk = 0; kk <= 2 * Ph; ++kk) {
+    for (int kk = 0; live && kk <= 2 * Ph; ++kk) {
         T f[W];
 #pragma unroll
         for (int l = 0; l < W; ++l) f[l] = s_F[kk * W + l];
@@ -748,8 +891,6 @@ __global__ void __launch_bounds__(kPsfThreads)
             for (int l = 0; l < W; ++l) acc[o] += f[l] * lv[o + l];
     }
 
-    const int i = pb.i0 + tr;
-    const int jb = pb.j0 + tc * kOutPerThread;
     if (partial) {
         double chi = 0.0;
         if (i < ny) {

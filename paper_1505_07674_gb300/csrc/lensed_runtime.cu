@@ -406,6 +406,10 @@ void enqueue_batch(lensed_model *m, const double *params, int P, double *out, La
             launch_trace(m->precision, cfg, g.nn, m->sys.p, m->comp_type.p, m->comp_plane.p,
                          m->cf.p, m->cd.p, m->valid.p, P, m->C_total, m->trace_blocks.p + g.off,
                          g.count, m->need.p, m->nodes(), p0, nP, m->Lbuf.p, m->total_pix, st);
+        if (m->precision == LENSED_PREC_MIXED)
+            launch_fix64(cfg, m->sys.p, 0, m->n_sys, m->comp_type.p, m->comp_plane.p, m->cf.p,
+                         m->cd.p, m->valid.p, P, m->C_total, m->need.p, m->nodes(), p0, nP,
+                         m->Lbuf.p, m->total_pix, st);
         if (tm) tm->end();
         if (tm) tm->begin(2);
         for (const PsfGroup &g : m->psf_groups)
@@ -638,6 +642,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
                 ++cnt;
             }
         need_count[s] = cnt;
+        S.n_need = cnt;
         // tiles of the chi^2 pass: those holding an output with w > 0
         S.tiles_x = (nx + kTileW - 1) / kTileW;
         S.tiles_y = (ny + kTileH - 1) / kTileH;
@@ -819,6 +824,10 @@ extern "C" int lensed_render(lensed_model *m, int system, const double *params, 
                  m->rcd.p, m->rvalid.p, 1, m->C_total,
                  m->render_trace.p + m->render_trace_off[system], m->render_trace_cnt[system],
                  nullptr, m->nodes(), 0, 1, m->rL.p, m->total_pix, st);
+    if (m->precision == LENSED_PREC_MIXED)
+        launch_fix64(m->cfg(), m->sys.p, system, 1, m->comp_type.p, m->comp_plane.p, m->rcf.p,
+                     m->rcd.p, m->rvalid.p, 1, m->C_total, nullptr, m->nodes(), 0, 1, m->rL.p,
+                     m->total_pix, st);
     if (flags == LENSED_RENDER_UNCONVOLVED) {
         launch_copy_image(m->precision, m->rL.p, S.pix_off, S.npix, m->rvalid.p + system,
                           out_image, st);
@@ -916,6 +925,10 @@ extern "C" int lensed_loglike_plain(lensed_model *m, const double *params, int P
                          m->cd.p, m->valid.p, P, m->C_total,
                          m->trace_blocks.p + m->trace_sys_off[s], m->trace_sys_cnt[s], m->need.p,
                          m->nodes(), p, 1, m->Lbuf.p, m->total_pix, st);
+            if (m->precision == LENSED_PREC_MIXED)
+                launch_fix64(cfg, m->sys.p, s, 1, m->comp_type.p, m->comp_plane.p, m->cf.p,
+                             m->cd.p, m->valid.p, P, m->C_total, m->need.p, m->nodes(), p, 1,
+                             m->Lbuf.p, m->total_pix, st);
             if (m->psf_sys_cnt[s] > 0)
                 launch_psf(m->precision, m->psf_q[s], m->psf_p[s], m->sys.p, m->psf_f.p,
                            m->psf_d.p, m->data.p, m->weight.p, m->data_d.p, m->weight_d.p, m->valid.p, P,
@@ -1001,7 +1014,8 @@ extern "C" int lensed_batch_plan(lensed_model *m, int P, int *launches, int *chu
     int rc = ensure_capacity(m, P);
     if (rc) return rc;
     const int chunks = (P + m->chunk_P - 1) / m->chunk_P;
-    *launches = 3 + chunks * ((int)m->trace_groups.size() + (int)m->psf_groups.size());
+    *launches = 3 + chunks * ((int)m->trace_groups.size() + (int)m->psf_groups.size() +
+                              (m->precision == LENSED_PREC_MIXED ? 1 : 0));
     *chunk_points = m->chunk_P;
     return LENSED_OK;
 }
