@@ -207,6 +207,32 @@ int lensed_loglike_plain(lensed_model *m, const double *params, int P, double *o
 int lensed_loglike_batch_host(lensed_model *m, const double *params_host, int P,
                               double *out_host, void *stream);
 
+/* lensed_loglike_batch for callers that cannot allocate device memory
+ * during evaluation: for example a sampler embedded in a framework that has
+ * reserved nearly all device memory for its own pool (so cudaMalloc fails),
+ * or a service whose device-memory budget is fixed at start-up.  This call
+ * allocates nothing: its scratch (per-point constants, validity flags,
+ * pixel luminosities, chi^2 partials) lives in one fixed 32 MiB device array
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits.  The paper has no counterpart; it is a property
+ * of this library's interface.
+ *   - Same arguments and results as lensed_loglike_batch (params and
+ *     out_loglike are caller-owned DEVICE arrays), launched directly on
+ *     stream without a graph.
+ *   - P is limited by the array: the per-point scratch of all P points plus
+ *     the pixel luminosities of at least one point must fit in 32 MiB;
+ *     larger requests return LENSED_E_ARG with the limit in the message.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array and overwrites it; calls whose work
+ *     overlaps on the GPU (two streams, or two host threads) race and give
+ *     wrong results: serialise them.
+ *   - Nothing in the array needs clearing: every value is written before
+ *     it is read within the call. */
+int lensed_loglike_batch_noalloc(lensed_model *m, const double *params, int P,
+                                 double *out_loglike, void *stream);
+
 /* Time the candidate tile configurations on a batch of P points drawn
  * inside the given DEVICE parameter array (same layout as
  * lensed_loglike_batch) and keep the fastest for later batched calls.

@@ -26,7 +26,7 @@ MAX_COMPONENT_PARAMS = 8
 EXPORTS = ("lensed_create_model", "lensed_destroy", "lensed_model_info_get", "lensed_render",
            "lensed_loglike_batch", "lensed_loglike_plain", "lensed_loglike_batch_host",
            "lensed_autotune", "lensed_tuned_config", "lensed_last_error", "lensed_batch_plan",
-           "lensed_profile_batch")
+           "lensed_profile_batch", "lensed_loglike_batch_noalloc")
 
 
 class Component(C.Structure):
@@ -75,7 +75,8 @@ def lib():
         L.lensed_destroy.restype = None
         L.lensed_model_info_get.argtypes = [vp, C.POINTER(ModelInfo)]
         L.lensed_render.argtypes = [vp, C.c_int, vp, C.c_int, vp, vp]
-        for name in ("lensed_loglike_batch", "lensed_loglike_plain", "lensed_loglike_batch_host"):
+        for name in ("lensed_loglike_batch", "lensed_loglike_plain", "lensed_loglike_batch_host",
+                     "lensed_loglike_batch_noalloc"):
             getattr(L, name).argtypes = [vp, vp, C.c_int, vp, vp]
         L.lensed_autotune.argtypes = [vp, vp, C.c_int, vp]
         L.lensed_tuned_config.argtypes = [vp, C.c_char_p, C.c_int]

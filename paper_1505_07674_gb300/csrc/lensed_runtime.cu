@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1056,4 +1057,104 @@ extern "C" int lensed_tuned_config(const lensed_model *m, char *buf, int buflen)
         snprintf(buf, (size_t)buflen, "%s%s", name, m->cfg_index < 0 ? " (default)" : "");
     }
     return m->cfg_index;
+}
+
+// ===========================================================================
+// Allocation-free evaluation (lensed_loglike_batch_noalloc)
+//
+// Its scratch is this file-scope device array.  In host code the symbol is
+// only a stand-in: the device address comes from cudaGetSymbolAddress, once
+// per device, with that device current.
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)32 << 20;  // 32 MiB
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void *g_static_ptr[256] = {nullptr};
+
+int static_scratch_address(void **out)
+{
+    int dev = 0;
+    CUDA_OK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(LENSED_E_UNSUPPORTED, "device index %d", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(LENSED_E_CUDA, "cudaGetSymbolAddress(static scratch): %s",
+                        cudaGetErrorString(e));
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return LENSED_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int lensed_loglike_batch_noalloc(lensed_model *m, const double *params, int P,
+                                            double *out_loglike, void *stream)
+{
+    int rc = loglike_args(m, params, P, out_loglike);
+    if (rc) return rc;
+    // carve the fixed array: constants, validity, partials, then as many
+    // points' pixel luminosities as fit
+    const size_t Pz = (size_t)P;
+    const size_t b_cf = align256(Pz * m->C_total * kNC * sizeof(float));
+    const size_t b_cd = align256(Pz * m->C_total * kNC * sizeof(double));
+    const size_t b_cv = align256(Pz * m->C_total);
+    const size_t b_v = align256(Pz * m->n_sys);
+    const size_t b_part = align256(Pz * std::max(m->T_total, 1) * sizeof(double));
+    const size_t fixed = b_cf + b_cd + b_cv + b_v + b_part;
+    const size_t per_point = (size_t)m->total_pix * m->elem();
+    if (fixed >= kStaticScratchBytes || (kStaticScratchBytes - fixed) / per_point < 1) {
+        const size_t per = (size_t)m->C_total * kNC * 12 + m->C_total + m->n_sys +
+                           (size_t)std::max(m->T_total, 1) * 8;
+        const size_t pmax = kStaticScratchBytes > per_point + 5 * 256
+                                ? (kStaticScratchBytes - per_point - 5 * 256) / per
+                                : 0;
+        return fail(LENSED_E_ARG,
+                    "P = %d needs more than the %zu bytes of fixed scratch of "
+                    "lensed_loglike_batch_noalloc (about %zu points fit for this model)",
+                    P, kStaticScratchBytes, pmax);
+    }
+    const int chunk = (int)std::min<size_t>(Pz, (kStaticScratchBytes - fixed) / per_point);
+    void *base = nullptr;
+    if ((rc = static_scratch_address(&base))) return rc;
+    unsigned char *b = (unsigned char *)base;
+    float *cf = (float *)b;
+    double *cd = (double *)(b + b_cf);
+    unsigned char *cvalid = b + b_cf + b_cd;
+    unsigned char *valid = cvalid + b_cv;
+    double *partial = (double *)(valid + b_v);
+    void *Lbuf = (unsigned char *)partial + b_part;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const LaunchCfg cfg = m->cfg();
+    launch_prologue(m->sys.p, m->comp_sys.p, 0, m->n_sys, 0, m->C_total, m->comp_type.p,
+                    m->comp_free.p, m->comp_value.p, params, false, P, 0, P, m->n_par_max,
+                    m->C_total, cf, cd, cvalid, valid, st);
+    for (int p0 = 0; p0 < P; p0 += chunk) {
+        const int nP = std::min(chunk, P - p0);
+        for (const TraceGroup &g : m->trace_groups)
+            launch_trace(m->precision, cfg, g.nn, m->sys.p, m->comp_type.p, m->comp_plane.p, cf,
+                         cd, valid, P, m->C_total, m->trace_blocks.p + g.off, g.count, m->need.p,
+                         m->nodes(), p0, nP, Lbuf, m->total_pix, st);
+        if (m->precision == LENSED_PREC_MIXED)
+            launch_fix64(cfg, m->sys.p, 0, m->n_sys, m->comp_type.p, m->comp_plane.p, cf, cd,
+                         valid, P, m->C_total, m->need.p, m->nodes(), p0, nP, Lbuf,
+                         m->total_pix, st);
+        for (const PsfGroup &g : m->psf_groups)
+            launch_psf(m->precision, g.q, g.p_max, m->sys.p, m->psf_f.p, m->psf_d.p, m->data.p,
+                       m->weight.p, m->data_d.p, m->weight_d.p, valid, P,
+                       m->psf_blocks.p + g.off, g.count, p0, nP, Lbuf, m->total_pix, partial,
+                       m->T_total, nullptr, st);
+    }
+    launch_finalize(m->sys.p, valid, P, partial, m->T_total, out_loglike, 0, 0, m->n_sys, P, st);
+    CUDA_OK(cudaGetLastError());
+    return LENSED_OK;
 }

@@ -151,6 +151,13 @@ class Model:
     def loglike_batch(self, params, out=None, stream=None):
         return self._loglike(N.lib().lensed_loglike_batch, params, out, stream)
 
+    def loglike_batch_noalloc(self, params, out=None, stream=None):
+        """loglike_batch without any device allocation by the library (its
+        scratch is a fixed array inside the library; see include/lensed.h).
+        params and out must already be device tensors to allocate nothing
+        on this side either."""
+        return self._loglike(N.lib().lensed_loglike_batch_noalloc, params, out, stream)
+
     def loglike_plain(self, params, out=None, stream=None):
         return self._loglike(N.lib().lensed_loglike_plain, params, out, stream)
 
