@@ -36,6 +36,12 @@ import numpy as np  # noqa: E402
 POINTS = 4096
 METRIC = "likelihood evals/s and Grays/s, batched vs plain on one GB300, at |dlogL|<=1e-3"
 WORKLOAD = "hst_200x200_h0.05_sie_shear_devauc_sersic_psf21_annulus_gl5x5_4096pts_11par"
+# other workloads (parity cases; --workload): points per system per step
+WORKLOADS = {
+    "c2": (WORKLOAD, POINTS),
+    "c1": ("single_64x64_h0.05_sie_shear_sersic_psf7_gl5x5_1000pts_13par", 1000),
+    "c3": ("uneven_256systems_48-320px_gl3-7_psf7-31_512pts_each", 512),
+}
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_SM_MHZ = 2070.0
 SMS = 152
@@ -53,6 +59,8 @@ def parse():
                     help="points per step (profiling of small cases only; the benchmark "
                          "workload is 4096)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-point pass")
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
+                    help="c2 (default, the benchmark), c1 or c3 (other configurations)")
     return ap.parse_args()
 
 
@@ -191,19 +199,29 @@ def main():
     torch.cuda.set_device(local)
     build_lib()
 
-    spec = W.c2_hst()
+    wname, default_pts = WORKLOADS[args.workload]
+    if args.workload == "c3":
+        specs = W.c3_batch(256)
+    else:
+        specs = [W.c2_hst() if args.workload == "c2" else W.c1_small()]
     # observation: the library's own noiseless render at the truth + seeded noise
-    probe = LZ.Model(spec, {"data": np.zeros((spec["ny"], spec["nx"])),
-                            "variance": np.ones((spec["ny"], spec["nx"]))},
-                     precision=args.precision)
-    noiseless = probe.render(0, np.asarray(spec["truth"]), convolved=True).double().cpu().numpy()
-    probe.close()
-    obs = W.add_noise(spec, noiseless, spec["seed"])
-    m = LZ.Model(spec, obs, precision=args.precision)
-    npts = args.points
-    pts = W.draw_points(spec, npts, 4242 + rank)
+    obs = []
+    for spec in specs:
+        probe = LZ.Model(spec, {"data": np.zeros((spec["ny"], spec["nx"])),
+                                "variance": np.ones((spec["ny"], spec["nx"]))},
+                         precision=args.precision)
+        noiseless = probe.render(0, np.asarray(spec["truth"]),
+                                 convolved=True).double().cpu().numpy()
+        probe.close()
+        obs.append(W.add_noise(spec, noiseless, spec["seed"]))
+    m = LZ.Model(specs, obs, precision=args.precision)
+    npts = args.points if args.points != POINTS or args.workload == "c2" else default_pts
+    pts = np.zeros((len(specs), npts, m.n_params_max))
+    for s_, spec in enumerate(specs):
+        pts[s_, :, :spec["n_params"]] = W.draw_points(spec, npts, 4242 + rank + 7919 * s_)
     params = m.pack_params(pts)
-    out = torch.empty((1, npts), dtype=torch.float64, device="cuda")
+    n_sys = len(specs)
+    out = torch.empty((n_sys, npts), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -273,7 +291,7 @@ def main():
     # ---- end to end through the host-buffer C call (copies inside)
     host_params = torch.empty(params.shape, dtype=torch.float64).pin_memory()
     host_params.copy_(params.cpu())
-    host_out = torch.empty((1, npts), dtype=torch.float64).pin_memory()
+    host_out = torch.empty((n_sys, npts), dtype=torch.float64).pin_memory()
     for _ in range(3):
         m.loglike_batch_host(host_params, host_out, stream=stream)
     k_e2e = max(10, args.steps // 2)
@@ -291,15 +309,15 @@ def main():
         return 0
 
     ms_step = dev_ms / args.steps
-    evals_s = world * npts / (ms_step * 1e-3)
-    rays_traced = m.rays_per_eval_traced
-    grays = evals_s * rays_traced / 1e9
+    evals_step = n_sys * npts
+    evals_s = world * evals_step / (ms_step * 1e-3)
+    rays_traced = m.rays_per_eval_traced  # summed over the systems, per point index
+    grays = world * npts * rays_traced / (ms_step * 1e-3) / 1e9
     pk, pk_src = peaks()
     sm_mhz_peak = float(pk.get("sm_max_mhz", FALLBACK_SM_MHZ))
     fp32_peak = SMS * 128 * 2 * sm_mhz_peak * 1e6 / 1e12  # TFLOP/s, FMA = 2
     trace_ms = stage_ms["trace"] / max(trace_launches, 1)
-    pts_per_launch = npts / max(trace_launches, 1)
-    flops_launch = pts_per_launch * rays_traced * m.flops_per_ray
+    flops_launch = npts / max(trace_launches, 1) * rays_traced * m.flops_per_ray
     achieved = flops_launch / (trace_ms * 1e-3) / 1e12
     line = {
         "metric": METRIC,
@@ -307,21 +325,24 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if npts == POINTS else f"{WORKLOAD} (profiling case: {npts} points)",
-                   "points_per_step": npts, "image": "200x200",
-                   "rule": "gauss-legendre 5x5", "psf": "21x21", "precision_mode": args.precision,
+        "config": {"workload": wname if npts == default_pts else f"{wname} (profiling case: {npts} points)",
+                   "points_per_step": evals_step, "systems": n_sys,
+                   "image": "200x200" if args.workload == "c2" else ("64x64" if args.workload == "c1" else "48-320 px"),
+                   "rule": "gauss-legendre 5x5" if args.workload != "c3" else "gauss-legendre 3x3..7x7",
+                   "psf": {"c2": "21x21", "c1": "7x7", "c3": "7x7..31x31"}[args.workload],
+                   "precision_mode": args.precision,
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"independent points per rank x{world}",
                    "tuned": tuned[1], "chunk_points": chunk},
         "grays_per_s": grays,
-        "rays_per_eval_traced": rays_traced,
+        "traced_rays_per_step": npts * rays_traced,
         "plain": None if plain_ms is None else {
-            "evals_per_s": world * npts / (plain_ms * 1e-3),
+            "evals_per_s": world * evals_step / (plain_ms * 1e-3),
             "grays_per_s": world * npts / (plain_ms * 1e-3) * rays_traced / 1e9,
             "speedup_batched_vs_plain": plain_ms / ms_step,
             "bit_identical_to_batched": bit_equal},
         "stage_ms": stage_ms,
-        "e2e": {"value": world * npts / e2e_s, "unit": "evals/s",
+        "e2e": {"value": world * evals_step / e2e_s, "unit": "evals/s",
                 "h2d_bytes_per_step": int(host_params.numel() * 8),
                 "d2h_bytes_per_step": int(host_out.numel() * 8)},
         "gpu_launches": launches * args.steps,
@@ -335,7 +356,8 @@ def main():
         "clocks": clocks,
         "loglike_finite_frac": float(np.isfinite(ll).mean()),
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and n_sys == 1:
+        spec = specs[0]
         cb, obs_o, pts_o, ref = cpu_baseline(spec)
         mo = LZ.Model(spec, obs_o, precision=args.precision)
         g = mo.loglike_batch(pts_o).cpu().numpy()[0]

@@ -8,6 +8,6 @@ __all__ = ["build", "lensed"]
 
 
 def build(force=False):
-    from .build import build as _build
+    from ._build import build as _build
 
     return _build(force=force)

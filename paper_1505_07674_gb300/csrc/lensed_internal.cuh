@@ -36,6 +36,12 @@ constexpr double kMixedCoreFactor = 2.0;
 // Series in e replaces atan/atanh below this (both precisions).
 constexpr double kSeriesE = 1e-3;
 
+// Sersic b_n table: piecewise Chebyshev series in log n over
+// [kBnMin, kBnMax], kBnSeg segments of degree kBnDeg (relative error ~3e-15);
+// outside that range the prologue solves for b_n by Newton.
+constexpr double kBnMin = 0.2, kBnMax = 12.0;
+constexpr int kBnSeg = 32, kBnDeg = 12;
+
 struct SysDev {
     int nx, ny, npix;
     float h, h_lo;       // pixel side as a float pair (h ~ h + h_lo)
@@ -90,8 +96,8 @@ struct LaunchCfg {
 void launch_prologue(const SysDev *sys, const int *comp_sys, int s0, int nS, int c0, int nC,
                      const int *comp_type, const int *comp_free, const double *comp_value,
                      const double *params, bool single_row, int P, int p0, int nP,
-                     int n_par_stride, int C_total, float *cf, double *cd, unsigned char *cvalid,
-                     unsigned char *valid, cudaStream_t st);
+                     int n_par_stride, int C_total, const double *bn_table, float *cf,
+                     double *cd, unsigned char *cvalid, unsigned char *valid, cudaStream_t st);
 
 // a2-a5: pixel luminosities of the pixels in the block table, for points
 // p0 .. p0 + nP - 1, into Lbuf[(p - p0) * L_stride + pix_off + pix].  Every

@@ -91,6 +91,28 @@ __device__ double sersic_b(double n)
     return b;
 }
 
+// b_n from the Chebyshev table when n lies in its range, else by Newton.
+__device__ double sersic_b_lookup(double n, const double *__restrict__ table)
+{
+    if (table && n >= kBnMin && n <= kBnMax) {
+        const double l0 = log(kBnMin), dl = (log(kBnMax) - l0) / kBnSeg;
+        const double ln = log(n);
+        const int k = min(max((int)((ln - l0) / dl), 0), kBnSeg - 1);
+        const double lo = l0 + k * dl;
+        const double t = (2.0 * (ln - lo) - dl) / dl;  // [-1, 1]
+        const double *c = table + k * (kBnDeg + 1);
+        // Clenshaw
+        double b1 = 0.0, b2 = 0.0;
+        for (int j = kBnDeg; j >= 1; --j) {
+            const double b0 = 2.0 * t * b1 - b2 + c[j];
+            b2 = b1;
+            b1 = b0;
+        }
+        return t * b1 - b2 + c[0];
+    }
+    return sersic_b(n);
+}
+
 // One thread per (point, component): resolve the component's parameters,
 // check its domain and write its packed constants and a validity byte.
 __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__restrict__ comp_sys,
@@ -98,7 +120,8 @@ __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__res
                                 const int *__restrict__ comp_free,
                                 const double *__restrict__ comp_value,
                                 const double *__restrict__ params, int single_row, int P, int p0,
-                                int nP, int n_par_stride, int C_total, float *__restrict__ cf,
+                                int nP, int n_par_stride, int C_total,
+                                const double *__restrict__ bn_table, float *__restrict__ cf,
                                 double *__restrict__ cd, unsigned char *__restrict__ cvalid)
 {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -202,7 +225,7 @@ __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__res
             o[13] = F / (M_PI * r2) * hd * hd;
             o[15] = kKindGauss;
         } else if (ok) {
-            const double bn = sersic_b(n);
+            const double bn = sersic_b_lookup(n, bn_table);
             // I_0 = F b^(2n) / (2 pi n r^2 Gamma(2n)), in logs
             const double lI0 = log(F) + 2.0 * n * log(bn) - log(2.0 * M_PI * n * r * r) -
                                lgamma(2.0 * n);
@@ -247,14 +270,14 @@ __global__ void k_prologue_valid(const SysDev *__restrict__ sys, int s0, int nS,
 void launch_prologue(const SysDev *sys, const int *comp_sys, int s0, int nS, int c0, int nC,
                      const int *comp_type, const int *comp_free, const double *comp_value,
                      const double *params, bool single_row, int P, int p0, int nP,
-                     int n_par_stride, int C_total, float *cf, double *cd, unsigned char *cvalid,
-                     unsigned char *valid, cudaStream_t st)
+                     int n_par_stride, int C_total, const double *bn_table, float *cf,
+                     double *cd, unsigned char *cvalid, unsigned char *valid, cudaStream_t st)
 {
     const long long n = (long long)nC * nP;
     const int threads = 64;
     k_prologue_comp<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
         sys, comp_sys, c0, nC, comp_type, comp_free, comp_value, params, single_row ? 1 : 0, P,
-        p0, nP, n_par_stride, C_total, cf, cd, cvalid);
+        p0, nP, n_par_stride, C_total, bn_table, cf, cd, cvalid);
     const long long n2 = (long long)nS * nP;
     k_prologue_valid<<<(unsigned)((n2 + 127) / 128), 128, 0, st>>>(sys, s0, nS, P, p0, nP,
                                                                     C_total, cvalid, valid);

@@ -127,6 +127,65 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
     if (n % 2 == 1) x[n / 2] = 0.0;
 }
 
+// Regularised lower incomplete gamma P(a, x) by its power series, long
+// double, summed as one fraction (host side, for the b_n table).
+long double host_gamma_p(long double a, long double x)
+{
+    if (x <= 0) return 0;
+    long double N = 1, D = 1, xk = 1;
+    for (int k = 1; k < 2000; ++k) {
+        const long double f = a + k;
+        xk *= x;
+        N = N * f + xk;
+        D *= f;
+        if (xk < 1e-21L * N) break;
+        if (D > 1e300L) {
+            N *= 1e-300L;
+            D *= 1e-300L;
+            xk *= 1e-300L;
+        }
+    }
+    return expl(a * logl(x) - x - lgammal(a + 1)) * (N / D);
+}
+
+// Sersic b_n (root of P(2n, b) = 1/2) by bisection in long double.
+double host_sersic_b(double n)
+{
+    long double lo = 0, hi = 2.0L * n;
+    for (int it = 0; it < 200; ++it) {
+        const long double mid = 0.5L * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (host_gamma_p(2.0L * n, mid) < 0.5L) lo = mid;
+        else hi = mid;
+    }
+    return (double)(0.5L * (lo + hi));
+}
+
+// Piecewise Chebyshev coefficients of b_n in log n (kBnSeg segments of
+// degree kBnDeg over [kBnMin, kBnMax]), from values at the Chebyshev points.
+std::vector<double> build_bn_table()
+{
+    std::vector<double> tab(kBnSeg * (kBnDeg + 1));
+    const double l0 = log(kBnMin), dl = (log(kBnMax) - l0) / kBnSeg;
+    const int N = kBnDeg + 1;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int k = 0; k < kBnSeg; ++k) {
+        std::vector<long double> f(N);
+        for (int i = 0; i < N; ++i) {
+            const long double t = cosl(pi * (i + 0.5L) / N);
+            f[i] = host_sersic_b((double)expl(l0 + dl * (k + 0.5L * (t + 1))));
+        }
+        for (int j = 0; j < N; ++j) {
+            long double c = 0;
+            for (int i = 0; i < N; ++i) c += f[i] * cosl(pi * j * (i + 0.5L) / N);
+            c *= 2.0L / N;
+            if (j == 0) c *= 0.5L;
+            tab[k * N + j] = (double)c;
+        }
+    }
+    return tab;
+}
+
 // 1-D rule on the unit pixel: offsets t in (-1/2, 1/2), weights summing to 1.
 bool rule_nodes(int rule, int order, std::vector<double> &t, std::vector<double> &wt)
 {
@@ -250,6 +309,7 @@ struct lensed_model {
     DevBuf<float> node_u, node_w;
     DevBuf<double> node_ud, node_wd;
     DevBuf<int> need;
+    DevBuf<double> bn_table;
 
     // chi^2 PSF blocks (grouped by q, systems contiguous) and render tables
     std::vector<PsfBlock> psf_blocks_h;
@@ -398,7 +458,7 @@ void enqueue_batch(lensed_model *m, const double *params, int P, double *out, La
     if (tm) tm->begin(0);
     launch_prologue(m->sys.p, m->comp_sys.p, 0, m->n_sys, 0, m->C_total, m->comp_type.p,
                     m->comp_free.p, m->comp_value.p, params, false, P, 0, P, m->n_par_max,
-                    m->C_total, m->cf.p, m->cd.p, m->cvalid.p, m->valid.p, st);
+                    m->C_total, m->bn_table.p, m->cf.p, m->cd.p, m->cvalid.p, m->valid.p, st);
     if (tm) tm->end();
     for (int p0 = 0; p0 < P; p0 += m->chunk_P) {
         const int nP = std::min(m->chunk_P, P - p0);
@@ -744,7 +804,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         (rc = m->psf_d.upload(psf_d)) || (rc = m->node_u.upload(node_u)) ||
         (rc = m->node_w.upload(node_w)) || (rc = m->node_ud.upload(node_ud)) ||
         (rc = m->node_wd.upload(node_wd)) || (rc = m->need.upload(need)) ||
-        (rc = m->psf_blocks.upload(m->psf_blocks_h)) ||
+        (rc = m->psf_blocks.upload(m->psf_blocks_h)) || (rc = m->bn_table.upload(build_bn_table())) ||
         (rc = m->render_psf.upload(m->render_psf_h))) {
         std::string msg = g_last_error;
         delete m;
@@ -819,7 +879,7 @@ extern "C" int lensed_render(lensed_model *m, int system, const double *params, 
     // one point: consts at p = 0, valid at index system (P = 1)
     launch_prologue(m->sys.p, m->comp_sys.p, system, 1, S.comp_off, S.ncomp, m->comp_type.p,
                     m->comp_free.p, m->comp_value.p, params, true, 1, 0, 1, m->n_par_max,
-                    m->C_total, m->rcf.p, m->rcd.p, m->rcvalid.p, m->rvalid.p, st);
+                    m->C_total, m->bn_table.p, m->rcf.p, m->rcd.p, m->rcvalid.p, m->rvalid.p, st);
     launch_trace(m->precision, m->cfg(), m->n_nodes[system], m->sys.p, m->comp_type.p,
                  m->comp_plane.p, m->rcf.p,
                  m->rcd.p, m->rvalid.p, 1, m->C_total,
@@ -919,8 +979,8 @@ extern "C" int lensed_loglike_plain(lensed_model *m, const double *params, int P
         for (int p = 0; p < P; ++p) {
             launch_prologue(m->sys.p, m->comp_sys.p, s, 1, m->sys_h[s].comp_off,
                             m->sys_h[s].ncomp, m->comp_type.p, m->comp_free.p, m->comp_value.p,
-                            params, false, P, p, 1, m->n_par_max, m->C_total, m->cf.p, m->cd.p,
-                            m->cvalid.p, m->valid.p, st);
+                            params, false, P, p, 1, m->n_par_max, m->C_total, m->bn_table.p,
+                            m->cf.p, m->cd.p, m->cvalid.p, m->valid.p, st);
             launch_trace(m->precision, cfg, m->n_nodes[s], m->sys.p, m->comp_type.p,
                          m->comp_plane.p, m->cf.p,
                          m->cd.p, m->valid.p, P, m->C_total,
@@ -1137,7 +1197,7 @@ extern "C" int lensed_loglike_batch_noalloc(lensed_model *m, const double *param
     const LaunchCfg cfg = m->cfg();
     launch_prologue(m->sys.p, m->comp_sys.p, 0, m->n_sys, 0, m->C_total, m->comp_type.p,
                     m->comp_free.p, m->comp_value.p, params, false, P, 0, P, m->n_par_max,
-                    m->C_total, cf, cd, cvalid, valid, st);
+                    m->C_total, m->bn_table.p, cf, cd, cvalid, valid, st);
     for (int p0 = 0; p0 < P; p0 += chunk) {
         const int nP = std::min(chunk, P - p0);
         for (const TraceGroup &g : m->trace_groups)
