@@ -839,6 +839,10 @@ static __host__ __device__ __forceinline__ int psf_row_stride(int q)
     return (kTileW + 2 * q + 3) & ~3;
 }
 
+// Row stride of the staged PSF: 2q+1 taps rounded up to a multiple of 4 so
+// each row starts 16-byte aligned.
+static __host__ __device__ __forceinline__ int psf_tap_stride(int q) { return (2 * q + 1 + 3) & ~3; }
+
 template <typename T, int Q>
 __global__ void __launch_bounds__(kPsfThreads)
     k_psf(const SysDev *__restrict__ sys, const T *__restrict__ psf,
@@ -850,6 +854,7 @@ __global__ void __launch_bounds__(kPsfThreads)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s_L = reinterpret_cast<T *>(smem_raw);
     constexpr int W = 2 * Q + 1;
+    constexpr int WS = (W + 3) & ~3;  // padded tap row
     const PsfBlock pb = blocks[blockIdx.x];
     const int p = p0 + blockIdx.y;
     const SysDev &S = sys[pb.sys];
@@ -871,8 +876,12 @@ __global__ void __launch_bounds__(kPsfThreads)
         return;
     }
 
-    // stage the flipped, normalised PSF and the clamped tile + halo
-    for (int k = threadIdx.x; k < (2 * Ph + 1) * W; k += blockDim.x) s_F[k] = psf[S.psf_off + k];
+    // stage the flipped, normalised PSF (rows padded to WS) and the clamped
+    // tile + halo
+    for (int k = threadIdx.x; k < (2 * Ph + 1) * WS; k += blockDim.x) {
+        const int r = k / WS, c = k - (k / WS) * WS;
+        s_F[k] = c < W ? psf[S.psf_off + r * W + c] : T(0);
+    }
     const T *L = Lbuf + (size_t)(p - p0) * L_stride + S.pix_off;
     const int cols = kTileW + 2 * Q;
     for (int k = threadIdx.x; k < rows * cols; k += blockDim.x) {
@@ -883,10 +892,13 @@ __global__ void __launch_bounds__(kPsfThreads)
     }
     __syncthreads();
 
-    const int tc = threadIdx.x % (kTileW / kOutPerThread);
-    const int tr = threadIdx.x / (kTileW / kOutPerThread);
+    // each warp owns a 16 x 16 block of outputs (the tile is 2 x 4 warps);
+    // each lane 8 consecutive outputs of one row
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tr = (warp >> 2) * 16 + (lane >> 1);
+    const int tcol = (warp & 3) * 16 + (lane & 1) * kOutPerThread;
     const int i = pb.i0 + tr;
-    const int jb = pb.j0 + tc * kOutPerThread;
+    const int jb = pb.j0 + tcol;
     // chi^2 mode: a warp none of whose outputs carries weight skips the
     // convolution (its partial is zero)
     bool live = true;
@@ -901,10 +913,10 @@ __global__ void __launch_bounds__(kPsfThreads)
 #pragma unroll
     for (int o = 0; o < kOutPerThread; ++o) acc[o] = T(0);
     for (int kk = 0; live && kk <= 2 * Ph; ++kk) {
-        T f[W];
+        T f[WS];
 #pragma unroll
-        for (int l = 0; l < W; ++l) f[l] = s_F[kk * W + l];
-        const T *srow = s_L + (tr + kk) * stride + tc * kOutPerThread;
+        for (int l = 0; l < WS; ++l) f[l] = s_F[kk * WS + l];
+        const T *srow = s_L + (tr + kk) * stride + tcol;
         T lv[kOutPerThread + 2 * Q];
 #pragma unroll
         for (int m = 0; m < kOutPerThread + 2 * Q; ++m) lv[m] = srow[m];
@@ -916,7 +928,7 @@ __global__ void __launch_bounds__(kPsfThreads)
 
     if (partial) {
         double chi = 0.0;
-        if (i < ny) {
+        if (live && i < ny) {
 #pragma unroll
             for (int o = 0; o < kOutPerThread; ++o) {
                 const int j = jb + o;
@@ -924,8 +936,10 @@ __global__ void __launch_bounds__(kPsfThreads)
                     const size_t pix = S.pix_off + (size_t)i * nx + j;
                     const T w = weight[pix];
                     if (w > T(0)) {
+                        // one product per pixel in the working precision,
+                        // accumulated in FP64
                         const T r = data[pix] - acc[o];
-                        chi += (double)w * ((double)r * (double)r);
+                        chi += (double)(w * r * r);
                     }
                 }
             }
@@ -933,7 +947,7 @@ __global__ void __launch_bounds__(kPsfThreads)
         // warp-shuffle tree, then across the 8 warps in fixed order
         __shared__ double s_red[kPsfThreads / 32];
         chi = warp_sum(chi);
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = chi;
+        if (lane == 0) s_red[warp] = chi;
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
@@ -949,24 +963,11 @@ __global__ void __launch_bounds__(kPsfThreads)
     }
 }
 
-template <typename T, int Q>
-static void psf_launch_t(int p_max, const SysDev *sys, const T *psf, const T *data,
-                         const T *weight, const unsigned char *valid, int P,
-                         const PsfBlock *blocks, int n_blocks, int p0, int nP, const T *Lbuf,
-                         long long L_stride, double *partial, int T_total, float *out,
-                         cudaStream_t st)
-{
-    const size_t smem = ((size_t)(kTileH + 2 * p_max) * psf_row_stride(Q) +
-                         (size_t)(2 * p_max + 1) * (2 * Q + 1)) * sizeof(T);
-    dim3 grid((unsigned)n_blocks, (unsigned)nP);
-    k_psf<T, Q><<<grid, kPsfThreads, smem, st>>>(sys, psf, data, weight, valid, P, blocks, p0,
-                                                  Lbuf, L_stride, partial, T_total, out);
-}
-
 // Largest dynamic shared memory a k_psf instance can ask for (Q = P = 15, FP64).
 static constexpr int kPsfSmemMax =
     ((kTileH + 2 * LENSED_MAX_PSF_HALF) * ((kTileW + 2 * LENSED_MAX_PSF_HALF + 3) & ~3) +
-     (2 * LENSED_MAX_PSF_HALF + 1) * (2 * LENSED_MAX_PSF_HALF + 1)) * (int)sizeof(double);
+     (2 * LENSED_MAX_PSF_HALF + 1) * ((2 * LENSED_MAX_PSF_HALF + 1 + 3) & ~3)) *
+    (int)sizeof(double);
 
 template <typename T, int Q>
 static void psf_attr_t()
@@ -984,6 +985,20 @@ void init_kernel_attributes()
 {
     psf_attr_all<float>(std::make_integer_sequence<int, LENSED_MAX_PSF_HALF + 1>{});
     psf_attr_all<double>(std::make_integer_sequence<int, LENSED_MAX_PSF_HALF + 1>{});
+}
+
+template <typename T, int Q>
+static void psf_launch_t(int p_max, const SysDev *sys, const T *psf, const T *data,
+                         const T *weight, const unsigned char *valid, int P,
+                         const PsfBlock *blocks, int n_blocks, int p0, int nP, const T *Lbuf,
+                         long long L_stride, double *partial, int T_total, float *out,
+                         cudaStream_t st)
+{
+    const size_t smem = ((size_t)(kTileH + 2 * p_max) * psf_row_stride(Q) +
+                         (size_t)(2 * p_max + 1) * psf_tap_stride(Q)) * sizeof(T);
+    dim3 grid((unsigned)n_blocks, (unsigned)nP);
+    k_psf<T, Q><<<grid, kPsfThreads, smem, st>>>(sys, psf, data, weight, valid, P, blocks, p0,
+                                                  Lbuf, L_stride, partial, T_total, out);
 }
 
 template <typename T>
