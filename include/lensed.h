@@ -96,7 +96,7 @@ enum { LENSED_RULE_POINT = 0, LENSED_RULE_SUB = 1, LENSED_RULE_GL = 2 };
  *   LENSED_PREC_FP32   rays, brightness and PSF in FP32; chi^2 summed in FP64
  *   LENSED_PREC_MIXED  as FP32, but the SIE deflection is evaluated in FP64
  *                      for axis ratios close to 1 (e = sqrt(1-q^2) < 0.05)
- *                      and for rays close to the core (psi < 4 s)
+ *                      and for rays within 2 s / q of the SIE centre
  *   LENSED_PREC_FP64   everything in FP64 (validation mode)              */
 enum { LENSED_PREC_FP32 = 0, LENSED_PREC_MIXED = 1, LENSED_PREC_FP64 = 2 };
 

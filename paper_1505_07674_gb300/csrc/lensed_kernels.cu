@@ -683,12 +683,14 @@ void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const
     }
 }
 
-// MIXED second pass.  One block per (system, point).  The pixels the MIXED
-// rule assigns to FP64 -- every listed pixel when an SIE of the point is
-// nearly round (e < 0.05), else the pixels whose square reaches within
-// 2 s / q of an SIE centre -- are recomputed ray by ray with that SIE in FP64
-// and every other component in FP32, overwriting the first pass.
-__device__ float pixel_mixed(const TraceSmem &sm, const SysDev &S, int pix, const bool *sie64)
+// MIXED second pass.  One block per (system, point).  The MIXED rule puts
+// the SIE in FP64 for every ray of a point whose SIE is nearly round
+// (e < 0.05), and otherwise for the rays within 2 s / q of an SIE centre.
+// The pixels holding such rays -- every listed pixel in the first case, the
+// pixels whose square reaches the disc in the second -- are recomputed ray by
+// ray (that SIE in FP64, every other component in FP32), overwriting the
+// first pass.
+__device__ float pixel_mixed(const TraceSmem &sm, const SysDev &S, int pix)
 {
     const int nn = S.nn, nx = S.nx, ncomp = S.ncomp;
     const int i = pix / nx, j = pix - (pix / nx) * nx;
@@ -709,7 +711,14 @@ __device__ float pixel_mixed(const TraceSmem &sm, const SysDev &S, int pix, cons
                 } else if (pl == LENSED_PLANE_LENS) {
                     const int t = sm.type[c];
                     if (t == LENSED_SIE) {
-                        if (sie64[c]) sie_ray_f64(jc, ic, S.hd, sm.ud[a], sm.ud[b], sm.cd + c * kNC, ax, ay);
+                        const double *cd = sm.cd + c * kNC;
+                        bool use64 = cd[17] != 0.0;
+                        if (!use64) {
+                            const double dx = (double)jc * S.hd + sm.ud[a] - cd[0];
+                            const double dy = (double)ic * S.hd + sm.ud[b] - cd[1];
+                            use64 = dx * dx + dy * dy < cd[18];
+                        }
+                        if (use64) sie_ray_f64(jc, ic, S.hd, sm.ud[a], sm.ud[b], cd, ax, ay);
                         else sie_f32(load_sie(cc), x, y, ax, ay);
                     } else if (t == LENSED_SHEAR) {
                         const float dx = x - cc[0], dy = y - cc[1];
@@ -763,18 +772,11 @@ __global__ void __launch_bounds__(128)
     bool whole = false;
     for (int c = 0; c < ncomp; ++c)
         if (sm.type[c] == LENSED_SIE && sm.cd[c * kNC + 17] != 0.0) whole = true;
-    bool sie64[LENSED_MAX_COMPONENTS];
     if (whole) {
         const int n = need ? S.n_need : S.npix;
         for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
             const int pix = need ? need[S.need_off + idx] : idx;
-            const int i = pix / nx, j = pix - (pix / nx) * nx;
-            for (int c = 0; c < ncomp; ++c) {
-                const double *cc = sm.cd + c * kNC;
-                sie64[c] = sm.type[c] == LENSED_SIE &&
-                           (cc[17] != 0.0 || pixel_near(S, i, j, cc[0], cc[1], cc[18]));
-            }
-            L[pix] = pixel_mixed(sm, S, pix, sie64);
+            L[pix] = pixel_mixed(sm, S, pix);
         }
         return;
     }
@@ -801,11 +803,7 @@ __global__ void __launch_bounds__(128)
                     earlier = true;
             }
             if (earlier) continue;
-            for (int c3 = 0; c3 < ncomp; ++c3) {
-                const double *c3c = sm.cd + c3 * kNC;
-                sie64[c3] = sm.type[c3] == LENSED_SIE && pixel_near(S, i, j, c3c[0], c3c[1], c3c[18]);
-            }
-            L[i * nx + j] = pixel_mixed(sm, S, i * nx + j, sie64);
+            L[i * nx + j] = pixel_mixed(sm, S, i * nx + j);
         }
     }
 }
