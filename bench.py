@@ -121,6 +121,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def trace_traffic(points_per_launch):
+    """DRAM bytes of one trace launch from the committed ncu record (a
+    512-point capture of the same kernel, scaled by points: its traffic is
+    the per-point luminosity writes and reads, proportional to points), or
+    None when the kernel source changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_trace_rows_traffic.json")
+    src = os.path.join(ROOT, "paper_1505_07674_gb300", "csrc", "lensed_kernels.cu")
+    try:
+        rec = json.load(open(path))
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_sha256") != digest:
+        return None
+    return rec["dram_bytes_per_point"] * points_per_launch
+
+
 def peaks():
     try:
         return json.load(open(MEASURED_PEAKS)), "measured"
@@ -347,7 +365,9 @@ def main():
                 "d2h_bytes_per_step": int(host_out.numel() * 8)},
         "gpu_launches": launches * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
+                     "frac": achieved / fp32_peak,
+                     "traffic": trace_traffic(npts / max(trace_launches, 1))
+                     if args.workload == "c2" else None,
                      "kernel": "k_trace (rays: Eqs. 1-3, 14)",
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz_peak:.0f} MHz "
                                     f"(sm_max_mhz, {pk_src})",

@@ -687,59 +687,53 @@ void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const
 // the SIE in FP64 for every ray of a point whose SIE is nearly round
 // (e < 0.05), and otherwise for the rays within 2 s / q of an SIE centre.
 // The pixels holding such rays -- every listed pixel in the first case, the
-// pixels whose square reaches the disc in the second -- are recomputed ray by
-// ray (that SIE in FP64, every other component in FP32), overwriting the
-// first pass.
-__device__ float pixel_mixed(const TraceSmem &sm, const SysDev &S, int pix)
+// pixels whose square reaches the disc in the second -- are recomputed (that
+// SIE in FP64, every other component in FP32) and overwrite the first pass.
+// Work is spread one thread per (pixel, ray); each pixel then sums its rays in
+// the fixed node order.
+
+// Brightness of ray (a, b) of pixel (i, j) under the MIXED rule.
+__device__ float ray_mixed(const TraceSmem &sm, const SysDev &S, int i, int j, int a, int b)
 {
-    const int nn = S.nn, nx = S.nx, ncomp = S.ncomp;
-    const int i = pix / nx, j = pix - (pix / nx) * nx;
+    const int ncomp = S.ncomp;
     const float jc = (float)j - S.cx, ic = (float)i - S.cy;
-    const float xc = fmaf(jc, S.h, jc * S.h_lo);
-    const float yc = fmaf(ic, S.h, ic * S.h_lo);
-    float acc = 0.f;
-    for (int b = 0; b < nn; ++b) {
-        const float y = yc + sm.u[b];
-        for (int a = 0; a < nn; ++a) {
-            const float x = xc + sm.u[a];
-            float I = 0.f, ax = 0.f, ay = 0.f;
-            for (int c = 0; c < ncomp; ++c) {
-                const int pl = sm.plane[c];
-                const float *cc = sm.cf + c * kNC;
-                if (pl == LENSED_PLANE_FOREGROUND) {
-                    I += light_f32(load_light(cc), x, y);
-                } else if (pl == LENSED_PLANE_LENS) {
-                    const int t = sm.type[c];
-                    if (t == LENSED_SIE) {
-                        const double *cd = sm.cd + c * kNC;
-                        bool use64 = cd[17] != 0.0;
-                        if (!use64) {
-                            const double dx = (double)jc * S.hd + sm.ud[a] - cd[0];
-                            const double dy = (double)ic * S.hd + sm.ud[b] - cd[1];
-                            use64 = dx * dx + dy * dy < cd[18];
-                        }
-                        if (use64) sie_ray_f64(jc, ic, S.hd, sm.ud[a], sm.ud[b], cd, ax, ay);
-                        else sie_f32(load_sie(cc), x, y, ax, ay);
-                    } else if (t == LENSED_SHEAR) {
-                        const float dx = x - cc[0], dy = y - cc[1];
-                        ax += fmaf(cc[2], dx, cc[3] * dy);
-                        ay += fmaf(cc[3], dx, -cc[2] * dy);
-                    } else {
-                        const float dx = x - cc[0], dy = y - cc[1];
-                        const float r2 = fmaf(dx, dx, dy * dy);
-                        const float f = r2 > 0.f ? __fdividef(cc[2], r2) : 0.f;
-                        ax = fmaf(f, dx, ax);
-                        ay = fmaf(f, dy, ay);
-                    }
+    const float x = fmaf(jc, S.h, jc * S.h_lo) + sm.u[a];
+    const float y = fmaf(ic, S.h, ic * S.h_lo) + sm.u[b];
+    float I = 0.f, ax = 0.f, ay = 0.f;
+    for (int c = 0; c < ncomp; ++c) {
+        const int pl = sm.plane[c];
+        const float *cc = sm.cf + c * kNC;
+        if (pl == LENSED_PLANE_FOREGROUND) {
+            I += light_f32(load_light(cc), x, y);
+        } else if (pl == LENSED_PLANE_LENS) {
+            const int t = sm.type[c];
+            if (t == LENSED_SIE) {
+                const double *cd = sm.cd + c * kNC;
+                bool use64 = cd[17] != 0.0;
+                if (!use64) {
+                    const double dx = (double)jc * S.hd + sm.ud[a] - cd[0];
+                    const double dy = (double)ic * S.hd + sm.ud[b] - cd[1];
+                    use64 = dx * dx + dy * dy < cd[18];
                 }
+                if (use64) sie_ray_f64(jc, ic, S.hd, sm.ud[a], sm.ud[b], cd, ax, ay);
+                else sie_f32(load_sie(cc), x, y, ax, ay);
+            } else if (t == LENSED_SHEAR) {
+                const float dx = x - cc[0], dy = y - cc[1];
+                ax += fmaf(cc[2], dx, cc[3] * dy);
+                ay += fmaf(cc[3], dx, -cc[2] * dy);
+            } else {
+                const float dx = x - cc[0], dy = y - cc[1];
+                const float r2 = fmaf(dx, dx, dy * dy);
+                const float f = r2 > 0.f ? __fdividef(cc[2], r2) : 0.f;
+                ax = fmaf(f, dx, ax);
+                ay = fmaf(f, dy, ay);
             }
-            for (int c = 0; c < ncomp; ++c)
-                if (sm.plane[c] == LENSED_PLANE_SOURCE)
-                    I += light_f32(load_light(sm.cf + c * kNC), x - ax, y - ay);
-            acc = fmaf(sm.w[b * nn + a], I, acc);
         }
     }
-    return acc;
+    for (int c = 0; c < ncomp; ++c)
+        if (sm.plane[c] == LENSED_PLANE_SOURCE)
+            I += light_f32(load_light(sm.cf + c * kNC), x - ax, y - ay);
+    return I;
 }
 
 // Does pixel (i, j)'s square reach within sqrt(r2) of (x0, y0)?
@@ -752,6 +746,31 @@ __device__ __forceinline__ bool pixel_near(const SysDev &S, int i, int j, double
     return dx * dx + dy * dy < r2;
 }
 
+constexpr int kFixRays = 1024;  // ray contributions staged per batch
+
+// Recompute the pixels of s_pix[0..n) (batches of kFixRays / (nn*nn)).
+__device__ void fix_pixels(const TraceSmem &sm, const SysDev &S, const int *s_pix, int n,
+                           float *s_ray, float *L)
+{
+    const int nn = S.nn, nr = nn * nn, nx = S.nx;
+    const int per = kFixRays / nr;
+    for (int b0 = 0; b0 < n; b0 += per) {
+        const int m = min(per, n - b0);
+        for (int t = threadIdx.x; t < m * nr; t += blockDim.x) {
+            const int pix = s_pix[b0 + t / nr], r = t % nr;
+            const int i = pix / nx, j = pix - (pix / nx) * nx;
+            s_ray[t] = ray_mixed(sm, S, i, j, r % nn, r / nn);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            float acc = 0.f;
+            for (int r = 0; r < nr; ++r) acc = fmaf(sm.w[r], s_ray[k * nr + r], acc);
+            L[s_pix[b0 + k]] = acc;
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(128)
     k_trace_fix64(const SysDev *__restrict__ sys, int s0, const int *__restrict__ comp_type,
                   const int *__restrict__ comp_plane, const float *__restrict__ cf,
@@ -760,6 +779,9 @@ __global__ void __launch_bounds__(128)
                   float *__restrict__ Lbuf, long long L_stride)
 {
     __shared__ __align__(16) TraceSmem sm;
+    __shared__ float s_ray[kFixRays];
+    __shared__ int s_pix[kFixRays];
+    __shared__ int s_n;
     const int s = s0 + blockIdx.x;
     const int p = p0 + blockIdx.y;
     if (!valid[(size_t)s * P + p]) return;
@@ -773,15 +795,19 @@ __global__ void __launch_bounds__(128)
     for (int c = 0; c < ncomp; ++c)
         if (sm.type[c] == LENSED_SIE && sm.cd[c * kNC + 17] != 0.0) whole = true;
     if (whole) {
+        // every listed pixel, in slices of kFixRays
         const int n = need ? S.n_need : S.npix;
-        for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-            const int pix = need ? need[S.need_off + idx] : idx;
-            L[pix] = pixel_mixed(sm, S, pix);
+        for (int q0 = 0; q0 < n; q0 += kFixRays) {
+            const int m = min(kFixRays, n - q0);
+            for (int k = threadIdx.x; k < m; k += blockDim.x)
+                s_pix[k] = need ? need[S.need_off + q0 + k] : q0 + k;
+            __syncthreads();
+            fix_pixels(sm, S, s_pix, m, s_ray, L);
         }
         return;
     }
-    // core boxes, one SIE after the other; a pixel already covered by an
-    // earlier SIE's box is skipped so every pixel is written once
+    // core discs, one SIE after the other; a pixel already covered by an
+    // earlier SIE's disc is skipped so every pixel is written once
     for (int c = 0; c < ncomp; ++c) {
         if (sm.type[c] != LENSED_SIE) continue;
         const double *cc = sm.cd + c * kNC;
@@ -792,18 +818,25 @@ __global__ void __launch_bounds__(128)
         const int i0 = max(0, (int)floor((cc[1] - r) / S.hd + S.cy - 1.0));
         const int i1 = min(ny - 1, (int)ceil((cc[1] + r) / S.hd + S.cy + 1.0));
         if (j1 < j0 || i1 < i0) continue;
-        const int bw = j1 - j0 + 1, n = bw * (i1 - i0 + 1);
-        for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
-            const int i = i0 + idx / bw, j = j0 + idx % bw;
-            if (!pixel_near(S, i, j, cc[0], cc[1], cc[18])) continue;
-            bool earlier = false;
-            for (int c2 = 0; c2 < c; ++c2) {
-                const double *c2c = sm.cd + c2 * kNC;
-                if (sm.type[c2] == LENSED_SIE && pixel_near(S, i, j, c2c[0], c2c[1], c2c[18]))
-                    earlier = true;
+        const int bw = j1 - j0 + 1, nbox = bw * (i1 - i0 + 1);
+        for (int q0 = 0; q0 < nbox; q0 += kFixRays) {
+            if (threadIdx.x == 0) s_n = 0;
+            __syncthreads();
+            for (int idx = q0 + threadIdx.x; idx < min(nbox, q0 + kFixRays); idx += blockDim.x) {
+                const int i = i0 + idx / bw, j = j0 + idx % bw;
+                if (!pixel_near(S, i, j, cc[0], cc[1], cc[18])) continue;
+                bool earlier = false;
+                for (int c2 = 0; c2 < c; ++c2) {
+                    const double *c2c = sm.cd + c2 * kNC;
+                    if (sm.type[c2] == LENSED_SIE && pixel_near(S, i, j, c2c[0], c2c[1], c2c[18]))
+                        earlier = true;
+                }
+                if (!earlier) s_pix[atomicAdd(&s_n, 1)] = i * nx + j;
             }
-            if (earlier) continue;
-            L[i * nx + j] = pixel_mixed(sm, S, i * nx + j);
+            __syncthreads();
+            const int n = s_n;
+            __syncthreads();
+            fix_pixels(sm, S, s_pix, n, s_ray, L);
         }
     }
 }
