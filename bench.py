@@ -127,7 +127,7 @@ def trace_traffic(points_per_launch):
     the per-point luminosity writes and reads, proportional to points), or
     None when the kernel source changed since that capture."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_trace_rows_traffic.json")
+    path = os.path.join(ROOT, "profiles", "k_trace_rows_traffic.txt")
     src = os.path.join(ROOT, "paper_1505_07674_gb300", "csrc", "lensed_kernels.cu")
     try:
         rec = json.load(open(path))
