@@ -257,6 +257,42 @@ int lensed_batch_plan(lensed_model *m, int P, int *launches, int *chunk_points);
 int lensed_profile_batch(lensed_model *m, const double *params, int P, double *out_loglike,
                          void *stream, double *stage_ms, int *trace_launches);
 
+/* ------------------------------------------------------------------------
+ * Log-likelihood surrogate network (the paper has no counterpart; the
+ * sampling driver uses it to pre-screen proposals, and the exact likelihood
+ * judges every point it accepts):
+ *     h1 = silu(x W1^T + b1), h2 = silu(h1 W2^T + b2), h3 = silu(h2 W3^T + b3),
+ *     y  = h3 . w4 + b4,   loss = mean over the batch of (y - t)^2 / 2.
+ * BF16 weights and activations on the tensor cores, FP32 accumulation, FP32
+ * master weights with Adam (beta 0.9 / 0.999, eps 1e-8).  Flat parameter
+ * order: W1 [H][n_in], b1 [H], W2 [H][H], b2 [H], W3 [H][H], b3 [H], w4 [H],
+ * b4 [1], each W stored [out][in].  Inputs X are row-major [B][n_in] FP32
+ * DEVICE arrays (the caller normalises them); targets t and outputs y are
+ * [B] FP32 DEVICE arrays.  Errors: status codes, message from
+ * lensed_mlp_last_error(). */
+typedef struct lensed_mlp lensed_mlp;
+
+/* n_in 1..64, hidden a multiple of 64, max_batch >= 1 (largest B of a
+ * gradient or training call; forward calls of any B run in slices of it).
+ * Parameters start at zero: set them with lensed_mlp_set_params. */
+int lensed_mlp_create(int n_in, int hidden, int max_batch, lensed_mlp **out);
+void lensed_mlp_destroy(lensed_mlp *m);                       /* NULL-safe */
+long long lensed_mlp_param_count(const lensed_mlp *m);
+/* HOST arrays of lensed_mlp_param_count floats; setting resets Adam. */
+int lensed_mlp_set_params(lensed_mlp *m, const float *host_params);
+int lensed_mlp_get_params(const lensed_mlp *m, float *host_params);
+/* y[0..B) = network(X[0..B)); asynchronous on stream. */
+int lensed_mlp_forward(lensed_mlp *m, const float *X, int B, float *y, void *stream);
+/* Loss (DEVICE scalar) and its gradient (DEVICE [param_count]) on one batch,
+ * B <= max_batch; asynchronous. */
+int lensed_mlp_gradient(lensed_mlp *m, const float *X, const float *t, int B, float *grad,
+                        float *loss, void *stream);
+/* One Adam step on one batch (B <= max_batch); writes the batch loss before
+ * the step to the DEVICE scalar loss; asynchronous. */
+int lensed_mlp_train_step(lensed_mlp *m, const float *X, const float *t, int B, float lr,
+                          float *loss, void *stream);
+const char *lensed_mlp_last_error(void);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char *lensed_last_error(void);
 

@@ -26,7 +26,10 @@ MAX_COMPONENT_PARAMS = 8
 EXPORTS = ("lensed_create_model", "lensed_destroy", "lensed_model_info_get", "lensed_render",
            "lensed_loglike_batch", "lensed_loglike_plain", "lensed_loglike_batch_host",
            "lensed_autotune", "lensed_tuned_config", "lensed_last_error", "lensed_batch_plan",
-           "lensed_profile_batch", "lensed_loglike_batch_noalloc")
+           "lensed_profile_batch", "lensed_loglike_batch_noalloc",
+           "lensed_mlp_create", "lensed_mlp_destroy", "lensed_mlp_param_count",
+           "lensed_mlp_set_params", "lensed_mlp_get_params", "lensed_mlp_forward",
+           "lensed_mlp_gradient", "lensed_mlp_train_step", "lensed_mlp_last_error")
 
 
 class Component(C.Structure):
@@ -82,6 +85,18 @@ def lib():
         L.lensed_tuned_config.argtypes = [vp, C.c_char_p, C.c_int]
         L.lensed_batch_plan.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.lensed_profile_batch.argtypes = [vp, vp, C.c_int, vp, vp, dp, C.POINTER(C.c_int)]
+        L.lensed_mlp_create.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(vp)]
+        L.lensed_mlp_destroy.argtypes = [vp]
+        L.lensed_mlp_destroy.restype = None
+        L.lensed_mlp_param_count.argtypes = [vp]
+        L.lensed_mlp_param_count.restype = C.c_longlong
+        L.lensed_mlp_set_params.argtypes = [vp, vp]
+        L.lensed_mlp_get_params.argtypes = [vp, vp]
+        L.lensed_mlp_forward.argtypes = [vp, vp, C.c_int, vp, vp]
+        L.lensed_mlp_gradient.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp]
+        L.lensed_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, vp, vp]
+        L.lensed_mlp_last_error.restype = C.c_char_p
+        L.lensed_mlp_last_error.argtypes = []
         L.lensed_last_error.restype = C.c_char_p
         L.lensed_last_error.argtypes = []
         _lib = L
@@ -91,4 +106,10 @@ def lib():
 def check(rc):
     if rc != LENSED_OK:
         raise LensedError(rc, lib().lensed_last_error().decode())
+    return rc
+
+
+def check_mlp(rc):
+    if rc != LENSED_OK:
+        raise LensedError(rc, lib().lensed_mlp_last_error().decode())
     return rc

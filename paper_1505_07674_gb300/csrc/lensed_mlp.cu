@@ -1,0 +1,580 @@
+// Log-likelihood surrogate network: BF16 tensor-core training and inference.
+//
+//   h1 = silu(x W1^T + b1), h2 = silu(h1 W2^T + b2), h3 = silu(h2 W3^T + b3),
+//   y = h3 . w4 + b4;  loss = mean((y - t)^2) / 2.
+//
+// The likelihood driver uses it to pre-screen nested-sampling proposals; the
+// exact likelihood judges every accepted point.  The paper has no such
+// component.
+//
+// Every matrix product runs through k_gemm: C[M][N] = A[M][K] B[N][K]^T with
+// BF16 operands staged in shared memory by cp.async (double-buffered, 64 x 64
+// output tile per 128-thread block, 32 x 32 per warp) and multiplied by
+// mma.sync m16n8k16 (FP32 accumulators), with fused epilogues: bias + SiLU
+// (forward), times SiLU'(z) (backward), or plain FP32.  Gradients of the
+// weights are products over the batch, so the batch-major activations and
+// output gradients are transposed (k_transpose) to make the batch the
+// contraction axis.  Reductions (bias gradients, output layer, loss) run in a
+// fixed order, so a training step is deterministic.  Adam keeps FP32 master
+// weights and refreshes the BF16 copies after each step.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "lensed.h"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int BM = 64, BN = 64, BK = 32, PADK = BK + 8;
+
+thread_local std::string g_mlp_error;
+
+int mfail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_mlp_error = buf;
+    return code;
+}
+
+#define MCUDA(call)                                                                         \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return mfail(e_ == cudaErrorMemoryAllocation ? LENSED_E_NOMEM : LENSED_E_CUDA,  \
+                         "%s: %s", #call, cudaGetErrorString(e_));                          \
+    } while (0)
+
+__device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
+__device__ __forceinline__ float silu_grad(float z)
+{
+    const float s = 1.f / (1.f + __expf(-z));
+    return s * (1.f + z * (1.f - s));
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// 16-byte global -> shared copy; src_bytes = 0 fills the destination with
+// zeros (rows beyond M or N).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
+                 "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+enum { EPI_F32 = 0, EPI_BIAS_SILU = 1, EPI_DSILU = 2 };
+
+// C = A B^T.  A: [M][lda] bf16 (K used), B: [N][ldb] bf16; K % 32 == 0,
+// lda, ldb multiples of 8.  Epilogues:
+//   EPI_F32        Cf[m][n] = acc
+//   EPI_BIAS_SILU  z = acc + bias[n]; Zout[m][n] = z (if Zout); Hout = bf16(silu(z))
+//   EPI_DSILU      d = acc * silu'(Zin[m][n]); Zout[m][n] = d; Hout = bf16(d)
+template <int EPI>
+__global__ void __launch_bounds__(128)
+    k_gemm(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb, int M, int N,
+           int K, float *__restrict__ Cf, int ldc, const float *__restrict__ bias,
+           const float *__restrict__ Zin, float *__restrict__ Zout, bf16 *__restrict__ Hout)
+{
+    __shared__ __align__(16) bf16 As[2][BM][PADK];
+    __shared__ __align__(16) bf16 Bs[2][BN][PADK];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int group = lane >> 2, tig = lane & 3;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+
+    float acc[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+
+    auto load_tile = [&](int buf, int k0) {
+        // 64 rows x 32 bf16 = 4 chunks of 16 bytes per row; 256 chunks per
+        // operand, two per thread
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {
+            const int ch = tid + it * 128;
+            const int r = ch >> 2, c = (ch & 3) * 8;
+            const int gm = m0 + r, gn = n0 + r;
+            cp_async16(&As[buf][r][c], A + (size_t)min(gm, M - 1) * lda + k0 + c, gm < M ? 16 : 0);
+            cp_async16(&Bs[buf][r][c], B + (size_t)min(gn, N - 1) * ldb + k0 + c, gn < N ? 16 : 0);
+        }
+        cp_async_commit();
+    };
+
+    const int nk = K / BK;
+    load_tile(0, 0);
+    for (int kt = 0; kt < nk; ++kt) {
+        const int buf = kt & 1;
+        if (kt + 1 < nk) {
+            load_tile(buf ^ 1, (kt + 1) * BK);
+            cp_async_wait1();
+        } else {
+            cp_async_wait0();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const int r = wm * 32 + mt * 16 + group;
+                af[mt][0] = *reinterpret_cast<const uint32_t *>(&As[buf][r][kk + tig * 2]);
+                af[mt][1] = *reinterpret_cast<const uint32_t *>(&As[buf][r + 8][kk + tig * 2]);
+                af[mt][2] = *reinterpret_cast<const uint32_t *>(&As[buf][r][kk + 8 + tig * 2]);
+                af[mt][3] = *reinterpret_cast<const uint32_t *>(&As[buf][r + 8][kk + 8 + tig * 2]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int n = wn * 32 + nt * 8 + group;
+                bfr[nt][0] = *reinterpret_cast<const uint32_t *>(&Bs[buf][n][kk + tig * 2]);
+                bfr[nt][1] = *reinterpret_cast<const uint32_t *>(&Bs[buf][n][kk + 8 + tig * 2]);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) mma_bf16_16816(acc[mt][nt], af[mt], bfr[nt]);
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = m0 + wm * 32 + mt * 16 + group + h * 8;
+                if (m >= M) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int n = n0 + wn * 32 + nt * 8 + tig * 2 + e;
+                    if (n >= N) continue;
+                    const float v = acc[mt][nt][h * 2 + e];
+                    const size_t o = (size_t)m * ldc + n;
+                    if (EPI == EPI_F32) {
+                        Cf[o] = v;
+                    } else if (EPI == EPI_BIAS_SILU) {
+                        const float z = v + bias[n];
+                        if (Zout) Zout[o] = z;
+                        Hout[o] = __float2bfloat16(silu(z));
+                    } else {
+                        const float d = v * silu_grad(Zin[o]);
+                        Zout[o] = d;
+                        Hout[o] = __float2bfloat16(d);
+                    }
+                }
+            }
+}
+
+// [R][C] bf16 -> [C][R] bf16 (32 x 32 tiles through shared memory)
+__global__ void k_transpose(const bf16 *__restrict__ in, int R, int C, bf16 *__restrict__ out)
+{
+    __shared__ bf16 t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        if (r < R && c < C) t[k][threadIdx.x] = in[(size_t)r * C + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[(size_t)c * R + r] = t[threadIdx.x][k];
+    }
+}
+
+// inputs [B][n_in] fp32 -> [Bp][kin] bf16, zero padded
+__global__ void k_pack(const float *__restrict__ X, int B, int n_in, int Bp, int kin,
+                       bf16 *__restrict__ Xb)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)Bp * kin) return;
+    const int r = (int)(i / kin), c = (int)(i % kin);
+    Xb[i] = __float2bfloat16(r < B && c < n_in ? X[(size_t)r * n_in + c] : 0.f);
+}
+
+// y[m] = h3[m] . w4 + b4 (one warp per row, fixed-order lane sums)
+__global__ void k_out(const bf16 *__restrict__ H3, int H, const float *__restrict__ w4,
+                      const float *__restrict__ b4, int B, float *__restrict__ y)
+{
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= B) return;
+    float s = 0.f;
+    for (int k = lane; k < H; k += 32) s += __bfloat162float(H3[(size_t)row * H + k]) * w4[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[row] = s + b4[0];
+}
+
+// Backward of the output layer: dy = (y - t)/B (zero on padding rows),
+// dZ3 = dy w4 silu'(Z3); loss terms r^2/(2B) per row.
+__global__ void k_out_back(const float *__restrict__ y, const float *__restrict__ t, int B, int Bp,
+                           int H, const float *__restrict__ w4, const float *__restrict__ Z3,
+                           float *__restrict__ dy, float *__restrict__ lossrow,
+                           float *__restrict__ dZf, bf16 *__restrict__ dZb)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)Bp * H) return;
+    const int m = (int)(i / H), k = (int)(i % H);
+    const float r = m < B ? y[m] - t[m] : 0.f;
+    const float d = r / (float)B;
+    if (k == 0) {
+        dy[m] = d;
+        lossrow[m] = 0.5f * r * r / (float)B;
+    }
+    const float g = d * w4[k] * silu_grad(Z3[i]);
+    dZf[i] = g;
+    dZb[i] = __float2bfloat16(g);
+}
+
+// out[n] = sum_m in[m][n] (fixed order), fp32 in
+__global__ void k_colsum(const float *__restrict__ in, int M, int N, float *__restrict__ out)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.f;
+    for (int m = 0; m < M; ++m) s += in[(size_t)m * N + n];
+    out[n] = s;
+}
+
+// dw4[k] = sum_m h3[m][k] dy[m]
+__global__ void k_dw4(const bf16 *__restrict__ H3, const float *__restrict__ dy, int Bp, int H,
+                      float *__restrict__ dw4)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= H) return;
+    float s = 0.f;
+    for (int m = 0; m < Bp; ++m) s += __bfloat162float(H3[(size_t)m * H + k]) * dy[m];
+    dw4[k] = s;
+}
+
+__global__ void k_sum(const float *__restrict__ in, int n, float *__restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float s = 0.f;
+    for (int i = 0; i < n; ++i) s += in[i];
+    out[0] = s;
+}
+
+// copy the first c columns of [R][ld] into [R][c]
+__global__ void k_copy_cols(const float *__restrict__ in, int R, int ld, int c,
+                            float *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= R * c) return;
+    out[i] = in[(size_t)(i / c) * ld + (i % c)];
+}
+
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, int n, float lr, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+}
+
+// bf16 weight copies from the fp32 master: W1 into [H][kin] (zero padded),
+// W2, W3 as they are
+__global__ void k_refresh(const float *__restrict__ p, int n_in, int kin, int H,
+                          bf16 *__restrict__ W1b, bf16 *__restrict__ W2b, bf16 *__restrict__ W3b)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n1 = H * kin, n2 = H * H;
+    if (i < n1) {
+        const int r = i / kin, c = i % kin;
+        W1b[i] = __float2bfloat16(c < n_in ? p[r * n_in + c] : 0.f);
+    }
+    const size_t o2 = (size_t)H * n_in + H;
+    const size_t o3 = o2 + (size_t)H * H + H;
+    if (i < n2) {
+        W2b[i] = __float2bfloat16(p[o2 + i]);
+        W3b[i] = __float2bfloat16(p[o3 + i]);
+    }
+}
+
+template <typename T>
+struct Buf {
+    T *p = nullptr;
+    size_t n = 0;
+    ~Buf()
+    {
+        if (p) cudaFree(p);
+    }
+    int alloc(size_t count)
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return mfail(LENSED_E_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+        }
+        n = count;
+        return LENSED_OK;
+    }
+};
+
+}  // namespace
+
+struct lensed_mlp {
+    int n_in, H, kin, maxB, Bp;  // Bp: max batch rounded up to 64
+    size_t np;                   // parameter count
+    size_t o_b1, o_W2, o_b2, o_W3, o_b3, o_w4, o_b4;
+    long long step = 0;
+    Buf<float> p, m, v, g;
+    Buf<bf16> W1b, W2b, W3b, WT;
+    Buf<bf16> Xb, XbT, H1, H2, H3, HT, dZa, dZbuf, dZT;
+    Buf<float> Z1, Z2, Z3, dZf, y, dy, lossrow, gW1, tmpcol;
+};
+
+namespace {
+
+int launch_gemm(int epi, const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K,
+                float *Cf, int ldc, const float *bias, const float *Zin, float *Zout, bf16 *Hout,
+                cudaStream_t st)
+{
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    if (epi == EPI_F32)
+        k_gemm<EPI_F32><<<grid, 128, 0, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc, bias, Zin, Zout, Hout);
+    else if (epi == EPI_BIAS_SILU)
+        k_gemm<EPI_BIAS_SILU><<<grid, 128, 0, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc, bias, Zin, Zout,
+                                                   Hout);
+    else
+        k_gemm<EPI_DSILU><<<grid, 128, 0, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc, bias, Zin, Zout, Hout);
+    return LENSED_OK;
+}
+
+void transpose(const bf16 *in, int R, int C, bf16 *out, cudaStream_t st)
+{
+    dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
+    k_transpose<<<grid, block, 0, st>>>(in, R, C, out);
+}
+
+// forward of rows [0, B) (B <= maxB): fills Xb, Z*, H*, y
+void forward(lensed_mlp *m, const float *X, int B, float *y, bool keep_z, cudaStream_t st)
+{
+    const int Bp = (B + 63) / 64 * 64, H = m->H;
+    const long long nx = (long long)Bp * m->kin;
+    k_pack<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(X, B, m->n_in, Bp, m->kin, m->Xb.p);
+    launch_gemm(EPI_BIAS_SILU, m->Xb.p, m->kin, m->W1b.p, m->kin, Bp, H, m->kin, nullptr, H,
+                m->p.p + m->o_b1, nullptr, keep_z ? m->Z1.p : nullptr, m->H1.p, st);
+    launch_gemm(EPI_BIAS_SILU, m->H1.p, H, m->W2b.p, H, Bp, H, H, nullptr, H, m->p.p + m->o_b2,
+                nullptr, keep_z ? m->Z2.p : nullptr, m->H2.p, st);
+    launch_gemm(EPI_BIAS_SILU, m->H2.p, H, m->W3b.p, H, Bp, H, H, nullptr, H, m->p.p + m->o_b3,
+                nullptr, keep_z ? m->Z3.p : nullptr, m->H3.p, st);
+    k_out<<<(B + 7) / 8, 256, 0, st>>>(m->H3.p, H, m->p.p + m->o_w4, m->p.p + m->o_b4, B, y);
+}
+
+// loss and gradient of rows [0, B) into m->g and loss (device scalar)
+void gradient(lensed_mlp *m, const float *X, const float *t, int B, float *loss, cudaStream_t st)
+{
+    const int Bp = (B + 63) / 64 * 64, H = m->H;
+    forward(m, X, B, m->y.p, true, st);
+    const long long nbh = (long long)Bp * H;
+    float *g = m->g.p;
+    // output layer and dZ3
+    k_out_back<<<(unsigned)((nbh + 255) / 256), 256, 0, st>>>(m->y.p, t, B, Bp, H,
+                                                               m->p.p + m->o_w4, m->Z3.p, m->dy.p,
+                                                               m->lossrow.p, m->dZf.p, m->dZa.p);
+    k_sum<<<1, 32, 0, st>>>(m->lossrow.p, Bp, loss);
+    k_dw4<<<(H + 127) / 128, 128, 0, st>>>(m->H3.p, m->dy.p, Bp, H, g + m->o_w4);
+    k_sum<<<1, 32, 0, st>>>(m->dy.p, Bp, g + m->o_b4);
+    // layer 3: dW3 = dZ3^T H2, db3, dZ2 = (dZ3 W3) * silu'(Z2)
+    transpose(m->dZa.p, Bp, H, m->dZT.p, st);
+    transpose(m->H2.p, Bp, H, m->HT.p, st);
+    launch_gemm(EPI_F32, m->dZT.p, Bp, m->HT.p, Bp, H, H, Bp, g + m->o_W3, H, nullptr, nullptr,
+                nullptr, nullptr, st);
+    k_colsum<<<(H + 127) / 128, 128, 0, st>>>(m->dZf.p, Bp, H, g + m->o_b3);
+    transpose(m->W3b.p, H, H, m->WT.p, st);
+    launch_gemm(EPI_DSILU, m->dZa.p, H, m->WT.p, H, Bp, H, H, nullptr, H, nullptr, m->Z2.p,
+                m->dZf.p, m->dZbuf.p, st);
+    // layer 2
+    transpose(m->dZbuf.p, Bp, H, m->dZT.p, st);
+    transpose(m->H1.p, Bp, H, m->HT.p, st);
+    launch_gemm(EPI_F32, m->dZT.p, Bp, m->HT.p, Bp, H, H, Bp, g + m->o_W2, H, nullptr, nullptr,
+                nullptr, nullptr, st);
+    k_colsum<<<(H + 127) / 128, 128, 0, st>>>(m->dZf.p, Bp, H, g + m->o_b2);
+    transpose(m->W2b.p, H, H, m->WT.p, st);
+    launch_gemm(EPI_DSILU, m->dZbuf.p, H, m->WT.p, H, Bp, H, H, nullptr, H, nullptr, m->Z1.p,
+                m->dZf.p, m->dZa.p, st);
+    // layer 1: dW1 = dZ1^T X (padded to kin columns), db1
+    transpose(m->dZa.p, Bp, H, m->dZT.p, st);
+    transpose(m->Xb.p, Bp, m->kin, m->XbT.p, st);
+    launch_gemm(EPI_F32, m->dZT.p, Bp, m->XbT.p, Bp, H, m->kin, Bp, m->gW1.p, m->kin, nullptr,
+                nullptr, nullptr, nullptr, st);
+    k_copy_cols<<<(H * m->n_in + 255) / 256, 256, 0, st>>>(m->gW1.p, H, m->kin, m->n_in, g);
+    k_colsum<<<(H + 127) / 128, 128, 0, st>>>(m->dZf.p, Bp, H, g + m->o_b1);
+}
+
+int refresh(lensed_mlp *m, cudaStream_t st)
+{
+    const int n = std::max(m->H * m->kin, m->H * m->H);
+    k_refresh<<<(n + 255) / 256, 256, 0, st>>>(m->p.p, m->n_in, m->kin, m->H, m->W1b.p, m->W2b.p,
+                                                m->W3b.p);
+    MCUDA(cudaGetLastError());
+    return LENSED_OK;
+}
+
+}  // namespace
+
+extern "C" const char *lensed_mlp_last_error(void) { return g_mlp_error.c_str(); }
+
+extern "C" int lensed_mlp_create(int n_in, int hidden, int max_batch, lensed_mlp **out)
+{
+    g_mlp_error.clear();
+    if (!out) return mfail(LENSED_E_ARG, "out is NULL");
+    if (n_in < 1 || n_in > 64) return mfail(LENSED_E_ARG, "n_in = %d (1..64)", n_in);
+    if (hidden < 64 || hidden % 64) return mfail(LENSED_E_ARG, "hidden = %d (multiple of 64)", hidden);
+    if (max_batch < 1) return mfail(LENSED_E_ARG, "max_batch = %d", max_batch);
+    lensed_mlp *m = new lensed_mlp();
+    m->n_in = n_in;
+    m->H = hidden;
+    m->kin = (n_in + 31) / 32 * 32;
+    m->maxB = max_batch;
+    m->Bp = (max_batch + 63) / 64 * 64;
+    const size_t H = hidden;
+    m->o_b1 = H * n_in;
+    m->o_W2 = m->o_b1 + H;
+    m->o_b2 = m->o_W2 + H * H;
+    m->o_W3 = m->o_b2 + H;
+    m->o_b3 = m->o_W3 + H * H;
+    m->o_w4 = m->o_b3 + H;
+    m->o_b4 = m->o_w4 + H;
+    m->np = m->o_b4 + 1;
+    const size_t bh = (size_t)m->Bp * H;
+    int rc;
+    if ((rc = m->p.alloc(m->np)) || (rc = m->m.alloc(m->np)) || (rc = m->v.alloc(m->np)) ||
+        (rc = m->g.alloc(m->np)) || (rc = m->W1b.alloc(H * m->kin)) ||
+        (rc = m->W2b.alloc(H * H)) || (rc = m->W3b.alloc(H * H)) || (rc = m->WT.alloc(H * H)) ||
+        (rc = m->Xb.alloc((size_t)m->Bp * m->kin)) || (rc = m->XbT.alloc((size_t)m->Bp * m->kin)) ||
+        (rc = m->H1.alloc(bh)) || (rc = m->H2.alloc(bh)) || (rc = m->H3.alloc(bh)) ||
+        (rc = m->HT.alloc(bh)) || (rc = m->dZa.alloc(bh)) || (rc = m->dZbuf.alloc(bh)) ||
+        (rc = m->dZT.alloc(bh)) || (rc = m->Z1.alloc(bh)) || (rc = m->Z2.alloc(bh)) ||
+        (rc = m->Z3.alloc(bh)) || (rc = m->dZf.alloc(bh)) || (rc = m->y.alloc(m->Bp)) ||
+        (rc = m->dy.alloc(m->Bp)) || (rc = m->lossrow.alloc(m->Bp)) ||
+        (rc = m->gW1.alloc(H * m->kin)) || (rc = m->tmpcol.alloc(H))) {
+        std::string msg = g_mlp_error;
+        delete m;
+        g_mlp_error = msg;
+        return rc;
+    }
+    cudaMemset(m->p.p, 0, m->np * sizeof(float));
+    cudaMemset(m->m.p, 0, m->np * sizeof(float));
+    cudaMemset(m->v.p, 0, m->np * sizeof(float));
+    if ((rc = refresh(m, nullptr))) {
+        delete m;
+        return rc;
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        delete m;
+        return mfail(LENSED_E_CUDA, "create: %s", cudaGetErrorString(e));
+    }
+    *out = m;
+    return LENSED_OK;
+}
+
+extern "C" void lensed_mlp_destroy(lensed_mlp *m)
+{
+    if (!m) return;
+    cudaDeviceSynchronize();
+    delete m;
+}
+
+extern "C" long long lensed_mlp_param_count(const lensed_mlp *m) { return m ? (long long)m->np : -1; }
+
+extern "C" int lensed_mlp_set_params(lensed_mlp *m, const float *host_params)
+{
+    if (!m || !host_params) return mfail(LENSED_E_ARG, "NULL argument");
+    MCUDA(cudaMemcpy(m->p.p, host_params, m->np * sizeof(float), cudaMemcpyHostToDevice));
+    MCUDA(cudaMemset(m->m.p, 0, m->np * sizeof(float)));
+    MCUDA(cudaMemset(m->v.p, 0, m->np * sizeof(float)));
+    m->step = 0;
+    int rc = refresh(m, nullptr);
+    if (rc) return rc;
+    MCUDA(cudaDeviceSynchronize());
+    return LENSED_OK;
+}
+
+extern "C" int lensed_mlp_get_params(const lensed_mlp *m, float *host_params)
+{
+    if (!m || !host_params) return mfail(LENSED_E_ARG, "NULL argument");
+    MCUDA(cudaDeviceSynchronize());
+    MCUDA(cudaMemcpy(host_params, m->p.p, m->np * sizeof(float), cudaMemcpyDeviceToHost));
+    return LENSED_OK;
+}
+
+extern "C" int lensed_mlp_forward(lensed_mlp *m, const float *X, int B, float *y, void *stream)
+{
+    if (!m || !X || !y) return mfail(LENSED_E_ARG, "NULL argument");
+    if (B < 0) return mfail(LENSED_E_ARG, "B = %d", B);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int b0 = 0; b0 < B; b0 += m->maxB) {
+        const int nb = std::min(m->maxB, B - b0);
+        forward(m, X + (size_t)b0 * m->n_in, nb, y + b0, false, st);
+    }
+    MCUDA(cudaGetLastError());
+    return LENSED_OK;
+}
+
+extern "C" int lensed_mlp_gradient(lensed_mlp *m, const float *X, const float *t, int B,
+                                   float *grad, float *loss, void *stream)
+{
+    if (!m || !X || !t || !grad || !loss) return mfail(LENSED_E_ARG, "NULL argument");
+    if (B < 1 || B > m->maxB) return mfail(LENSED_E_ARG, "B = %d (1..%d)", B, m->maxB);
+    cudaStream_t st = (cudaStream_t)stream;
+    gradient(m, X, t, B, loss, st);
+    MCUDA(cudaMemcpyAsync(grad, m->g.p, m->np * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    MCUDA(cudaGetLastError());
+    return LENSED_OK;
+}
+
+extern "C" int lensed_mlp_train_step(lensed_mlp *m, const float *X, const float *t, int B,
+                                     float lr, float *loss, void *stream)
+{
+    if (!m || !X || !t || !loss) return mfail(LENSED_E_ARG, "NULL argument");
+    if (B < 1 || B > m->maxB) return mfail(LENSED_E_ARG, "B = %d (1..%d)", B, m->maxB);
+    if (!(lr > 0.f)) return mfail(LENSED_E_ARG, "lr must be > 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    gradient(m, X, t, B, loss, st);
+    m->step += 1;
+    const float c1 = 1.f - powf(0.9f, (float)m->step), c2 = 1.f - powf(0.999f, (float)m->step);
+    k_adam<<<(unsigned)((m->np + 255) / 256), 256, 0, st>>>(m->p.p, m->g.p, m->m.p, m->v.p,
+                                                            (int)m->np, lr, c1, c2);
+    const int n = std::max(m->H * m->kin, m->H * m->H);
+    k_refresh<<<(n + 255) / 256, 256, 0, st>>>(m->p.p, m->n_in, m->kin, m->H, m->W1b.p, m->W2b.p,
+                                                m->W3b.p);
+    MCUDA(cudaGetLastError());
+    return LENSED_OK;
+}
