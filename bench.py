@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -41,6 +42,8 @@ WORKLOADS = {
     "c2": (WORKLOAD, POINTS),
     "c1": ("single_64x64_h0.05_sie_shear_sersic_psf7_gl5x5_1000pts_13par", 1000),
     "c3": ("uneven_256systems_48-320px_gl3-7_psf7-31_512pts_each", 512),
+    "c4": ("euclid_400x400_h0.1_18par_nested_sampling_2000live", 0),
+    "c5": ("euclid_400x400_h0.1_18par_surrogate_prescreen_65536", 0),
 }
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_SM_MHZ = 2070.0
@@ -60,7 +63,11 @@ def parse():
                          "workload is 4096)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-point pass")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
-                    help="c2 (default, the benchmark), c1 or c3 (other configurations)")
+                    help="c2 (default, the benchmark), c1 or c3 (other configurations), "
+                         "c4 (posterior run), c5 (surrogate pre-screen vs plain)")
+    ap.add_argument("--live", type=int, default=2000, help="live points (c4, c5)")
+    ap.add_argument("--oracle-points", type=int, default=384,
+                    help="posterior points the CPU oracle re-evaluates (c4)")
     return ap.parse_args()
 
 
@@ -199,10 +206,147 @@ def run_reference(args):
     return 0
 
 
+def _c4_model(LZ, W, precision):
+    spec = W.c4_euclid()
+    probe = LZ.Model(spec, {"data": np.zeros((spec["ny"], spec["nx"])),
+                            "variance": np.ones((spec["ny"], spec["nx"]))}, precision=precision)
+    noiseless = probe.render(0, np.asarray(spec["truth"]), convolved=True).double().cpu().numpy()
+    probe.close()
+    obs = W.add_noise(spec, noiseless, spec["seed"])
+    return spec, obs, LZ.Model(spec, obs, precision=precision)
+
+
+def run_posterior(args):
+    """c4: one nested-sampling run driven by the batched likelihood; the CPU
+    leg re-evaluates posterior points with the oracle."""
+    import torch
+
+    import workloads as W
+    from paper_1505_07674_gb300 import build as build_lib
+    from paper_1505_07674_gb300 import lensed as LZ
+    from paper_1505_07674_gb300.posterior import GpuLikelihood
+    from paper_1505_07674_gb300.sampler import nested_sampling
+
+    torch.cuda.set_device(0)
+    build_lib()
+    spec, obs, m = _c4_model(LZ, W, args.precision)
+    like = GpuLikelihood(m, spec)
+    sampler = ClockSampler(0)
+    sampler.start()
+    res = nested_sampling(like, like.ndim, args.live, seed=21, dlogz=0.1, max_evals=20_000_000)
+    clocks = sampler.stop()
+    post = like.to_params(res.posterior_mean())
+    w = np.exp(res["logwt"] - res["logwt"].max())
+    sd = np.sqrt(((like.to_params(res["samples"]) - post) ** 2 * w[:, None]).sum(0) / w.sum())
+    truth = np.asarray(spec["truth"])
+    line = {"metric": "nested-sampling posterior run, batched GPU likelihood",
+            "workload": WORKLOADS["c4"][0], "n_live": args.live, "precision_mode": args.precision,
+            "logz": res["logz"], "logz_err": res["logz_err"], "information": res["information"],
+            "n_evals": res["n_evals"], "n_iter": res["n_iter"], "wall_s": res["wall_s"],
+            "likelihood_s": like.seconds, "evals_per_s_overall": res["n_evals"] / res["wall_s"],
+            "posterior_mean": dict(zip(spec["param_names"], np.round(post, 5).tolist())),
+            "posterior_sd": dict(zip(spec["param_names"], np.round(sd, 5).tolist())),
+            "truth_pull": dict(zip(spec["param_names"],
+                                   np.round((post - truth) / np.maximum(sd, 1e-12), 2).tolist())),
+            "clocks": clocks, "data": "synthetic"}
+    if not args.no_cpu_baseline and args.oracle_points > 0:
+        # oracle re-evaluation of posterior points (drawn by weight): logL
+        # parity on the posterior, and posterior means re-weighted to the
+        # oracle's likelihood
+        from oracle import oracle as O
+        rng = np.random.default_rng(5)
+        pick = rng.choice(len(w), size=args.oracle_points, p=w / w.sum())
+        th = like.to_params(res["samples"][pick])
+        osys = O.OracleSystem(spec, {"data": obs["data"], "gain": obs["gain"],
+                                     "offset": obs["offset"]})
+        t0 = time.perf_counter()
+        lo = osys.loglike(th, nthreads=os.cpu_count())
+        dt = time.perf_counter() - t0
+        lg = res["logl"][pick]
+        rw = np.exp((lo - lg) - (lo - lg).max())
+        mean_gpu = th.mean(0)
+        mean_ora = (th * rw[:, None]).sum(0) / rw.sum()
+        line["cpu_baseline"] = {
+            "value": args.oracle_points / dt, "unit": "evals/s", "cores": os.cpu_count(),
+            "kind": "oracle", "sample": f"{args.oracle_points} posterior points drawn by weight",
+            "max_abs_dlogl": float(np.abs(lo - lg).max()),
+            "max_rel_dlogl": float((np.abs(lo - lg) / np.abs(lo)).max()),
+            "posterior_mean_shift_in_sd": dict(zip(
+                spec["param_names"],
+                np.round((mean_ora - mean_gpu) / np.maximum(sd, 1e-12), 4).tolist()))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_surrogate(args):
+    """c5: surrogate trained on the (parameters, logL) pairs of one plain
+    run; then a plain run and a pre-screened run on a new seed, compared on
+    wall time and evidence."""
+    import torch
+
+    import workloads as W
+    from paper_1505_07674_gb300 import build as build_lib
+    from paper_1505_07674_gb300 import lensed as LZ
+    from paper_1505_07674_gb300.posterior import GpuLikelihood, SurrogateScreen
+    from paper_1505_07674_gb300.sampler import nested_sampling
+
+    torch.cuda.set_device(0)
+    build_lib()
+    spec, obs, m = _c4_model(LZ, W, args.precision)
+    # training pairs: every evaluation of a plain run (seed 11), at most 2M
+    rec = GpuLikelihood(m, spec, record=True)
+    t0 = time.perf_counter()
+    nested_sampling(rec, rec.ndim, args.live, seed=11, dlogz=0.1, max_evals=20_000_000)
+    gen_s = time.perf_counter() - t0
+    U = np.concatenate(rec.U)[-2_000_000:]
+    L = np.concatenate(rec.L)[-2_000_000:]
+    screen = SurrogateScreen(rec.ndim, 256, 8192).fit(U, L, epochs=20)
+    # MLP inference throughput on 65,536 proposals
+    X = torch.rand((65536, rec.ndim), device="cuda")
+    y = torch.empty(65536, device="cuda")
+    for _ in range(3):
+        screen.net.forward(X, out=y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        screen.net.forward(X, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 20
+    flops = 2 * 65536 * (32 * 256 + 2 * 256 * 256 + 256)
+    runs = {}
+    for name, pre in (("plain", None), ("surrogate", screen)):
+        like = GpuLikelihood(m, spec)
+        res = nested_sampling(like, like.ndim, args.live, seed=12, dlogz=0.1, prescreen=pre,
+                              max_evals=20_000_000)
+        runs[name] = {"logz": res["logz"], "logz_err": res["logz_err"],
+                      "n_evals": res["n_evals"], "n_prescreened": res["n_prescreened"],
+                      "n_iter": res["n_iter"], "wall_s": res["wall_s"],
+                      "likelihood_s": like.seconds}
+    a, b = runs["plain"], runs["surrogate"]
+    line = {"metric": "wall time to the evidence estimate, surrogate pre-screen vs plain batched",
+            "workload": WORKLOADS["c5"][0], "n_live": args.live,
+            "plain": a, "surrogate": b,
+            "speedup_wall": a["wall_s"] / b["wall_s"],
+            "exact_evals_saved_frac": 1 - b["n_evals"] / a["n_evals"],
+            "logz_diff_in_sigma": (b["logz"] - a["logz"]) / math.hypot(a["logz_err"], b["logz_err"]),
+            "training": {"pairs": int(screen.n_train), "generation_s": gen_s,
+                         "train_s": screen.train_s, "holdout_rms_y": screen.val_rms,
+                         "margin_y": screen.margin, "screen_s_in_run": screen.screen_s},
+            "mlp_forward_65536": {"ms": fwd_ms, "tflops": flops / (fwd_ms * 1e-3) / 1e12},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c4":
+        return run_posterior(args)
+    if args.workload == "c5":
+        return run_surrogate(args)
 
     import torch
 
