@@ -233,16 +233,17 @@ def run_posterior(args):
     like = GpuLikelihood(m, spec)
     sampler = ClockSampler(0)
     sampler.start()
-    res = nested_sampling(like, like.ndim, args.live, seed=21, dlogz=0.1, max_evals=20_000_000)
+    res = nested_sampling(like, like.ndim, args.live, seed=21, dlogz=0.1, max_evals=8_000_000)
     clocks = sampler.stop()
     post = like.to_params(res.posterior_mean())
     w = np.exp(res["logwt"] - res["logwt"].max())
-    sd = np.sqrt(((like.to_params(res["samples"]) - post) ** 2 * w[:, None]).sum(0) / w.sum())
+    sd = res.posterior_sd() * (like.hi - like.lo)
     truth = np.asarray(spec["truth"])
     line = {"metric": "nested-sampling posterior run, batched GPU likelihood",
             "workload": WORKLOADS["c4"][0], "n_live": args.live, "precision_mode": args.precision,
             "logz": res["logz"], "logz_err": res["logz_err"], "information": res["information"],
             "n_evals": res["n_evals"], "n_iter": res["n_iter"], "wall_s": res["wall_s"],
+            "walk_accept": res["accept"],
             "likelihood_s": like.seconds, "evals_per_s_overall": res["n_evals"] / res["wall_s"],
             "posterior_mean": dict(zip(spec["param_names"], np.round(post, 5).tolist())),
             "posterior_sd": dict(zip(spec["param_names"], np.round(sd, 5).tolist())),
@@ -296,7 +297,7 @@ def run_surrogate(args):
     # training pairs: every evaluation of a plain run (seed 11), at most 2M
     rec = GpuLikelihood(m, spec, record=True)
     t0 = time.perf_counter()
-    nested_sampling(rec, rec.ndim, args.live, seed=11, dlogz=0.1, max_evals=20_000_000)
+    nested_sampling(rec, rec.ndim, args.live, seed=11, dlogz=0.1, max_evals=8_000_000)
     gen_s = time.perf_counter() - t0
     U = np.concatenate(rec.U)[-2_000_000:]
     L = np.concatenate(rec.L)[-2_000_000:]
@@ -318,7 +319,7 @@ def run_surrogate(args):
     for name, pre in (("plain", None), ("surrogate", screen)):
         like = GpuLikelihood(m, spec)
         res = nested_sampling(like, like.ndim, args.live, seed=12, dlogz=0.1, prescreen=pre,
-                              max_evals=20_000_000)
+                              max_evals=8_000_000)
         runs[name] = {"logz": res["logz"], "logz_err": res["logz_err"],
                       "n_evals": res["n_evals"], "n_prescreened": res["n_prescreened"],
                       "n_iter": res["n_iter"], "wall_s": res["wall_s"],

@@ -3,7 +3,7 @@ the optional surrogate pre-screen.
 
 ``GpuLikelihood`` maps unit-cube points to the model's parameters (uniform
 box priors) and evaluates them with one ``lensed_loglike_batch`` call per
-batch; batch sizes are rounded up to a multiple of 2,048 (padding repeats the
+batch; batch sizes are rounded up to a multiple of 128 (padding repeats the
 first point) so the library's CUDA-graph cache sees a handful of shapes.
 
 ``SurrogateScreen`` trains the BF16 network on (parameters, logL) pairs from
@@ -28,7 +28,7 @@ from .surrogate import Surrogate
 
 
 class GpuLikelihood:
-    def __init__(self, model: Model, spec, record=False, pad_to=2048):
+    def __init__(self, model: Model, spec, record=False, pad_to=128):
         self.m = model
         self.lo = np.asarray(spec["prior_lo"], float)
         self.hi = np.asarray(spec["prior_hi"], float)

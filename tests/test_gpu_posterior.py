@@ -38,8 +38,7 @@ def test_posterior_recovers_truth(setup):
     like = GpuLikelihood(m, spec)
     res = nested_sampling(like, like.ndim, 200, seed=3, dlogz=0.2)
     post = like.to_params(res.posterior_mean())
-    w = np.exp(res["logwt"] - res["logwt"].max())
-    sd = np.sqrt(((like.to_params(res["samples"]) - post) ** 2 * w[:, None]).sum(0) / w.sum())
+    sd = res.posterior_sd() * (like.hi - like.lo)
     truth = np.asarray(spec["truth"])
     names = spec["param_names"]
     for k in ("b_L", "q_L", "x_S", "r_S"):

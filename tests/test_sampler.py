@@ -23,22 +23,25 @@ def gauss(mu, s):
 @pytest.mark.parametrize("d,s,n_live", [(2, 0.05, 300), (5, 0.08, 400)])
 def test_gaussian_evidence_and_mean(d, s, n_live):
     mu = np.full(d, 0.45)
-    res = nested_sampling(gauss(mu, s), d, n_live, seed=1, dlogz=0.05, batch_min=256)
+    res = nested_sampling(gauss(mu, s), d, n_live, seed=1, dlogz=0.05)
     exact = 0.5 * d * math.log(2 * math.pi * s * s)
     assert abs(res["logz"] - exact) < 4 * res["logz_err"] + 0.05, (res["logz"], exact, res["logz_err"])
     assert np.allclose(res.posterior_mean(), mu, atol=4 * s / math.sqrt(n_live) + 0.01)
     # information of a Gaussian posterior under a unit-cube prior
     H = -0.5 * d * (math.log(2 * math.pi * s * s) + 1)
     assert abs(res["information"] - H) < 0.15 * H
+    assert 0.1 < res["accept"] < 0.9
 
 
 def test_prescreen_below_threshold_changes_nothing_but_work():
     mu, s, d = np.full(3, 0.6), 0.07, 3
     f = gauss(mu, s)
-    plain = nested_sampling(f, d, 200, seed=3, dlogz=0.05, batch_min=256)
-    # an exact pre-screen: drops only candidates the exact likelihood rejects
-    screened = nested_sampling(f, d, 200, seed=3, dlogz=0.05, batch_min=256,
+    plain = nested_sampling(f, d, 200, seed=3, dlogz=0.05)
+    # an exact pre-screen: drops only proposals the exact likelihood rejects,
+    # so the walks are the same moves with fewer exact evaluations
+    screened = nested_sampling(f, d, 200, seed=3, dlogz=0.05,
                                prescreen=lambda U, thr: f(U) > thr)
+    assert screened["logz"] == plain["logz"]
     assert screened["n_prescreened"] > 0
     assert screened["n_evals"] < plain["n_evals"]
     exact = 0.5 * d * math.log(2 * math.pi * s * s)
@@ -56,6 +59,6 @@ def test_bimodal_evidence():
         lb = -0.5 * ((U - b) ** 2).sum(1) / s ** 2
         return np.logaddexp(la, lb)
 
-    res = nested_sampling(f, d, 500, seed=5, dlogz=0.05, batch_min=256)
+    res = nested_sampling(f, d, 500, seed=5, dlogz=0.05)
     exact = 0.5 * d * math.log(2 * math.pi * s * s) + math.log(2.0)
     assert abs(res["logz"] - exact) < 4 * res["logz_err"] + 0.05
