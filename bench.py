@@ -280,30 +280,60 @@ def run_posterior(args):
 
 
 def run_surrogate(args):
-    """c5: surrogate trained on the (parameters, logL) pairs of one plain
-    run; then a plain run and a pre-screened run on a new seed, compared on
-    wall time and evidence."""
+    """c5: wall time to the evidence estimate with the surrogate versus the
+    plain batched run (same seed).  Two surrogate modes: retrained online
+    during the run on its own exact evaluations (whitened inputs), and
+    trained once on the (parameters, logL) pairs of an earlier run (at most
+    2M).  In both the network constrains the intermediate walk steps and
+    the exact likelihood judges every end point."""
     import torch
 
     import workloads as W
     from paper_1505_07674_gb300 import build as build_lib
     from paper_1505_07674_gb300 import lensed as LZ
-    from paper_1505_07674_gb300.posterior import GpuLikelihood, SurrogateScreen
+    from paper_1505_07674_gb300.posterior import GpuLikelihood, OnlineSurrogate, SurrogateScreen
     from paper_1505_07674_gb300.sampler import nested_sampling
 
     torch.cuda.set_device(0)
     build_lib()
     spec, obs, m = _c4_model(LZ, W, args.precision)
-    # training pairs: every evaluation of a plain run (seed 11), at most 2M
+
+    def summary(res, like, extra=None):
+        d = {"logz": res["logz"], "logz_err": res["logz_err"], "n_evals": res["n_evals"],
+             "n_iter": res["n_iter"], "wall_s": res["wall_s"], "likelihood_s": like.seconds,
+             "n_prescreened": res["n_prescreened"],
+             "screened_end_accept": res["screened_end_accept"]}
+        d.update(extra or {})
+        return d
+
+    runs = {}
+    like = GpuLikelihood(m, spec)
+    res = nested_sampling(like, like.ndim, args.live, seed=12, dlogz=0.1, max_evals=8_000_000)
+    runs["plain"] = summary(res, like)
     rec = GpuLikelihood(m, spec, record=True)
+    online = OnlineSurrogate(rec, rec.ndim)
+    res = nested_sampling(rec, rec.ndim, args.live, seed=12, dlogz=0.1, prescreen=online,
+                          on_round=online.on_round, max_evals=8_000_000)
+    runs["online_surrogate"] = summary(res, rec, {
+        "train_s": online.train_s, "screen_s": online.screen_s, "fits": len(online.fits),
+        "active_fits": int(sum(f[3] for f in online.fits)),
+        "last_rms_y": online.fits[-1][2] if online.fits else None})
+    # global surrogate from an earlier run's evaluations (seed 11)
+    gen = GpuLikelihood(m, spec, record=True)
     t0 = time.perf_counter()
-    nested_sampling(rec, rec.ndim, args.live, seed=11, dlogz=0.1, max_evals=8_000_000)
+    nested_sampling(gen, gen.ndim, args.live, seed=11, dlogz=0.1, max_evals=8_000_000)
     gen_s = time.perf_counter() - t0
-    U = np.concatenate(rec.U)[-2_000_000:]
-    L = np.concatenate(rec.L)[-2_000_000:]
-    screen = SurrogateScreen(rec.ndim, 256, 8192).fit(U, L, epochs=20)
-    # MLP inference throughput on 65,536 proposals
-    X = torch.rand((65536, rec.ndim), device="cuda")
+    U = np.concatenate(gen.U)[-2_000_000:]
+    L = np.concatenate(gen.L)[-2_000_000:]
+    screen = SurrogateScreen(gen.ndim, 256, 8192).fit(U, L, epochs=20, margin_sigmas=2.0)
+    like = GpuLikelihood(m, spec)
+    res = nested_sampling(like, like.ndim, args.live, seed=12, dlogz=0.1, prescreen=screen,
+                          max_evals=8_000_000)
+    runs["global_surrogate"] = summary(res, like, {
+        "pairs": int(screen.n_train), "generation_s": gen_s, "train_s": screen.train_s,
+        "holdout_rms_y": screen.val_rms, "margin_y": screen.margin})
+    # network inference throughput on 65,536 proposals
+    X = torch.rand((65536, gen.ndim), device="cuda")
     y = torch.empty(65536, device="cuda")
     for _ in range(3):
         screen.net.forward(X, out=y)
@@ -315,25 +345,14 @@ def run_surrogate(args):
     torch.cuda.synchronize()
     fwd_ms = e0.elapsed_time(e1) / 20
     flops = 2 * 65536 * (32 * 256 + 2 * 256 * 256 + 256)
-    runs = {}
-    for name, pre in (("plain", None), ("surrogate", screen)):
-        like = GpuLikelihood(m, spec)
-        res = nested_sampling(like, like.ndim, args.live, seed=12, dlogz=0.1, prescreen=pre,
-                              max_evals=8_000_000)
-        runs[name] = {"logz": res["logz"], "logz_err": res["logz_err"],
-                      "n_evals": res["n_evals"], "n_prescreened": res["n_prescreened"],
-                      "n_iter": res["n_iter"], "wall_s": res["wall_s"],
-                      "likelihood_s": like.seconds}
-    a, b = runs["plain"], runs["surrogate"]
-    line = {"metric": "wall time to the evidence estimate, surrogate pre-screen vs plain batched",
-            "workload": WORKLOADS["c5"][0], "n_live": args.live,
-            "plain": a, "surrogate": b,
-            "speedup_wall": a["wall_s"] / b["wall_s"],
-            "exact_evals_saved_frac": 1 - b["n_evals"] / a["n_evals"],
-            "logz_diff_in_sigma": (b["logz"] - a["logz"]) / math.hypot(a["logz_err"], b["logz_err"]),
-            "training": {"pairs": int(screen.n_train), "generation_s": gen_s,
-                         "train_s": screen.train_s, "holdout_rms_y": screen.val_rms,
-                         "margin_y": screen.margin, "screen_s_in_run": screen.screen_s},
+    a = runs["plain"]
+    for k in ("online_surrogate", "global_surrogate"):
+        b = runs[k]
+        b["speedup_wall_vs_plain"] = a["wall_s"] / b["wall_s"]
+        b["exact_evals_vs_plain"] = b["n_evals"] / a["n_evals"]
+        b["logz_diff_in_sigma"] = (b["logz"] - a["logz"]) / math.hypot(a["logz_err"], b["logz_err"])
+    line = {"metric": "wall time to the evidence estimate, surrogate vs plain batched run",
+            "workload": WORKLOADS["c5"][0], "n_live": args.live, "runs": runs,
             "mlp_forward_65536": {"ms": fwd_ms, "tflops": flops / (fwd_ms * 1e-3) / 1e12},
             "data": "synthetic"}
     print(json.dumps(line), flush=True)

@@ -6,9 +6,13 @@ box priors) and evaluates them with one ``lensed_loglike_batch`` call per
 batch; batch sizes are rounded up to a multiple of 128 (padding repeats the
 first point) so the library's CUDA-graph cache sees a handful of shapes.
 
-``SurrogateScreen`` trains the BF16 network on (parameters, logL) pairs from
-earlier exact evaluations and drops, before the exact evaluation, candidates
-it predicts to lie far below the current threshold.  The regression target is
+``SurrogateScreen`` trains the BF16 network once on (parameters, logL) pairs
+from earlier exact evaluations and drops, before the exact evaluation,
+candidates it predicts to lie far below the current threshold.
+``OnlineSurrogate`` retrains it during the run, every few rounds, on the most
+recent exact evaluations with the inputs whitened by the live points'
+covariance, so the network models the likelihood locally (near the current
+contour, where it is close to quadratic) to a few per cent.  The regression target is
 y = log(1 + L_ref - logL) (L_ref the best logL in the training data), which
 spreads the region near the top of the likelihood and compresses the far
 tails; a candidate is kept when its prediction is within `margin` (a multiple
@@ -138,3 +142,88 @@ def _init_params(n_in, H, seed):
              rng.standard_normal((H, H)) * math.sqrt(2.0 / H), np.zeros(H),
              rng.standard_normal(H) * math.sqrt(1.0 / H), np.zeros(1)]
     return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+class OnlineSurrogate:
+    """Surrogate retrained during a nested-sampling run (see the module
+    docstring).  Pass it as the sampler's `prescreen` and its `on_round` as
+    the sampler's `on_round`; it reads the exact evaluations the recording
+    likelihood keeps.  Inactive (the sampler then runs exact walks) until the
+    first fit and whenever the held-out scatter exceeds `max_rms`."""
+
+    def __init__(self, recorder: GpuLikelihood, ndim, hidden=256, retrain_every=8,
+                 window=200_000, min_pairs=20_000, steps=200, batch=8192, lr=1e-3,
+                 margin_sigmas=3.0, max_rms=0.3, seed=0):
+        self.rec = recorder
+        self.ndim = ndim
+        self.net = Surrogate(ndim, hidden, batch)
+        self.net.set_params(_init_params(ndim, hidden, seed))
+        self.retrain_every, self.window, self.min_pairs = retrain_every, window, min_pairs
+        self.steps, self.batch, self.lr = steps, batch, lr
+        self.margin_sigmas, self.max_rms = margin_sigmas, max_rms
+        self.rng = np.random.default_rng(seed)
+        self.round = 0
+        self.active = False
+        self.fits = []
+        self.train_s = 0.0
+        self.screen_s = 0.0
+        self.n_screen = 0
+
+    def _x(self, U):
+        return np.asarray(np.linalg.solve(self.W, (np.asarray(U) - self.c).T).T, np.float32)
+
+    def on_round(self, live_u, live_l, threshold):
+        self.round += 1
+        if self.round % self.retrain_every != 1 and self.retrain_every > 1:
+            return
+        # the most recent exact evaluations, at least `window` of them
+        n, calls = 0, 0
+        for u in reversed(self.rec.U):
+            n += len(u)
+            calls += 1
+            if n >= self.window:
+                break
+        if n < self.min_pairs:
+            return
+        t0 = time.perf_counter()
+        U = np.concatenate(self.rec.U[-calls:])
+        L = np.concatenate(self.rec.L[-calls:])
+        U, L = U[-self.window:], L[-self.window:]
+        ok = np.isfinite(L)
+        U, L = U[ok], L[ok]
+        self.c = live_u.mean(0)
+        self.W = np.linalg.cholesky(np.cov(live_u.T) + 1e-12 * np.eye(self.ndim))
+        self.L_ref = float(max(live_l.max(), L.max()))
+        y = np.log1p(self.L_ref - L)
+        self.y_mean, self.y_std = float(y.mean()), float(y.std() + 1e-12)
+        X = self._x(U)
+        idx = self.rng.permutation(len(U))
+        n_hold = max(2048, len(U) // 20)
+        hold, train = idx[:n_hold], idx[n_hold:]
+        Xd = torch.as_tensor(X[train], device="cuda")
+        Td = torch.as_tensor(((y[train] - self.y_mean) / self.y_std).astype(np.float32),
+                             device="cuda")
+        n = len(train)
+        g = torch.Generator(device="cuda").manual_seed(int(self.round))
+        for s in range(self.steps):
+            j = torch.randint(0, n, (self.batch,), device="cuda", generator=g)
+            self.net.train_step(Xd[j], Td[j], self.lr * (0.5 * (1 + math.cos(math.pi * s / self.steps))) + 1e-5)
+        pred = self.net.forward(X[hold]).cpu().numpy().astype(np.float64) * self.y_std + self.y_mean
+        # scatter of the prediction near the current threshold
+        y_thr = math.log1p(max(self.L_ref - threshold, 0.0))
+        near = np.abs(y[hold] - y_thr) < 1.0
+        resid = (pred - y[hold])[near] if near.sum() > 100 else (pred - y[hold])
+        self.rms = float(np.sqrt(np.mean(resid ** 2)))
+        self.margin = self.margin_sigmas * self.rms
+        self.active = self.rms < self.max_rms
+        self.train_s += time.perf_counter() - t0
+        self.fits.append((self.round, len(U), self.rms, self.active))
+
+    def __call__(self, U, threshold):
+        t0 = time.perf_counter()
+        y_thr = math.log1p(max(self.L_ref - threshold, 0.0))
+        pred = self.net.forward(self._x(U)).cpu().numpy().astype(np.float64)
+        keep = pred * self.y_std + self.y_mean < y_thr + self.margin
+        self.n_screen += len(U)
+        self.screen_s += time.perf_counter() - t0
+        return keep

@@ -16,9 +16,17 @@ in lockstep -- each starts at a surviving live point and takes `walks`
 Metropolis steps under the constraint L > L* (L* the highest removed
 likelihood), with Gaussian steps shaped by the live points' covariance and a
 scale adapted towards a 40 % acceptance -- so every step of all k walks is
-one batched likelihood evaluation.  An optional pre-screen (the surrogate
-network) may reject proposals before the exact evaluation; every accepted
-move is judged by the exact likelihood.
+one batched likelihood evaluation.
+
+With a pre-screen (the surrogate network: prescreen(U, L*) says which points
+it predicts above the threshold, with a safety margin) the intermediate walk
+steps are constrained by the pre-screen alone and only each walk's end point
+is evaluated exactly; an end point replaces a removed point only if its exact
+likelihood exceeds L*.  When the margin-enlarged predicted region contains the
+true contour, those end points are uniform in the contour just as with exact
+walks.  Slots whose end points fail are retried, and after `screen_retries`
+attempts filled by exact walks.  Every accepted point is judged by the exact
+likelihood.
 """
 from __future__ import annotations
 
@@ -31,8 +39,9 @@ import numpy as np
 class Result(dict):
     """logz, logz_err, information, n_evals, n_iter, samples (dead + live, in
     the unit cube), logl, logwt (normalised log posterior weights), wall_s,
-    n_prescreened (proposals the pre-screen rejected), accept (mean walk
-    acceptance)."""
+    n_prescreened (walk proposals the pre-screen rejected), accept (mean
+    exact-walk acceptance), screened_end_accept (fraction of pre-screened walk
+    end points the exact likelihood accepted)."""
 
     def posterior_mean(self):
         w = np.exp(self["logwt"] - self["logwt"].max())
@@ -45,13 +54,17 @@ class Result(dict):
 
 
 def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks=20,
-                    prescreen=None, max_evals=None, callback=None):
+                    prescreen=None, screen_retries=4, max_evals=None, callback=None,
+                    on_round=None):
     """Run nested sampling.
 
     loglike(U) -> logL for a float64 array U [B, ndim] in the unit cube (one
     batched evaluation).  prescreen(U, threshold) -> boolean mask of the
-    proposals worth an exact evaluation (or None).  Stops when the live
-    points can add at most dlogz to log Z (or after max_evals evaluations)."""
+    proposals worth an exact evaluation (or None); a pre-screen whose
+    attribute `active` is False is skipped for that round.  on_round(live_u,
+    live_l, threshold) is called before each round's replacements.  Stops
+    when the live points can add at most dlogz to log Z (or after max_evals
+    evaluations)."""
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
     N = n_live
@@ -59,6 +72,8 @@ def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks
     live_u = rng.random((N, ndim))
     live_l = np.asarray(loglike(live_u), dtype=np.float64)
     n_evals, n_screened, n_prop, n_acc = N, 0, 0, 0
+    n_final, n_final_ok = 0, 0
+    sscale = 1.0
     dead_u, dead_l, dead_logw = [], [], []
     logz, info, logx = -np.inf, 0.0, 0.0
     scale = 1.0
@@ -91,33 +106,62 @@ def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks
             dead_logw.append(logw)
             logx += step
             it += 1
+        if on_round is not None:
+            on_round(live_u[kept], live_l[kept], lstar)
         # k constrained random walks from surviving points
         cov = np.cov(live_u[kept].T) + 1e-12 * np.eye(ndim)
         chol = np.linalg.cholesky(cov)
-        start = kept[rng.integers(0, len(kept), size=k)]
-        cu, cl = live_u[start].copy(), live_l[start].copy()
-        for _ in range(walks):
-            prop = cu + scale * rng.standard_normal((k, ndim)) @ chol.T
-            ok = np.all((prop > 0.0) & (prop < 1.0), axis=1)
-            if prescreen is not None and ok.any():
-                idx = np.nonzero(ok)[0]
-                keep = np.asarray(prescreen(prop[idx], lstar), dtype=bool)
-                n_screened += int((~keep).sum())
-                ok[idx[~keep]] = False
-            acc = np.zeros(k, dtype=bool)
-            if ok.any():
-                idx = np.nonzero(ok)[0]
-                pl = np.asarray(loglike(prop[idx]), dtype=np.float64)
-                n_evals += len(idx)
-                good = pl > lstar
-                acc[idx[good]] = True
-                cu[idx[good]] = prop[idx[good]]
-                cl[idx[good]] = pl[good]
-            frac = acc.mean()
-            n_prop += k
-            n_acc += int(acc.sum())
-            scale *= math.exp(frac - 0.4)
-            scale = min(max(scale, 1e-4), 10.0)
+        cu = np.empty((k, ndim))
+        cl = np.empty(k)
+        todo = np.arange(k)
+        if prescreen is not None and getattr(prescreen, "active", True):
+            # walks constrained by the pre-screen; exact check of the end points
+            for _ in range(screen_retries):
+                if len(todo) == 0:
+                    break
+                m = len(todo)
+                start = kept[rng.integers(0, len(kept), size=m)]
+                wu = live_u[start].copy()
+                for _ in range(walks):
+                    prop = wu + sscale * rng.standard_normal((m, ndim)) @ chol.T
+                    ok = np.all((prop > 0.0) & (prop < 1.0), axis=1)
+                    idx = np.nonzero(ok)[0]
+                    if len(idx):
+                        ok[idx] = np.asarray(prescreen(prop[idx], lstar), dtype=bool)
+                    n_screened += int(len(idx) - ok.sum())
+                    wu[ok] = prop[ok]
+                    frac = ok.mean()
+                    sscale = min(max(sscale * math.exp(frac - 0.4), 1e-4), 10.0)
+                wl = np.asarray(loglike(wu), dtype=np.float64)
+                n_evals += m
+                good = wl > lstar
+                n_final += m
+                n_final_ok += int(good.sum())
+                cu[todo[good]] = wu[good]
+                cl[todo[good]] = wl[good]
+                todo = todo[~good]
+        if len(todo):
+            m = len(todo)
+            start = kept[rng.integers(0, len(kept), size=m)]
+            wu, wl = live_u[start].copy(), live_l[start].copy()
+            for _ in range(walks):
+                prop = wu + scale * rng.standard_normal((m, ndim)) @ chol.T
+                ok = np.all((prop > 0.0) & (prop < 1.0), axis=1)
+                acc = np.zeros(m, dtype=bool)
+                if ok.any():
+                    idx = np.nonzero(ok)[0]
+                    pl = np.asarray(loglike(prop[idx]), dtype=np.float64)
+                    n_evals += len(idx)
+                    good = pl > lstar
+                    acc[idx[good]] = True
+                    wu[idx[good]] = prop[idx[good]]
+                    wl[idx[good]] = pl[good]
+                frac = acc.mean()
+                n_prop += m
+                n_acc += int(acc.sum())
+                scale = min(max(scale * math.exp(frac - 0.4), 1e-4), 10.0)
+            cu[todo] = wu
+            cl[todo] = wl
         live_u[gone] = cu
         live_l[gone] = cl
         if callback:
@@ -132,4 +176,5 @@ def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks
     return Result(logz=float(logz), logz_err=float(math.sqrt(max(info, 0.0) / N)),
                   information=float(info), n_evals=int(n_evals), n_iter=it, samples=samples,
                   logl=logl, logwt=logw + logl - logz, wall_s=time.perf_counter() - t0,
-                  n_prescreened=n_screened, accept=n_acc / max(n_prop, 1))
+                  n_prescreened=n_screened, accept=n_acc / max(n_prop, 1),
+                  screened_end_accept=n_final_ok / max(n_final, 1))

@@ -60,3 +60,18 @@ def test_surrogate_prescreen_same_evidence_fewer_exact_evals(setup):
                         prescreen=screen)
     assert b["n_prescreened"] > 0 and b["n_evals"] < a["n_evals"]
     assert abs(a["logz"] - b["logz"]) < 4 * math.hypot(a["logz_err"], b["logz_err"]), (a["logz"], b["logz"])
+
+
+def test_online_surrogate_same_evidence_fewer_exact_evals(setup):
+    from paper_1505_07674_gb300.posterior import GpuLikelihood, OnlineSurrogate
+    from paper_1505_07674_gb300.sampler import nested_sampling
+    spec, m = setup
+    a = nested_sampling(GpuLikelihood(m, spec), 13, 200, seed=9, dlogz=0.2)
+    rec = GpuLikelihood(m, spec, record=True)
+    online = OnlineSurrogate(rec, 13, retrain_every=4, window=60_000, min_pairs=8_000,
+                             batch=4096)
+    b = nested_sampling(rec, 13, 200, seed=9, dlogz=0.2, prescreen=online,
+                        on_round=online.on_round)
+    assert any(f[3] for f in online.fits), online.fits
+    assert b["n_evals"] < a["n_evals"]
+    assert abs(a["logz"] - b["logz"]) < 4 * math.hypot(a["logz_err"], b["logz_err"]), (a["logz"], b["logz"])

@@ -33,17 +33,18 @@ def test_gaussian_evidence_and_mean(d, s, n_live):
     assert 0.1 < res["accept"] < 0.9
 
 
-def test_prescreen_below_threshold_changes_nothing_but_work():
+def test_prescreened_walks_keep_the_evidence_and_save_exact_evaluations():
     mu, s, d = np.full(3, 0.6), 0.07, 3
     f = gauss(mu, s)
     plain = nested_sampling(f, d, 200, seed=3, dlogz=0.05)
-    # an exact pre-screen: drops only proposals the exact likelihood rejects,
-    # so the walks are the same moves with fewer exact evaluations
+    # a pre-screen whose predicted region contains the true contour (here
+    # the exact constraint loosened by 1): walks are constrained by it and
+    # only their end points are evaluated exactly
     screened = nested_sampling(f, d, 200, seed=3, dlogz=0.05,
-                               prescreen=lambda U, thr: f(U) > thr)
-    assert screened["logz"] == plain["logz"]
+                               prescreen=lambda U, thr: f(U) > thr - 1.0)
     assert screened["n_prescreened"] > 0
-    assert screened["n_evals"] < plain["n_evals"]
+    assert screened["n_evals"] < 0.5 * plain["n_evals"]
+    assert 0.05 < screened["screened_end_accept"] < 1.0
     exact = 0.5 * d * math.log(2 * math.pi * s * s)
     for r in (plain, screened):
         assert abs(r["logz"] - exact) < 4 * r["logz_err"] + 0.05
