@@ -284,8 +284,9 @@ def run_surrogate(args):
     plain batched run (same seed).  Two surrogate modes: retrained online
     during the run on its own exact evaluations (whitened inputs), and
     trained once on the (parameters, logL) pairs of an earlier run (at most
-    2M).  In both the network constrains the intermediate walk steps and
-    the exact likelihood judges every end point."""
+    2M).  In both the network is the first stage of delayed-acceptance walk
+    steps: proposals it rejects skip the exact evaluation; the exact
+    likelihood judges every accepted point."""
     import torch
 
     import workloads as W
@@ -301,8 +302,7 @@ def run_surrogate(args):
     def summary(res, like, extra=None):
         d = {"logz": res["logz"], "logz_err": res["logz_err"], "n_evals": res["n_evals"],
              "n_iter": res["n_iter"], "wall_s": res["wall_s"], "likelihood_s": like.seconds,
-             "n_prescreened": res["n_prescreened"],
-             "screened_end_accept": res["screened_end_accept"]}
+             "n_prescreened": res["n_prescreened"], "walk_accept": res["accept"]}
         d.update(extra or {})
         return d
 
@@ -325,7 +325,7 @@ def run_surrogate(args):
     gen_s = time.perf_counter() - t0
     U = np.concatenate(gen.U)[-2_000_000:]
     L = np.concatenate(gen.L)[-2_000_000:]
-    screen = SurrogateScreen(gen.ndim, 256, 8192).fit(U, L, epochs=20, margin_sigmas=2.0)
+    screen = SurrogateScreen(gen.ndim, 256, 8192).fit(U, L, epochs=20, margin_sigmas=4.0)
     like = GpuLikelihood(m, spec)
     res = nested_sampling(like, like.ndim, args.live, seed=12, dlogz=0.1, prescreen=screen,
                           max_evals=8_000_000)

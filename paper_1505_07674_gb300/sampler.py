@@ -18,15 +18,16 @@ likelihood), with Gaussian steps shaped by the live points' covariance and a
 scale adapted towards a 40 % acceptance -- so every step of all k walks is
 one batched likelihood evaluation.
 
-With a pre-screen (the surrogate network: prescreen(U, L*) says which points
-it predicts above the threshold, with a safety margin) the intermediate walk
-steps are constrained by the pre-screen alone and only each walk's end point
-is evaluated exactly; an end point replaces a removed point only if its exact
-likelihood exceeds L*.  When the margin-enlarged predicted region contains the
-true contour, those end points are uniform in the contour just as with exact
-walks.  Slots whose end points fail are retried, and after `screen_retries`
-attempts filled by exact walks.  Every accepted point is judged by the exact
-likelihood.
+With a pre-screen (the surrogate network: prescreen(U, L*) says which
+points it predicts above the threshold, with a safety margin) each walk step
+is a two-stage (delayed-acceptance, Christen & Fox 2005) Metropolis step: a
+proposal the pre-screen places outside is rejected without an exact
+evaluation; one it lets through is evaluated exactly and accepted iff
+L > L*.  For the uniform target on the contour this chain samples exactly the
+part of the contour inside the pre-screen's region -- the whole contour when
+the margin-enlarged region contains it -- and every accepted point is judged
+by the exact likelihood; the saving is the exact evaluations of the rejected
+proposals the pre-screen catches.
 """
 from __future__ import annotations
 
@@ -39,9 +40,8 @@ import numpy as np
 class Result(dict):
     """logz, logz_err, information, n_evals, n_iter, samples (dead + live, in
     the unit cube), logl, logwt (normalised log posterior weights), wall_s,
-    n_prescreened (walk proposals the pre-screen rejected), accept (mean
-    exact-walk acceptance), screened_end_accept (fraction of pre-screened walk
-    end points the exact likelihood accepted)."""
+    n_prescreened (walk proposals the pre-screen rejected without an exact
+    evaluation), accept (mean walk acceptance)."""
 
     def posterior_mean(self):
         w = np.exp(self["logwt"] - self["logwt"].max())
@@ -54,8 +54,7 @@ class Result(dict):
 
 
 def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks=20,
-                    prescreen=None, screen_retries=4, max_evals=None, callback=None,
-                    on_round=None):
+                    prescreen=None, max_evals=None, callback=None, on_round=None):
     """Run nested sampling.
 
     loglike(U) -> logL for a float64 array U [B, ndim] in the unit cube (one
@@ -72,8 +71,6 @@ def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks
     live_u = rng.random((N, ndim))
     live_l = np.asarray(loglike(live_u), dtype=np.float64)
     n_evals, n_screened, n_prop, n_acc = N, 0, 0, 0
-    n_final, n_final_ok = 0, 0
-    sscale = 1.0
     dead_u, dead_l, dead_logw = [], [], []
     logz, info, logx = -np.inf, 0.0, 0.0
     scale = 1.0
@@ -111,57 +108,31 @@ def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks
         # k constrained random walks from surviving points
         cov = np.cov(live_u[kept].T) + 1e-12 * np.eye(ndim)
         chol = np.linalg.cholesky(cov)
-        cu = np.empty((k, ndim))
-        cl = np.empty(k)
-        todo = np.arange(k)
-        if prescreen is not None and getattr(prescreen, "active", True):
-            # walks constrained by the pre-screen; exact check of the end points
-            for _ in range(screen_retries):
-                if len(todo) == 0:
-                    break
-                m = len(todo)
-                start = kept[rng.integers(0, len(kept), size=m)]
-                wu = live_u[start].copy()
-                for _ in range(walks):
-                    prop = wu + sscale * rng.standard_normal((m, ndim)) @ chol.T
-                    ok = np.all((prop > 0.0) & (prop < 1.0), axis=1)
-                    idx = np.nonzero(ok)[0]
-                    if len(idx):
-                        ok[idx] = np.asarray(prescreen(prop[idx], lstar), dtype=bool)
-                    n_screened += int(len(idx) - ok.sum())
-                    wu[ok] = prop[ok]
-                    frac = ok.mean()
-                    sscale = min(max(sscale * math.exp(frac - 0.4), 1e-4), 10.0)
-                wl = np.asarray(loglike(wu), dtype=np.float64)
-                n_evals += m
-                good = wl > lstar
-                n_final += m
-                n_final_ok += int(good.sum())
-                cu[todo[good]] = wu[good]
-                cl[todo[good]] = wl[good]
-                todo = todo[~good]
-        if len(todo):
-            m = len(todo)
-            start = kept[rng.integers(0, len(kept), size=m)]
-            wu, wl = live_u[start].copy(), live_l[start].copy()
-            for _ in range(walks):
-                prop = wu + scale * rng.standard_normal((m, ndim)) @ chol.T
-                ok = np.all((prop > 0.0) & (prop < 1.0), axis=1)
-                acc = np.zeros(m, dtype=bool)
-                if ok.any():
-                    idx = np.nonzero(ok)[0]
-                    pl = np.asarray(loglike(prop[idx]), dtype=np.float64)
-                    n_evals += len(idx)
-                    good = pl > lstar
-                    acc[idx[good]] = True
-                    wu[idx[good]] = prop[idx[good]]
-                    wl[idx[good]] = pl[good]
-                frac = acc.mean()
-                n_prop += m
-                n_acc += int(acc.sum())
-                scale = min(max(scale * math.exp(frac - 0.4), 1e-4), 10.0)
-            cu[todo] = wu
-            cl[todo] = wl
+        screen = prescreen if (prescreen is not None and
+                               getattr(prescreen, "active", True)) else None
+        start = kept[rng.integers(0, len(kept), size=k)]
+        cu, cl = live_u[start].copy(), live_l[start].copy()
+        for _ in range(walks):
+            prop = cu + scale * rng.standard_normal((k, ndim)) @ chol.T
+            ok = np.all((prop > 0.0) & (prop < 1.0), axis=1)
+            if screen is not None and ok.any():
+                idx = np.nonzero(ok)[0]
+                keep = np.asarray(screen(prop[idx], lstar), dtype=bool)
+                n_screened += int((~keep).sum())
+                ok[idx[~keep]] = False
+            acc = np.zeros(k, dtype=bool)
+            if ok.any():
+                idx = np.nonzero(ok)[0]
+                pl = np.asarray(loglike(prop[idx]), dtype=np.float64)
+                n_evals += len(idx)
+                good = pl > lstar
+                acc[idx[good]] = True
+                cu[idx[good]] = prop[idx[good]]
+                cl[idx[good]] = pl[good]
+            frac = acc.mean()
+            n_prop += k
+            n_acc += int(acc.sum())
+            scale = min(max(scale * math.exp(frac - 0.4), 1e-4), 10.0)
         live_u[gone] = cu
         live_l[gone] = cl
         if callback:
@@ -176,5 +147,4 @@ def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks
     return Result(logz=float(logz), logz_err=float(math.sqrt(max(info, 0.0) / N)),
                   information=float(info), n_evals=int(n_evals), n_iter=it, samples=samples,
                   logl=logl, logwt=logw + logl - logz, wall_s=time.perf_counter() - t0,
-                  n_prescreened=n_screened, accept=n_acc / max(n_prop, 1),
-                  screened_end_accept=n_final_ok / max(n_final, 1))
+                  n_prescreened=n_screened, accept=n_acc / max(n_prop, 1))
