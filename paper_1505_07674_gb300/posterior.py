@@ -151,8 +151,8 @@ class OnlineSurrogate:
     likelihood keeps.  Inactive (the sampler then runs exact walks) until the
     first fit and whenever the held-out scatter exceeds `max_rms`."""
 
-    def __init__(self, recorder: GpuLikelihood, ndim, hidden=256, retrain_every=8,
-                 window=200_000, min_pairs=20_000, steps=200, batch=8192, lr=1e-3,
+    def __init__(self, recorder: GpuLikelihood, ndim, hidden=256, retrain_every=12,
+                 window=150_000, min_pairs=20_000, steps=120, batch=8192, lr=1e-3,
                  margin_sigmas=3.0, max_rms=0.3, seed=0):
         self.rec = recorder
         self.ndim = ndim
