@@ -14,6 +14,10 @@
  *             Eq. 2  image-plane brightness I(x) = I_L(x) + I_S(y(x))
  *             Eq. 3  pixel luminosity       L_i = integral of I over pixel i
  *   Sec. 3.1  Eq. 14 quadrature             L_i ~ sum_k w_k I(x_k)
+ *                    (rules of Sec. 4.5: point, subN, Gauss-Kronrod gNk(2N+1)
+ *                     as the Cartesian square of the 1-D rule; the embedded
+ *                     N x N Gauss rule gives the per-pixel error estimate
+ *                     |L_Kronrod - L_Gauss| of the unconvolved luminosity)
  *             Eq. 15 discrete PSF           L*_ij = sum_kl F_{-k,-l} L_{i+k,j+l}
  *                    (PSF normalised to unit sum; border padded by repeating
  *                     the nearest pixel)
@@ -56,8 +60,9 @@ enum { ORA_SIE = 1, ORA_SHEAR = 2, ORA_POINTMASS = 3,
 /* planes: mass on the lens plane, light on the lens plane (unlensed,
  * evaluated at x) or on the source plane (lensed, evaluated at y) */
 enum { ORA_PLANE_LENS = 0, ORA_PLANE_FOREGROUND = 1, ORA_PLANE_SOURCE = 2 };
-/* integration rules of Sec. 4.5 (point, subN) plus Gauss-Legendre N x N */
-enum { ORA_RULE_POINT = 0, ORA_RULE_SUB = 1, ORA_RULE_GL = 2 };
+/* integration rules of Sec. 4.5 (point, subN, Gauss-Kronrod gNk(2N+1)) plus
+ * Gauss-Legendre N x N */
+enum { ORA_RULE_POINT = 0, ORA_RULE_SUB = 1, ORA_RULE_GL = 2, ORA_RULE_GK = 3 };
 
 #define ORA_MAXPAR 8
 
@@ -147,6 +152,118 @@ int ora_gauss_legendre(int n, double *x, double *w)
     return found == n ? 0 : -2;
 }
 
+/* Dense linear solve (Gaussian elimination with partial pivoting), n <= 64. */
+static int solve(int n, double *A, double *b)
+{
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(A[r * n + c]) > fabs(A[piv * n + c])) piv = r;
+        if (A[piv * n + c] == 0.0) return -1;
+        if (piv != c) {
+            for (int k = 0; k < n; ++k) {
+                double t = A[c * n + k]; A[c * n + k] = A[piv * n + k]; A[piv * n + k] = t;
+            }
+            double t = b[c]; b[c] = b[piv]; b[piv] = t;
+        }
+        for (int r = c + 1; r < n; ++r) {
+            double f = A[r * n + c] / A[c * n + c];
+            for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double s = b[r];
+        for (int k = r + 1; k < n; ++k) s -= A[r * n + k] * b[k];
+        b[r] = s / A[r * n + r];
+    }
+    return 0;
+}
+
+/* Gauss-Kronrod rule with 2n+1 points on [-1, 1] (Kronrod's extension of the
+ * n-point Gauss rule, the rules of Sec. 3.1 and Sec. 4.5, Patterson 1968).
+ * The n+1 new nodes are the roots of the Stieltjes polynomial E_{n+1}: the
+ * monic-in-P_{n+1} combination E = P_{n+1} + sum_j a_j P_j (j < n+1 of the
+ * parity of n+1) with integral of P_n E P_k = 0 for k = 0..n, solved with the
+ * integrals done by a 64-point Gauss-Legendre rule (exact here).  The
+ * weights make the rule exact on P_0..P_{2n} (Legendre moments).  Outputs
+ * the 2n+1 nodes ascending, the Kronrod weights wk and the embedded Gauss
+ * weights wg (zero on the new nodes). */
+int ora_gauss_kronrod(int n, double *x, double *wk, double *wg)
+{
+    if (n < 1 || n > 7) return -1;
+    double gx[64], gw[64];
+    if (ora_gauss_legendre(64, gx, gw) != 0) return -2;
+    /* unknown coefficients a_j for j = n+1-2, n+1-4, ... >= 0 */
+    int js[16], m = 0;
+    for (int j = n - 1; j >= 0; j -= 2) js[m++] = j;
+    /* conditions for k of the parity of n+1+n ... choose k with nonzero
+     * integrals: k = 0..n with (n + k + j) even for some j; use the m
+     * lowest such k */
+    int ks[16], mk = 0;
+    for (int k = 0; k <= n && mk < m; ++k)
+        if ((n + k + (n + 1)) % 2 == 0) ks[mk++] = k;
+    if (mk != m) return -3;
+    double A[256], b[16];
+    for (int r = 0; r < m; ++r) {
+        double rhs = 0.0;
+        for (int c = 0; c < m; ++c) A[r * m + c] = 0.0;
+        for (int q = 0; q < 64; ++q) {
+            double pn, d, pk, pj, pe;
+            legendre(n, gx[q], &pn, &d);
+            legendre(ks[r], gx[q], &pk, &d);
+            legendre(n + 1, gx[q], &pe, &d);
+            rhs -= gw[q] * pn * pk * pe;
+            for (int c = 0; c < m; ++c) {
+                legendre(js[c], gx[q], &pj, &d);
+                A[r * m + c] += gw[q] * pn * pk * pj;
+            }
+        }
+        b[r] = rhs;
+    }
+    if (m > 0 && solve(m, A, b) != 0) return -4;
+    /* E(x) and its roots by sign changes + bisection */
+    double ex[16];
+    int found = 0, grid = 20001;
+    double xa = -1.0, ea = 0.0, d;
+    for (int g = 0; g <= grid; ++g) {
+        double xb = -1.0 + 2.0 * g / grid, eb, t;
+        legendre(n + 1, xb, &eb, &d);
+        for (int c = 0; c < m; ++c) { legendre(js[c], xb, &t, &d); eb += b[c] * t; }
+        if (g > 0 && (ea < 0.0) != (eb < 0.0)) {
+            double lo = xa, hi = xb, elo = ea;
+            for (int it = 0; it < 200; ++it) {
+                double mid = 0.5 * (lo + hi), em;
+                if (mid <= lo || mid >= hi) break;
+                legendre(n + 1, mid, &em, &d);
+                for (int c = 0; c < m; ++c) { legendre(js[c], mid, &t, &d); em += b[c] * t; }
+                if ((em < 0.0) == (elo < 0.0)) { lo = mid; elo = em; } else hi = mid;
+            }
+            if (found < 16) ex[found++] = 0.5 * (lo + hi);
+        }
+        xa = xb;
+        ea = eb;
+    }
+    if (found != n + 1) return -5;
+    /* merge with the Gauss nodes, ascending */
+    double gxn[16], gwn[16];
+    if (ora_gauss_legendre(n, gxn, gwn) != 0) return -6;
+    int N = 2 * n + 1, ig = 0, ie = 0;
+    for (int k = 0; k < N; ++k) {
+        if (ie < n + 1 && (ig >= n || ex[ie] < gxn[ig])) { x[k] = ex[ie++]; wg[k] = 0.0; }
+        else { x[k] = gxn[ig]; wg[k] = gwn[ig]; ++ig; }
+    }
+    /* Kronrod weights: sum_i w_i P_k(x_i) = integral of P_k = 2 delta_k0 */
+    double M[31 * 31], r[31];
+    for (int k = 0; k < N; ++k) {
+        for (int i = 0; i < N; ++i) { double p; legendre(k, x[i], &p, &d); M[k * N + i] = p; }
+        r[k] = k == 0 ? 2.0 : 0.0;
+    }
+    if (solve(N, M, r) != 0) return -7;
+    for (int i = 0; i < N; ++i) wk[i] = r[i];
+    return 0;
+}
+
 /* 1-D rule on the unit pixel: abscissae t in (-1/2, 1/2), weights summing
  * to one (Eq. 14; the 2-D rule is the Cartesian square). */
 int ora_rule_nodes(int rule, int order, double *t, double *wt)
@@ -159,6 +276,12 @@ int ora_rule_nodes(int rule, int order, double *t, double *wt)
             wt[a] = 1.0 / order;
         }
         return order;
+    }
+    if (rule == ORA_RULE_GK) {
+        double x[15], wk[15], wg[15];
+        if (ora_gauss_kronrod(order, x, wk, wg) != 0) return -1;
+        for (int a = 0; a < 2 * order + 1; ++a) { t[a] = 0.5 * x[a]; wt[a] = 0.5 * wk[a]; }
+        return 2 * order + 1;
     }
     if (rule == ORA_RULE_GL) {
         if (order < 1 || order > 128) return -1;
@@ -398,6 +521,31 @@ static void psf_convolve(const ora_system *sys, const double *L, double *Ls)
                 }
             Ls[i * nx + j] = s;
         }
+}
+
+/* Per-pixel integration error estimate of a Gauss-Kronrod system (Sec. 3.1,
+ * the embedded-Gauss estimate): |L_K - L_G| with L_K the (2N+1)^2-point
+ * Kronrod luminosity and L_G the N^2-point Gauss luminosity of the same
+ * pixel, both unconvolved.  Returns 0, 1 outside the domain, -1 if the
+ * system's rule is not Gauss-Kronrod. */
+int ora_render_error(const ora_system *sys, const double *xi, double *err)
+{
+    ora_comp_eval ce[64];
+    double tk[64], wk[64], tg[64], wg[64];
+    if (sys->rule != ORA_RULE_GK || sys->ncomp > 64) return -1;
+    int nk = ora_rule_nodes(ORA_RULE_GK, sys->order, tk, wk);
+    int ng = ora_rule_nodes(ORA_RULE_GL, sys->order, tg, wg);
+    if (nk < 1 || ng < 1) return -1;
+    if (!resolve(sys, xi, ce)) return 1;
+    int n = sys->nx * sys->ny;
+    double *LK = (double *)malloc(sizeof(double) * n);
+    double *LG = (double *)malloc(sizeof(double) * n);
+    pixel_luminosities(sys, ce, tk, wk, nk, LK);
+    pixel_luminosities(sys, ce, tg, wg, ng, LG);
+    for (int i = 0; i < n; ++i) err[i] = fabs(LK[i] - LG[i]);
+    free(LK);
+    free(LG);
+    return 0;
 }
 
 /* Weights w_i = extra_i / s_i^2 (Sec. 3.2, Sec. 3.3), zero where masked. */

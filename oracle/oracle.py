@@ -22,7 +22,7 @@ _OUT = os.path.join(_HERE, "_build", "liblensed_oracle.so")
 
 TYPES = {"sie": 1, "shear": 2, "pointmass": 3, "sersic": 4, "devauc": 5, "gauss": 6}
 PLANES = {"lens": 0, "foreground": 1, "source": 2}
-RULES = {"point": 0, "sub": 1, "gl": 2}
+RULES = {"point": 0, "sub": 1, "gl": 2, "gk": 3}
 MAXPAR = 8
 
 
@@ -64,6 +64,8 @@ def lib():
         dp = C.POINTER(C.c_double)
         L.ora_gauss_legendre.argtypes = [C.c_int, dp, dp]
         L.ora_rule_nodes.argtypes = [C.c_int, C.c_int, dp, dp]
+        L.ora_gauss_kronrod.argtypes = [C.c_int, dp, dp, dp]
+        L.ora_render_error.argtypes = [C.c_void_p, dp, dp]
         L.ora_gammainc_lower.argtypes = [C.c_double, C.c_double]
         L.ora_gammainc_lower.restype = C.c_double
         L.ora_sersic_bn.argtypes = [C.c_double]
@@ -156,6 +158,17 @@ class OracleSystem:
             return None
         return out.reshape(self.spec["ny"], self.spec["nx"])
 
+    def render_error(self, xi):
+        """Per-pixel Gauss-Kronrod error estimate |L_K - L_G| (unconvolved)."""
+        xi = np.ascontiguousarray(xi, dtype=np.float64)
+        out = np.zeros(self.spec["ny"] * self.spec["nx"])
+        rc = lib().ora_render_error(C.byref(self.sys), _dp(xi), _dp(out))
+        if rc < 0:
+            raise RuntimeError("oracle error map failed (rule not Gauss-Kronrod?)")
+        if rc == 1:
+            return None
+        return out.reshape(self.spec["ny"], self.spec["nx"])
+
     def loglike(self, xis, nthreads=None):
         xis = np.ascontiguousarray(np.atleast_2d(xis), dtype=np.float64)
         assert xis.shape[1] == self.spec["n_params"]
@@ -198,6 +211,16 @@ def gauss_legendre(n):
     if lib().ora_gauss_legendre(n, _dp(x), _dp(w)) != 0:
         raise RuntimeError("gauss_legendre failed")
     return x, w
+
+
+def gauss_kronrod(n):
+    """(2n+1)-point Kronrod extension of the n-point Gauss rule on [-1, 1]:
+    nodes ascending, Kronrod weights, embedded Gauss weights (zero on the
+    added nodes)."""
+    x, wk, wg = np.zeros(2 * n + 1), np.zeros(2 * n + 1), np.zeros(2 * n + 1)
+    if lib().ora_gauss_kronrod(n, _dp(x), _dp(wk), _dp(wg)) != 0:
+        raise RuntimeError("gauss_kronrod failed")
+    return x, wk, wg
 
 
 def rule_nodes(rule, order):

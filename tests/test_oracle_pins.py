@@ -66,6 +66,86 @@ def test_sub_and_point_rules():
     assert np.allclose(t, [-0.375, -0.125, 0.125, 0.375]) and np.allclose(w, 0.25)
 
 
+# Gauss-Kronrod rules g3k7 / g5k11 / g7k15 (Sec. 3.1 default rule, Sec. 4.5)
+
+# 15-point Kronrod extension of the 7-point Gauss rule as tabulated in
+# QUADPACK (Piessens et al. 1983), the non-negative half: nodes, Kronrod
+# weights, Gauss weights on the shared nodes.
+G7K15_X = [0.991455371120812639, 0.949107912342758525, 0.864864423359769073,
+           0.741531185599394440, 0.586087235467691130, 0.405845151377397167,
+           0.207784955007898468, 0.0]
+G7K15_WK = [0.022935322010529225, 0.063092092629978553, 0.104790010322250184,
+            0.140653259715525919, 0.169004726639267903, 0.190350578064785410,
+            0.204432940075298892, 0.209482141084727828]
+G7K15_WG = [0.129484966168869693, 0.279705391489276668, 0.381830050505118945,
+            0.417959183673469388]
+
+
+def test_g7k15_matches_published_table():
+    x, wk, wg = O.gauss_kronrod(7)
+    assert np.allclose(x[7:][::-1], G7K15_X, rtol=0, atol=2e-15)
+    assert np.allclose(x[:8], -np.array(G7K15_X), rtol=0, atol=2e-15)
+    assert np.allclose(wk[7:][::-1], G7K15_WK, rtol=0, atol=2e-15)
+    assert np.allclose(wg[7:][::-1][1::2], G7K15_WG, rtol=0, atol=2e-15)
+    assert np.all(wg[7:][::-1][0::2] == 0.0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7])
+def test_kronrod_extension_properties(n):
+    x, wk, wg = O.gauss_kronrod(n)
+    # the embedded rule is the n-point Gauss-Legendre rule
+    gx, gw = np.polynomial.legendre.leggauss(n)
+    shared = wg != 0.0
+    assert shared.sum() == n
+    assert np.allclose(x[shared], gx, atol=1e-14) and np.allclose(wg[shared], gw, atol=1e-14)
+    # added nodes interlace with the Gauss nodes (one on each side and one
+    # between every pair), all weights positive
+    assert np.all(np.diff(x) > 0) and np.all(wk > 0)
+    assert shared[1::2].all() and not shared[0::2].any()
+    # exact on x^k up to degree 3n+1 (3n+2 for odd n by symmetry) and not beyond
+    deg = 3 * n + 1 + (n % 2)
+    for k in range(deg + 1):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs((wk * x ** k).sum() - exact) < 1e-14, k
+    k = deg + 1 if (deg + 1) % 2 == 0 else deg + 2
+    assert abs((wk * x ** k).sum() - 2.0 / (k + 1)) > 1e-10
+
+
+def test_kronrod_smallest_case_is_three_point_gauss():
+    # the Kronrod extension of the 1-point rule is the 3-point Gauss rule
+    x, wk, _ = O.gauss_kronrod(1)
+    assert np.allclose(x, [-math.sqrt(0.6), 0.0, math.sqrt(0.6)], atol=1e-15)
+    assert np.allclose(wk, [5 / 9, 8 / 9, 5 / 9], atol=1e-15)
+    t, w = O.rule_nodes("gk", 3)
+    assert len(t) == 7 and abs(w.sum() - 1.0) < 1e-15 and np.all(np.abs(t) < 0.5)
+
+
+def test_kronrod_error_estimate_tracks_gauss_error():
+    # The per-pixel error estimate |L_K - L_G| measures the error of the
+    # embedded Gauss rule: against a 64 x 64 Gauss-Legendre integral of a
+    # lensed arc, |L_ref - L_G| agrees with it to a few per cent wherever
+    # the error is not negligible, and the Kronrod luminosity itself is much
+    # closer to the reference than the Gauss one.
+    comps = [component("sie", "lens", [fixed(0.02), fixed(0.0), fixed(0.2), fixed(0.7), fixed(30),
+                                       fixed(0.0)]),
+             component("sersic", "source", [fixed(0.01), fixed(0.005), fixed(0.03), fixed(0),
+                                            fixed(0.5), fixed(0.8), fixed(0)])]
+    for n in (3, 5):
+        spec = make_spec(comps, nx=16, ny=16, h=0.04, rule=("gk", n))
+        err = O.OracleSystem(spec).render_error(np.zeros(0))
+        LK = O.OracleSystem(spec).render(np.zeros(0), convolved=False)
+        LG = O.OracleSystem(make_spec(comps, nx=16, ny=16, h=0.04, rule=("gl", n))).render(
+            np.zeros(0), convolved=False)
+        ref = O.OracleSystem(make_spec(comps, nx=16, ny=16, h=0.04, rule=("gl", 64))).render(
+            np.zeros(0), convolved=False)
+        assert np.array_equal(err, np.abs(LK - LG))
+        true_g = np.abs(ref - LG)
+        big = true_g > 1e-3 * true_g.max()
+        assert big.sum() > 10
+        assert np.allclose(err[big], true_g[big], rtol=0.05), np.abs(err[big] / true_g[big] - 1).max()
+        assert np.abs(LK - ref).max() < 0.05 * true_g.max()
+
+
 # --------------------------------------------------------------------------
 # Sersic law (Sec. 4.1, Eqs. 22-23)
 
