@@ -89,8 +89,14 @@ enum {
  * Cartesian square of a 1-D rule on the pixel:
  *   LENSED_RULE_POINT  one ray at the pixel centre (rule_order ignored)
  *   LENSED_RULE_SUB    rule_order x rule_order uniform sub-sampling
- *   LENSED_RULE_GL     rule_order x rule_order Gauss-Legendre            */
-enum { LENSED_RULE_POINT = 0, LENSED_RULE_SUB = 1, LENSED_RULE_GL = 2 };
+ *   LENSED_RULE_GL     rule_order x rule_order Gauss-Legendre
+ *   LENSED_RULE_GK     Gauss-Kronrod: the (2N+1) x (2N+1) Kronrod extension
+ *                      of the N x N Gauss rule, N = rule_order in 1..7
+ *                      (g3k7 is N = 3, the paper's default; g5k11 N = 5;
+ *                      g7k15 N = 7); lensed_render_error gives its
+ *                      embedded-Gauss error estimate per pixel            */
+enum { LENSED_RULE_POINT = 0, LENSED_RULE_SUB = 1, LENSED_RULE_GL = 2, LENSED_RULE_GK = 3 };
+#define LENSED_MAX_KRONROD_ORDER 7
 
 /* Arithmetic of the evaluation:
  *   LENSED_PREC_FP32   rays, brightness and PSF in FP32; chi^2 summed in FP64
@@ -170,6 +176,16 @@ typedef struct {
 int lensed_create_model(const lensed_system_desc *systems, int n_systems, int precision,
                         lensed_model **out);
 
+/* The 1-D integration rule on the unit pixel that a system with this rule
+ * and order uses (Sec. 3.1, Eq. 14; the 2-D rule is its Cartesian square):
+ * writes the offsets t (in (-1/2, 1/2), ascending) and weights w (summing
+ * to one) into HOST arrays of at least LENSED_MAX_RULE_ORDER doubles, and
+ * for LENSED_RULE_GK the embedded Gauss weights into w_gauss (zero on the
+ * Kronrod-only nodes; may be NULL).  Returns the number of nodes, or
+ * LENSED_E_ARG for an unknown rule or an order out of range.  Host only:
+ * needs no device. */
+int lensed_rule_nodes(int rule, int order, double *t, double *w, double *w_gauss);
+
 /* Free everything the model owns.  NULL-safe.  Synchronises the device
  * work the model has in flight before freeing. */
 void lensed_destroy(lensed_model *m);
@@ -184,6 +200,21 @@ int lensed_model_info_get(const lensed_model *m, lensed_model_info *info);
  * the domain the image is filled with NaN.  Asynchronous on stream. */
 int lensed_render(lensed_model *m, int system, const double *params, int flags,
                   float *out_image, void *stream);
+
+/* Per-pixel integration error estimate of one Gauss-Kronrod system (Sec.
+ * 3.1: the Gauss rule embedded in the Kronrod rule estimates each pixel's
+ * quadrature error, kept as a diagnostic beside the image).  Writes
+ * |L_K - L_G| for every pixel into out_error, a DEVICE array of ny*nx floats
+ * (row-major), where L_K is the unconvolved pixel luminosity by the
+ * (2N+1)^2-point Kronrod rule (what lensed_render writes with
+ * LENSED_RENDER_UNCONVOLVED) and L_G the one by the N^2-point Gauss rule on
+ * the shared nodes, both in the model's precision.  params is a DEVICE
+ * array of the system's n_params doubles.  Returns LENSED_E_ARG if the
+ * system's rule is not LENSED_RULE_GK.  Outside the domain the map is NaN.
+ * Asynchronous on stream; it shares the model's render scratch with
+ * lensed_render, so render calls on one model must not overlap. */
+int lensed_render_error(lensed_model *m, int system, const double *params, float *out_error,
+                        void *stream);
 
 /* Log-likelihood (Eq. 17) of P parameter points for every system, batched:
  * params is a DEVICE array [n_systems][P][n_params_max] of doubles (entries

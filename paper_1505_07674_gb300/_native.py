@@ -17,13 +17,16 @@ STATUS = {0: "LENSED_OK", -1: "LENSED_E_ARG", -2: "LENSED_E_NOMEM", -3: "LENSED_
 
 SIE, SHEAR, POINTMASS, SERSIC, DEVAUC, GAUSS = 1, 2, 3, 4, 5, 6
 PLANE_LENS, PLANE_FOREGROUND, PLANE_SOURCE = 0, 1, 2
-RULE_POINT, RULE_SUB, RULE_GL = 0, 1, 2
+RULE_POINT, RULE_SUB, RULE_GL, RULE_GK = 0, 1, 2, 3
 PREC_FP32, PREC_MIXED, PREC_FP64 = 0, 1, 2
 RENDER_UNCONVOLVED, RENDER_CONVOLVED = 0, 1
 MAX_COMPONENT_PARAMS = 8
+MAX_RULE_ORDER = 16
+MAX_KRONROD_ORDER = 7
 
 # the C entry points, by name (the ABI symbol list the tests check)
 EXPORTS = ("lensed_create_model", "lensed_destroy", "lensed_model_info_get", "lensed_render",
+           "lensed_render_error", "lensed_rule_nodes",
            "lensed_loglike_batch", "lensed_loglike_plain", "lensed_loglike_batch_host",
            "lensed_autotune", "lensed_tuned_config", "lensed_last_error", "lensed_batch_plan",
            "lensed_profile_batch", "lensed_loglike_batch_noalloc",
@@ -78,6 +81,8 @@ def lib():
         L.lensed_destroy.restype = None
         L.lensed_model_info_get.argtypes = [vp, C.POINTER(ModelInfo)]
         L.lensed_render.argtypes = [vp, C.c_int, vp, C.c_int, vp, vp]
+        L.lensed_render_error.argtypes = [vp, C.c_int, vp, vp, vp]
+        L.lensed_rule_nodes.argtypes = [C.c_int, C.c_int, vp, vp, vp]
         for name in ("lensed_loglike_batch", "lensed_loglike_plain", "lensed_loglike_batch_host",
                      "lensed_loglike_batch_noalloc"):
             getattr(L, name).argtypes = [vp, vp, C.c_int, vp, vp]

@@ -1135,4 +1135,25 @@ void launch_copy_image(int precision, const void *Lbuf, long long off, int npix,
                                                       npix, valid, out);
 }
 
+__global__ void k_error_image(int fp64, const void *__restrict__ LK, const void *__restrict__ LG,
+                              long long off, int npix, const unsigned char *__restrict__ valid,
+                              float *__restrict__ out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npix) return;
+    if (!valid[0]) {
+        out[k] = __int_as_float(0x7fc00000);
+        return;
+    }
+    out[k] = fp64 ? (float)fabs(((const double *)LK)[off + k] - ((const double *)LG)[off + k])
+                  : fabsf(((const float *)LK)[off + k] - ((const float *)LG)[off + k]);
+}
+
+void launch_error_image(int precision, const void *LK, const void *LG, long long off, int npix,
+                        const unsigned char *valid, float *out, cudaStream_t st)
+{
+    k_error_image<<<(npix + 255) / 256, 256, 0, st>>>(precision == LENSED_PREC_FP64, LK, LG, off,
+                                                       npix, valid, out);
+}
+
 }  // namespace lensed

@@ -186,8 +186,106 @@ std::vector<double> build_bn_table()
     return tab;
 }
 
+// Integral of x^k P_n(x) over [-1, 1]: zero unless k >= n and k - n even,
+// then 2^(n+1) k! ((k+n)/2)! / (((k-n)/2)! (k+n+1)!) (Rodrigues' formula
+// integrated by parts n times).
+static long double legendre_moment(int n, int k)
+{
+    if (k < n || (k - n) % 2) return 0.0L;
+    return expl((n + 1) * logl(2.0L) + lgammal(k + 1.0L) + lgammal((k + n) / 2 + 1.0L) -
+                lgammal((k - n) / 2 + 1.0L) - lgammal(k + n + 2.0L));
+}
+
+// Kronrod's (2n+1)-point extension of the n-point Gauss rule on [-1, 1]
+// (Sec. 3.1 default rule; Patterson 1968).  The n+1 added nodes are the
+// roots of the Stieltjes polynomial E(x) = x^(n+1) + sum_j c_j x^j (j of the
+// parity of n+1), fixed by integral P_n E x^k = 0 for odd k, with the
+// moments in closed form; each root lies between consecutive Gauss nodes
+// (or a Gauss node and an end point) and is found by bisection there.  The
+// Kronrod weights integrate the Lagrange basis of the 2n+1 nodes with a
+// Gauss-Legendre rule exact for its degree.  Long double throughout.
+bool gauss_kronrod(int n, std::vector<double> &x, std::vector<double> &wk,
+                   std::vector<double> &wg)
+{
+    if (n < 1 || n > LENSED_MAX_KRONROD_ORDER) return false;
+    std::vector<int> js, ks;
+    for (int j = n - 1; j >= 0; j -= 2) js.push_back(j);
+    for (int k = 1; (int)ks.size() < (int)js.size(); k += 2) ks.push_back(k);
+    const int m = (int)js.size();
+    std::vector<long double> A(m * m), c(m);
+    for (int r = 0; r < m; ++r) {
+        for (int q = 0; q < m; ++q) A[r * m + q] = legendre_moment(n, js[q] + ks[r]);
+        c[r] = -legendre_moment(n, n + 1 + ks[r]);
+    }
+    // Gauss-Jordan with partial pivoting (m <= 4)
+    for (int col = 0; col < m; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < m; ++r)
+            if (fabsl(A[r * m + col]) > fabsl(A[piv * m + col])) piv = r;
+        if (A[piv * m + col] == 0.0L) return false;
+        for (int q = 0; q < m; ++q) std::swap(A[col * m + q], A[piv * m + q]);
+        std::swap(c[col], c[piv]);
+        for (int r = 0; r < m; ++r) {
+            if (r == col) continue;
+            const long double f = A[r * m + col] / A[col * m + col];
+            for (int q = 0; q < m; ++q) A[r * m + q] -= f * A[col * m + q];
+            c[r] -= f * c[col];
+        }
+    }
+    for (int r = 0; r < m; ++r) c[r] /= A[r * m + r];
+    auto E = [&](long double z) {
+        long double v = powl(z, n + 1);
+        for (int q = 0; q < m; ++q) v += c[q] * powl(z, js[q]);
+        return v;
+    };
+    std::vector<double> gx, gw;
+    gauss_legendre(n, gx, gw);
+    std::vector<long double> edges(n + 2);
+    edges[0] = -1.0L;
+    for (int i = 0; i < n; ++i) edges[i + 1] = gx[i];
+    edges[n + 1] = 1.0L;
+    x.assign(2 * n + 1, 0.0);
+    wg.assign(2 * n + 1, 0.0);
+    std::vector<long double> xl(2 * n + 1);
+    for (int i = 0; i <= n; ++i) {
+        long double lo = edges[i], hi = edges[i + 1];
+        const long double flo = E(lo);
+        if ((flo < 0) == (E(hi) < 0)) return false;
+        for (int it = 0; it < 200; ++it) {
+            const long double mid = 0.5L * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if ((E(mid) < 0) == (flo < 0)) lo = mid;
+            else hi = mid;
+        }
+        xl[2 * i] = 0.5L * (lo + hi);
+        if (i < n) {
+            xl[2 * i + 1] = gx[i];
+            wg[2 * i + 1] = gw[i];
+        }
+    }
+    xl[n] = 0.0L;  // the middle node (Gauss for odd n, added for even n) by symmetry
+    std::vector<double> qx, qw;
+    gauss_legendre(2 * n + 2, qx, qw);  // exact to degree 4n + 3 >= 2n
+    wk.assign(2 * n + 1, 0.0);
+    for (int i = 0; i < 2 * n + 1; ++i) {
+        long double acc = 0.0L;
+        for (size_t q = 0; q < qx.size(); ++q) {
+            long double l = 1.0L;
+            for (int k = 0; k < 2 * n + 1; ++k)
+                if (k != i) l *= (qx[q] - xl[k]) / (xl[i] - xl[k]);
+            acc += qw[q] * l;
+        }
+        wk[i] = (double)acc;
+        x[i] = (double)xl[i];
+    }
+    return true;
+}
+
 // 1-D rule on the unit pixel: offsets t in (-1/2, 1/2), weights summing to 1.
-bool rule_nodes(int rule, int order, std::vector<double> &t, std::vector<double> &wt)
+// For LENSED_RULE_GK, wt_gauss (if given) receives the embedded Gauss
+// weights (zero on the added nodes).
+bool rule_nodes(int rule, int order, std::vector<double> &t, std::vector<double> &wt,
+                std::vector<double> *wt_gauss = nullptr)
 {
     if (rule == LENSED_RULE_POINT) {
         t = {0.0};
@@ -199,6 +297,19 @@ bool rule_nodes(int rule, int order, std::vector<double> &t, std::vector<double>
         t.resize(order);
         wt.assign(order, 1.0 / order);
         for (int a = 0; a < order; ++a) t[a] = (a + 0.5) / order - 0.5;
+        return true;
+    }
+    if (rule == LENSED_RULE_GK) {
+        std::vector<double> x, wk, wg;
+        if (!gauss_kronrod(order, x, wk, wg)) return false;
+        t.resize(x.size());
+        wt.resize(x.size());
+        if (wt_gauss) wt_gauss->resize(x.size());
+        for (size_t a = 0; a < x.size(); ++a) {
+            t[a] = 0.5 * x[a];
+            wt[a] = 0.5 * wk[a];
+            if (wt_gauss) (*wt_gauss)[a] = 0.5 * wg[a];
+        }
         return true;
     }
     if (rule == LENSED_RULE_GL) {
@@ -292,14 +403,16 @@ struct lensed_model {
     size_t scratch_budget = (size_t)1 << 30;  // bytes of per-point image scratch
 
     std::vector<SysDev> sys_h;
+    std::vector<SysDev> sys_gauss_h;  // per system: its embedded Gauss rule (GK systems)
     std::vector<int> need_count;      // per system
     std::vector<int> n_nodes;         // per system
+    std::vector<int> n_nodes_gauss;   // per system: Gauss nodes per axis (GK), else 0
     std::vector<int> psf_p, psf_q;    // per system
     std::vector<int> tiles_all;       // per system: tiles_x * tiles_y
     std::vector<double> ray_flops, ray_transc;  // per system, per ray
 
     // device tables
-    DevBuf<SysDev> sys;
+    DevBuf<SysDev> sys, sys_gauss;
     DevBuf<int> comp_type, comp_plane, comp_free, comp_sys;
     DevBuf<double> comp_value;
     DevBuf<float> data, weight;
@@ -341,7 +454,7 @@ struct lensed_model {
     DevBuf<float> rcf;
     DevBuf<double> rcd;
     DevBuf<unsigned char> rvalid, rcvalid;
-    DevBuf<unsigned char> rL;
+    DevBuf<unsigned char> rL, rLg;  // rLg: the embedded-Gauss luminosities (GK systems)
     // host-API staging
     DevBuf<double> stage_params, stage_out;
 
@@ -530,8 +643,11 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         if (d.rule != LENSED_RULE_POINT &&
             (d.rule_order < 1 || d.rule_order > LENSED_MAX_RULE_ORDER))
             return fail(LENSED_E_ARG, "system %d: rule order %d out of range", s, d.rule_order);
-        if (d.rule < LENSED_RULE_POINT || d.rule > LENSED_RULE_GL)
+        if (d.rule < LENSED_RULE_POINT || d.rule > LENSED_RULE_GK)
             return fail(LENSED_E_ARG, "system %d: unknown rule %d", s, d.rule);
+        if (d.rule == LENSED_RULE_GK && d.rule_order > LENSED_MAX_KRONROD_ORDER)
+            return fail(LENSED_E_ARG, "system %d: Gauss-Kronrod order %d out of range (1..%d)", s,
+                        d.rule_order, LENSED_MAX_KRONROD_ORDER);
         if (d.n_components < 1 || d.n_components > LENSED_MAX_COMPONENTS || !d.components)
             return fail(LENSED_E_ARG, "system %d: %d components (1..%d)", s, d.n_components,
                         LENSED_MAX_COMPONENTS);
@@ -561,7 +677,8 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
     }
 
     // ---- host tables
-    std::vector<SysDev> sh(n_systems);
+    std::vector<SysDev> sh(n_systems), shg(n_systems);
+    std::vector<int> nng_v(n_systems);
     std::vector<int> ctype, cplane, cfree, csys;
     std::vector<double> cval;
     std::vector<float> data, weight, psf_f, node_u, node_w;
@@ -654,33 +771,36 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         // quadrature (Eq. 14): 1-D offsets t*h, 2-D weights W_a W_b; the float
         // weights are adjusted at the largest one so they sum to one in exact
         // arithmetic, leaving no coherent scale error
-        std::vector<double> t, wt;
-        rule_nodes(d.rule, d.rule_order, t, wt);
-        const int nn = (int)t.size();
-        S.nn = nn;
-        S.node_off = (int)node_u.size();
-        S.w2_off = (int)node_w.size();
-        nn_v[s] = nn;
-        for (int a = 0; a < nn; ++a) {
-            node_ud.push_back(t[a] * d.pixel_scale);
-            node_u.push_back((float)(t[a] * d.pixel_scale));
-        }
-        {
+        std::vector<double> t, wt, wtg;
+        rule_nodes(d.rule, d.rule_order, t, wt, &wtg);
+        auto append_rule = [&](const std::vector<double> &tt, const std::vector<double> &ww,
+                               SysDev &D) {
+            const int nn = (int)tt.size();
+            D.nn = nn;
+            D.node_off = (int)node_u.size();
+            D.w2_off = (int)node_w.size();
+            for (int a = 0; a < nn; ++a) {
+                node_ud.push_back(tt[a] * d.pixel_scale);
+                node_u.push_back((float)(tt[a] * d.pixel_scale));
+            }
             std::vector<float> w2f(nn * nn);
             int kmax = 0;
             for (int b = 0; b < nn; ++b)
                 for (int a = 0; a < nn; ++a) {
-                    const double v = wt[a] * wt[b];
+                    const double v = ww[a] * ww[b];
                     node_wd.push_back(v);
                     w2f[b * nn + a] = (float)v;
-                    if (v > wt[kmax % nn] * wt[kmax / nn]) kmax = b * nn + a;
+                    if (v > ww[kmax % nn] * ww[kmax / nn]) kmax = b * nn + a;
                 }
             double rest = 0.0;
             for (int k = 0; k < nn * nn; ++k)
                 if (k != kmax) rest += (double)w2f[k];
             w2f[kmax] = (float)(1.0 - rest);
             node_w.insert(node_w.end(), w2f.begin(), w2f.end());
-        }
+        };
+        append_rule(t, wt, S);
+        const int nn = S.nn;
+        nn_v[s] = nn;
         // needed pixels: every pixel an unmasked output reads through the
         // (clamped) PSF footprint
         std::vector<unsigned char> nd(npix, 0);
@@ -748,9 +868,26 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         }
         S.pix_off = pix_off;
         pix_off += npix;
+        // the embedded Gauss rule of a Gauss-Kronrod system as a system of
+        // its own (same image, components and tables, Gauss nodes only) for
+        // the per-pixel error estimate
+        shg[s] = S;
+        nng_v[s] = 0;
+        if (d.rule == LENSED_RULE_GK) {
+            std::vector<double> tg, wg;
+            for (size_t a = 0; a < t.size(); ++a)
+                if (wtg[a] != 0.0) {
+                    tg.push_back(t[a]);
+                    wg.push_back(wtg[a]);
+                }
+            append_rule(tg, wg, shg[s]);
+            nng_v[s] = shg[s].nn;
+        }
     }
 
     lensed_model *m = new lensed_model();
+    m->sys_gauss_h = shg;
+    m->n_nodes_gauss = nng_v;
     m->precision = precision;
     m->n_sys = n_systems;
     m->n_par_max = n_par_max;
@@ -795,7 +932,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
 
     int rc;
     init_kernel_attributes();
-    if ((rc = m->sys.upload(sh)) || (rc = m->comp_type.upload(ctype)) ||
+    if ((rc = m->sys.upload(sh)) || (rc = m->sys_gauss.upload(shg)) || (rc = m->comp_type.upload(ctype)) ||
         (rc = m->comp_plane.upload(cplane)) || (rc = m->comp_free.upload(cfree)) || (rc = m->comp_sys.upload(csys)) ||
         (rc = m->comp_value.upload(cval)) || (rc = m->data.upload(data)) ||
         (rc = m->weight.upload(weight)) ||
@@ -821,7 +958,10 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
     }
     size_t max_npix = 0;
     for (auto &S : sh) max_npix = std::max(max_npix, (size_t)S.npix);
-    if ((rc = m->rL.alloc(total_pix * m->elem()))) {
+    bool any_gk = false;
+    for (int s = 0; s < n_systems; ++s) any_gk |= systems[s].rule == LENSED_RULE_GK;
+    if ((rc = m->rL.alloc(total_pix * m->elem())) ||
+        (any_gk && (rc = m->rLg.alloc(total_pix * m->elem())))) {
         std::string msg = g_last_error;
         delete m;
         g_last_error = msg;
@@ -898,6 +1038,56 @@ extern "C" int lensed_render(lensed_model *m, int system, const double *params, 
                    m->render_psf.p + m->render_psf_off[system], m->render_psf_cnt[system], 0, 1,
                    m->rL.p, m->total_pix, nullptr, 0, out_image, st);
     }
+    CUDA_OK(cudaGetLastError());
+    return LENSED_OK;
+}
+
+extern "C" int lensed_rule_nodes(int rule, int order, double *t, double *w, double *w_gauss)
+{
+    if (!t || !w) return fail(LENSED_E_ARG, "t/w is NULL");
+    if (rule < LENSED_RULE_POINT || rule > LENSED_RULE_GK)
+        return fail(LENSED_E_ARG, "unknown rule %d", rule);
+    std::vector<double> tt, ww, wg;
+    if (!rule_nodes(rule, order, tt, ww, &wg))
+        return fail(LENSED_E_ARG, "rule %d: order %d out of range", rule, order);
+    for (size_t a = 0; a < tt.size(); ++a) {
+        t[a] = tt[a];
+        w[a] = ww[a];
+        if (w_gauss) w_gauss[a] = rule == LENSED_RULE_GK ? wg[a] : 0.0;
+    }
+    return (int)tt.size();
+}
+
+extern "C" int lensed_render_error(lensed_model *m, int system, const double *params,
+                                   float *out_error, void *stream)
+{
+    if (check_model(m)) return LENSED_E_ARG;
+    if (system < 0 || system >= m->n_sys) return fail(LENSED_E_ARG, "system %d out of range", system);
+    if (!params || !out_error) return fail(LENSED_E_ARG, "params/out_error is NULL");
+    if (m->n_nodes_gauss[system] == 0)
+        return fail(LENSED_E_ARG, "system %d: rule is not Gauss-Kronrod (no error estimate)", system);
+    cudaStream_t st = (cudaStream_t)stream;
+    const SysDev &S = m->sys_h[system];
+    launch_prologue(m->sys.p, m->comp_sys.p, system, 1, S.comp_off, S.ncomp, m->comp_type.p,
+                    m->comp_free.p, m->comp_value.p, params, true, 1, 0, 1, m->n_par_max,
+                    m->C_total, m->bn_table.p, m->rcf.p, m->rcd.p, m->rcvalid.p, m->rvalid.p, st);
+    // the Kronrod and the embedded Gauss luminosities, each with the trace
+    // (and MIXED fix-up) kernels of lensed_render
+    for (int g = 0; g < 2; ++g) {
+        const SysDev *sys = g ? m->sys_gauss.p : m->sys.p;
+        void *L = g ? (void *)m->rLg.p : (void *)m->rL.p;
+        const int nn = g ? m->n_nodes_gauss[system] : m->n_nodes[system];
+        launch_trace(m->precision, m->cfg(), nn, sys, m->comp_type.p, m->comp_plane.p, m->rcf.p,
+                     m->rcd.p, m->rvalid.p, 1, m->C_total,
+                     m->render_trace.p + m->render_trace_off[system], m->render_trace_cnt[system],
+                     nullptr, m->nodes(), 0, 1, L, m->total_pix, st);
+        if (m->precision == LENSED_PREC_MIXED)
+            launch_fix64(m->cfg(), sys, system, 1, m->comp_type.p, m->comp_plane.p, m->rcf.p,
+                         m->rcd.p, m->rvalid.p, 1, m->C_total, nullptr, m->nodes(), 0, 1, L,
+                         m->total_pix, st);
+    }
+    launch_error_image(m->precision, m->rL.p, m->rLg.p, S.pix_off, S.npix, m->rvalid.p + system,
+                       out_error, st);
     CUDA_OK(cudaGetLastError());
     return LENSED_OK;
 }

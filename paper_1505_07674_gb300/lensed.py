@@ -18,7 +18,7 @@ from . import _native as N
 _TYPES = {"sie": N.SIE, "shear": N.SHEAR, "pointmass": N.POINTMASS, "sersic": N.SERSIC,
           "devauc": N.DEVAUC, "gauss": N.GAUSS}
 _PLANES = {"lens": N.PLANE_LENS, "foreground": N.PLANE_FOREGROUND, "source": N.PLANE_SOURCE}
-_RULES = {"point": N.RULE_POINT, "sub": N.RULE_SUB, "gl": N.RULE_GL}
+_RULES = {"point": N.RULE_POINT, "sub": N.RULE_SUB, "gl": N.RULE_GL, "gk": N.RULE_GK}
 _PREC = {"fp32": N.PREC_FP32, "mixed": N.PREC_MIXED, "fp64": N.PREC_FP64}
 
 
@@ -135,6 +135,18 @@ class Model:
         self._last = p
         return out
 
+    def render_error(self, system, params, out=None, stream=None):
+        """Per-pixel Gauss-Kronrod error estimate |L_K - L_G| (unconvolved) of
+        a system whose rule is ("gk", N)."""
+        spec = self.specs[system]
+        p = torch.as_tensor(params, dtype=torch.float64).to("cuda").contiguous()
+        if out is None:
+            out = torch.empty((spec["ny"], spec["nx"]), dtype=torch.float32, device="cuda")
+        N.check(N.lib().lensed_render_error(self._h, system, C.c_void_p(p.data_ptr()),
+                                            C.c_void_p(out.data_ptr()), _stream_handle(stream)))
+        self._last = p
+        return out
+
     def _loglike(self, fn, params, out, stream):
         if not (isinstance(params, torch.Tensor) and params.is_cuda and params.dtype == torch.float64
                 and params.dim() == 3 and params.shape[2] == self.n_params_max
@@ -213,3 +225,16 @@ class Model:
         buf = C.create_string_buffer(128)
         idx = N.lib().lensed_tuned_config(self._h, buf, 128)
         return idx, buf.value.decode()
+
+
+def rule_nodes(rule, order):
+    """The library's 1-D rule on the unit pixel for ("point"|"sub"|"gl"|"gk",
+    order): offsets t, weights w and, for "gk", the embedded Gauss weights
+    (zero on the Kronrod-only nodes; all zero for other rules).  Host only."""
+    t = np.zeros(N.MAX_RULE_ORDER)
+    w = np.zeros(N.MAX_RULE_ORDER)
+    wg = np.zeros(N.MAX_RULE_ORDER)
+    n = N.lib().lensed_rule_nodes(_RULES[rule], int(order), t.ctypes.data, w.ctypes.data,
+                                  wg.ctypes.data)
+    N.check(min(n, 0))
+    return t[:n].copy(), w[:n].copy(), wg[:n].copy()
