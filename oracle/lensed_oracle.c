@@ -45,6 +45,12 @@
  *     incomplete gamma); total flux F = 10^(-0.4 (mag - zp)) gives
  *     I_0 = F b_n^(2n) / (2 pi n r^2 Gamma(2n)); de Vaucouleurs is n = 4;
  *     the Gaussian profile is I_0 exp(-R^2 / (2 sigma^2)), I_0 = F/(2 pi sigma^2);
+ *   - the flat sky (Sec. 5) is a constant surface brightness, in the image's
+ *     flux units per arcsec^2 and of either sign (it absorbs residuals of
+ *     the sky subtraction), on the foreground or source plane;
+ *   - an image-plane prior (Sec. 5) gives a source's position parameters as
+ *     an image-plane position theta; the source is centred on
+ *     theta - alpha(theta) of the same parameter point's lens;
  *   - a parameter point with q outside (0, 1], a non-positive radius or
  *     Sersic index, a negative Einstein radius or core has loglike = -inf.
  */
@@ -56,10 +62,13 @@
 
 /* component types */
 enum { ORA_SIE = 1, ORA_SHEAR = 2, ORA_POINTMASS = 3,
-       ORA_SERSIC = 4, ORA_DEVAUC = 5, ORA_GAUSS = 6 };
+       ORA_SERSIC = 4, ORA_DEVAUC = 5, ORA_GAUSS = 6, ORA_SKY = 7 };
 /* planes: mass on the lens plane, light on the lens plane (unlensed,
- * evaluated at x) or on the source plane (lensed, evaluated at y) */
-enum { ORA_PLANE_LENS = 0, ORA_PLANE_FOREGROUND = 1, ORA_PLANE_SOURCE = 2 };
+ * evaluated at x) or on the source plane (lensed, evaluated at y); a source
+ * on ORA_PLANE_SOURCE_IMAGE gives its position as an image-plane position
+ * (the image-plane prior of Sec. 5) */
+enum { ORA_PLANE_LENS = 0, ORA_PLANE_FOREGROUND = 1, ORA_PLANE_SOURCE = 2,
+       ORA_PLANE_SOURCE_IMAGE = 3 };
 /* integration rules of Sec. 4.5 (point, subN, Gauss-Kronrod gNk(2N+1)) plus
  * Gauss-Legendre N x N */
 enum { ORA_RULE_POINT = 0, ORA_RULE_SUB = 1, ORA_RULE_GL = 2, ORA_RULE_GK = 3 };
@@ -99,6 +108,7 @@ int ora_nparams_of(int type)
     case ORA_SERSIC: return 7;    /* x, y, r, mag, n, q, pa */
     case ORA_DEVAUC: return 6;    /* x, y, r, mag, q, pa */
     case ORA_GAUSS: return 6;     /* x, y, sigma, mag, q, pa */
+    case ORA_SKY: return 1;       /* surface brightness per arcsec^2 */
     }
     return -1;
 }
@@ -337,6 +347,9 @@ typedef struct {
 
 static double deg2rad(double d) { return d * (ORA_PI / 180.0); }
 
+void ora_deflection_one(int type, const double *p, double x, double y,
+                        double *ax, double *ay);
+
 /* Resolve parameters and derived constants; returns 0 if the point is
  * outside the valid domain of the component. */
 static int resolve(const ora_system *sys, const double *xi, ora_comp_eval *ce)
@@ -389,9 +402,28 @@ static int resolve(const ora_system *sys, const double *xi, ora_comp_eval *ce)
             e->cos_pa = cos(deg2rad(e->p[5]));
             e->sin_pa = sin(deg2rad(e->p[5]));
             break;
+        case ORA_SKY:
+            break;
         default:
             return 0;
         }
+    }
+    /* image-plane priors (Sec. 5): a source whose position parameters are an
+     * image-plane position theta sits at the source-plane position
+     * theta - alpha(theta) of the same lens (Eq. 1) */
+    for (int c = 0; c < sys->ncomp; ++c) {
+        if (ce[c].plane != ORA_PLANE_SOURCE_IMAGE) continue;
+        double tx = ce[c].p[0], ty = ce[c].p[1], ax = 0.0, ay = 0.0;
+        for (int l = 0; l < sys->ncomp; ++l) {
+            if (ce[l].plane != ORA_PLANE_LENS) continue;
+            double dax, day;
+            ora_deflection_one(ce[l].type, ce[l].p, tx, ty, &dax, &day);
+            ax += dax;
+            ay += day;
+        }
+        ce[c].p[0] = tx - ax;
+        ce[c].p[1] = ty - ay;
+        ce[c].plane = ORA_PLANE_SOURCE;
     }
     return 1;
 }
@@ -445,6 +477,7 @@ void ora_deflection_one(int type, const double *p, double x, double y,
 /* Surface brightness of one light component at (x, y) (Eqs. 22-23). */
 static double brightness_one(const ora_comp_eval *e, double x, double y)
 {
+    if (e->type == ORA_SKY) return e->p[0]; /* flat sky (Sec. 5) */
     double dx = x - e->p[0], dy = y - e->p[1];
     double u = dx * e->cos_pa + dy * e->sin_pa;
     double v = -dx * e->sin_pa + dy * e->cos_pa;

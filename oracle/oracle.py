@@ -20,8 +20,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lensed_oracle.c")
 _OUT = os.path.join(_HERE, "_build", "liblensed_oracle.so")
 
-TYPES = {"sie": 1, "shear": 2, "pointmass": 3, "sersic": 4, "devauc": 5, "gauss": 6}
-PLANES = {"lens": 0, "foreground": 1, "source": 2}
+TYPES = {"sie": 1, "shear": 2, "pointmass": 3, "sersic": 4, "devauc": 5, "gauss": 6, "sky": 7}
+PLANES = {"lens": 0, "foreground": 1, "source": 2, "source_image": 3}
 RULES = {"point": 0, "sub": 1, "gl": 2, "gk": 3}
 MAXPAR = 8
 

@@ -434,6 +434,76 @@ def test_surface_brightness_conservation():
     assert np.abs(L / (1e-3 * 0.01) - 1).max() < 1e-8
 
 
+@pytest.mark.parametrize("plane", ["foreground", "source"])
+@pytest.mark.parametrize("rule", [("point", 1), ("sub", 4), ("gk", 3)])
+def test_flat_sky(plane, rule):
+    # Sec. 5's flat sky: a constant surface brightness S gives S h^2 in every
+    # pixel whatever the rule (weights sum to one), the lens (surface
+    # brightness is conserved) and the unit-sum PSF; it adds linearly to the
+    # other components, and it may be negative.
+    lens = [component("sie", "lens", [fixed(0.1), fixed(0), fixed(1.2), fixed(0.6), fixed(30),
+                                      fixed(0.0)]),
+            component("pointmass", "lens", [fixed(-0.3), fixed(0.4), fixed(0.2)])]
+    src = component("sersic", "source", [fixed(0.05), fixed(0.02), fixed(0.2), fixed(0), fixed(1.5),
+                                         fixed(0.7), fixed(20)])
+    psf = W.gaussian_psf(5, 0.15, 0.1)
+    for S in (0.37, -0.05):
+        sky = component("sky", plane, [fixed(S)])
+        L = O.OracleSystem(make_spec(lens + [sky], nx=20, ny=16, h=0.1, rule=rule, psf=psf)).render(
+            np.zeros(0), convolved=True)
+        assert np.abs(L - S * 0.01).max() <= 1e-14 * abs(S)
+        a = O.OracleSystem(make_spec(lens + [src], nx=20, ny=16, h=0.1, rule=rule)).render(
+            np.zeros(0), convolved=False)
+        b = O.OracleSystem(make_spec(lens + [src, sky], nx=20, ny=16, h=0.1, rule=rule)).render(
+            np.zeros(0), convolved=False)
+        assert np.allclose(b - a, S * 0.01, rtol=0, atol=1e-14)
+
+
+def test_image_plane_prior_places_source_behind_theta():
+    # Sec. 5's image-plane prior: the source position parameters are an
+    # image-plane position theta, and the source sits at y(theta).  With the
+    # point rule a pixel whose centre is theta therefore sees the source's
+    # central surface brightness I_0 exactly, for any lens.
+    h = 0.05
+    theta = (3 * h, -7 * h)   # a pixel centre of the 24 x 24 grid (offset by h/2)
+    tx, ty = theta[0] + h / 2, theta[1] + h / 2
+    lens = [component("sie", "lens", [fixed(0.03), fixed(-0.02), fixed(0.6), fixed(0.7), fixed(40),
+                                      fixed(0.0)]),
+            component("shear", "lens", [fixed(0), fixed(0), fixed(0.07), fixed(15.0)]),
+            component("pointmass", "lens", [fixed(-0.25), fixed(0.1), fixed(0.1)])]
+    mag, r, n = 1.0, 0.08, 1.3
+    src = component("sersic", "source_image", [fixed(tx), fixed(ty), fixed(r), fixed(mag),
+                                               fixed(n), fixed(0.6), fixed(30)])
+    L = O.OracleSystem(make_spec(lens + [src], nx=24, ny=24, h=h, rule=("point", 1))).render(
+        np.zeros(0), convolved=False)
+    i = int(round(ty / h + 11.5))
+    j = int(round(tx / h + 11.5))
+    I0 = O.sersic_I0(n, r, 10 ** (-0.4 * mag))
+    assert abs(L[i, j] / (h * h) - I0) < 1e-12 * I0
+    assert L[i, j] == L.max()
+
+
+def test_image_plane_prior_sis_closed_form():
+    # For a singular isothermal sphere of Einstein radius b at the origin the
+    # lens equation gives y = theta (1 - b/|theta|): an image-plane prior at
+    # theta = (1.5, 0) is a source at (0.5, 0); and with no lens at all the
+    # image-plane position is the source position.
+    sis = component("sie", "lens", [fixed(0), fixed(0), fixed(1.0), fixed(1.0), fixed(0), fixed(0)])
+
+    def img(plane, x, y, lens):
+        src = component("sersic", plane, [fixed(x), fixed(y), fixed(0.1), fixed(0), fixed(1.0),
+                                          fixed(0.8), fixed(10)])
+        return O.OracleSystem(make_spec(lens + [src], nx=40, ny=40, h=0.1, rule=("gl", 3))).render(
+            np.zeros(0), convolved=False)
+
+    a = img("source_image", 1.5, 0.0, [sis])
+    b = img("source", 0.5, 0.0, [sis])
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-15 * b.max())
+    a = img("source_image", 0.3, -0.2, [])
+    b = img("source", 0.3, -0.2, [])
+    assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("lens", ["sis", "pointmass"])
 def test_rendered_einstein_ring(lens):
     # A small source behind the lens centre is imaged into a ring of radius

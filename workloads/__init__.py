@@ -22,8 +22,10 @@ Component parameter order (the same on both sides):
     sersic     x, y, r_e, mag, n, q, pa_deg
     devauc     x, y, r_e, mag, q, pa_deg
     gauss      x, y, sigma, mag, q, pa_deg
+    sky        surface brightness per arcsec^2 (flat sky)
 Planes: "lens" (mass), "foreground" (light at the image position), "source"
-(light at the traced position).
+(light at the traced position), "source_image" (a source whose x, y are an
+image-plane position: the image-plane prior).
 """
 from __future__ import annotations
 
@@ -31,7 +33,7 @@ import math
 
 import numpy as np
 
-NPAR = {"sie": 6, "shear": 4, "pointmass": 3, "sersic": 7, "devauc": 6, "gauss": 6}
+NPAR = {"sie": 6, "shear": 4, "pointmass": 3, "sersic": 7, "devauc": 6, "gauss": 6, "sky": 1}
 MASS_TYPES = ("sie", "shear", "pointmass")
 
 
@@ -47,8 +49,10 @@ def component(ctype, plane, params):
     assert len(params) == NPAR[ctype], (ctype, len(params))
     if ctype in MASS_TYPES:
         assert plane == "lens"
-    else:
+    elif ctype == "sky":
         assert plane in ("foreground", "source")
+    else:
+        assert plane in ("foreground", "source", "source_image")
     return {"type": ctype, "plane": plane, "params": list(params)}
 
 
