@@ -44,6 +44,14 @@ WORKLOADS = {
     "c3": ("uneven_256systems_48-320px_gl3-7_psf7-31_512pts_each", 512),
     "c4": ("euclid_400x400_h0.1_18par_nested_sampling_2000live", 0),
     "c5": ("euclid_400x400_h0.1_18par_surrogate_prescreen_65536", 0),
+    "j0808": ("j0808like_160x160_h0.05_2sie_sky_5sersic_imageprior_psf15_g3k7_1024pts_35par", 1024),
+}
+# image, rule and PSF of the throughput workloads (for the JSON config)
+SHAPES = {
+    "c2": ("200x200", "gauss-legendre 5x5", "21x21"),
+    "c1": ("64x64", "gauss-legendre 5x5", "7x7"),
+    "c3": ("48-320 px", "gauss-legendre 3x3..7x7", "7x7..31x31"),
+    "j0808": ("160x160", "gauss-kronrod g3k7 (7x7)", "15x15"),
 }
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_SM_MHZ = 2070.0
@@ -64,7 +72,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-point pass")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
                     help="c2 (default, the benchmark), c1 or c3 (other configurations), "
-                         "c4 (posterior run), c5 (surrogate pre-screen vs plain)")
+                         "c4 (posterior run), c5 (surrogate pre-screen vs plain), j0808 "
+                         "(35-parameter multi-component model with sky and image-plane prior)")
     ap.add_argument("--live", type=int, default=2000, help="live points (c4, c5)")
     ap.add_argument("--oracle-points", type=int, default=384,
                     help="posterior points the CPU oracle re-evaluates (c4)")
@@ -384,6 +393,8 @@ def main():
     wname, default_pts = WORKLOADS[args.workload]
     if args.workload == "c3":
         specs = W.c3_batch(256)
+    elif args.workload == "j0808":
+        specs = [W.j0808_like(image_prior=True)]
     else:
         specs = [W.c2_hst() if args.workload == "c2" else W.c1_small()]
     # observation: the library's own noiseless render at the truth + seeded noise
@@ -509,9 +520,9 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wname if npts == default_pts else f"{wname} (profiling case: {npts} points)",
                    "points_per_step": evals_step, "systems": n_sys,
-                   "image": "200x200" if args.workload == "c2" else ("64x64" if args.workload == "c1" else "48-320 px"),
-                   "rule": "gauss-legendre 5x5" if args.workload != "c3" else "gauss-legendre 3x3..7x7",
-                   "psf": {"c2": "21x21", "c1": "7x7", "c3": "7x7..31x31"}[args.workload],
+                   "image": SHAPES[args.workload][0],
+                   "rule": SHAPES[args.workload][1],
+                   "psf": SHAPES[args.workload][2],
                    "precision_mode": args.precision,
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"independent points per rank x{world}",

@@ -34,7 +34,13 @@
  *       LENSED_SERSIC     x, y, r_e, mag, n, q, pa
  *       LENSED_DEVAUC     x, y, r_e, mag, q, pa  (Sersic with n = 4)
  *       LENSED_GAUSS      x, y, sigma, mag, q, pa
+ *       LENSED_SKY        S                      (flat sky, Sec. 5: constant
+ *                          surface brightness S per arcsec^2 in the data's
+ *                          flux units, either sign)
  *     Total flux of a light profile is 10^(-0.4 (mag - zeropoint)).
+ *     A source on LENSED_PLANE_SOURCE_IMAGE (image-plane prior, Sec. 5)
+ *     takes x, y as an image-plane position theta and is centred on
+ *     theta - alpha(theta), the same point's lens deflection (Eq. 1).
  *
  * Memory and streams: every input array of lensed_create_model is copied
  * into library-owned device memory, so the caller may free it on return.
@@ -76,13 +82,16 @@ enum {
     LENSED_POINTMASS = 3,
     LENSED_SERSIC = 4,
     LENSED_DEVAUC = 5,
-    LENSED_GAUSS = 6
+    LENSED_GAUSS = 6,
+    LENSED_SKY = 7
 };
 
 enum {
     LENSED_PLANE_LENS = 0,        /* mass: contributes to alpha */
     LENSED_PLANE_FOREGROUND = 1,  /* light evaluated at the image position x */
-    LENSED_PLANE_SOURCE = 2       /* light evaluated at the traced position y */
+    LENSED_PLANE_SOURCE = 2,      /* light evaluated at the traced position y */
+    LENSED_PLANE_SOURCE_IMAGE = 3 /* as SOURCE, position given on the image
+                                     plane (image-plane prior); not for SKY */
 };
 
 /* Integration rules (Sec. 3.1, Eq. 14; rule list of Sec. 4.5), each the
@@ -119,7 +128,7 @@ enum { LENSED_RENDER_UNCONVOLVED = 0, LENSED_RENDER_CONVOLVED = 1 };
  * may share an index, which ties parameters) and fixed to value[k]
  * otherwise. */
 typedef struct {
-    int type;   /* LENSED_SIE ... LENSED_GAUSS */
+    int type;   /* LENSED_SIE ... LENSED_SKY */
     int plane;  /* LENSED_PLANE_* (mass types must be LENSED_PLANE_LENS) */
     int free_index[LENSED_MAX_COMPONENT_PARAMS];
     double value[LENSED_MAX_COMPONENT_PARAMS];
@@ -302,6 +311,7 @@ int lensed_profile_batch(lensed_model *m, const double *params, int P, double *o
  * [B] FP32 DEVICE arrays.  Errors: status codes, message from
  * lensed_mlp_last_error(). */
 typedef struct lensed_mlp lensed_mlp;
+
 
 /* n_in 1..64, hidden a multiple of 64, max_batch >= 1 (largest B of a
  * gradient or training call; forward calls of any B run in slices of it).

@@ -15,8 +15,8 @@ LENSED_OK = 0
 STATUS = {0: "LENSED_OK", -1: "LENSED_E_ARG", -2: "LENSED_E_NOMEM", -3: "LENSED_E_CUDA",
           -4: "LENSED_E_NONFINITE", -5: "LENSED_E_TIMEOUT", -6: "LENSED_E_UNSUPPORTED"}
 
-SIE, SHEAR, POINTMASS, SERSIC, DEVAUC, GAUSS = 1, 2, 3, 4, 5, 6
-PLANE_LENS, PLANE_FOREGROUND, PLANE_SOURCE = 0, 1, 2
+SIE, SHEAR, POINTMASS, SERSIC, DEVAUC, GAUSS, SKY = 1, 2, 3, 4, 5, 6, 7
+PLANE_LENS, PLANE_FOREGROUND, PLANE_SOURCE, PLANE_SOURCE_IMAGE = 0, 1, 2, 3
 RULE_POINT, RULE_SUB, RULE_GL, RULE_GK = 0, 1, 2, 3
 PREC_FP32, PREC_MIXED, PREC_FP64 = 0, 1, 2
 RENDER_UNCONVOLVED, RENDER_CONVOLVED = 0, 1

@@ -26,6 +26,7 @@ constexpr int kPsfThreads = (kTileW / kOutPerThread) * kTileH;  // 256
 // Light-profile kinds inside the packed constants.
 constexpr int kKindPower = 0;  // Sersic / de Vaucouleurs: 2^-(2^(p2 lg2 R^2 + lc))
 constexpr int kKindGauss = 1;  // Gaussian: 2^-(k R^2)
+constexpr int kKindFlat = 2;   // flat sky: the constant A
 
 // SIE evaluation in MIXED precision switches to FP64 for every pixel when
 // e = sqrt(1 - q^2) < kMixedRoundE, and for the pixels whose square comes
@@ -60,6 +61,7 @@ struct SysDev {
     int tile_off, n_tiles;  // into the active-tile list
     int tiles_x, tiles_y;   // full tiling of the image
     double zeropoint;
+    int imgpos_mask;        // bit c: component c is a source placed by an image-plane prior
 };
 
 // Trace-kernel block table entry: system and the range [start, end) of its

@@ -147,7 +147,8 @@ __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__res
 #pragma unroll
     for (int k = 0; k < kNC; ++k) lo[k] = -1;
     const int np = type == LENSED_SIE ? 6 : type == LENSED_SHEAR ? 4
-                 : type == LENSED_POINTMASS ? 3 : type == LENSED_SERSIC ? 7 : 6;
+                 : type == LENSED_POINTMASS ? 3 : type == LENSED_SERSIC ? 7
+                 : type == LENSED_SKY ? 1 : 6;
     bool ok = true;
     for (int k = 0; k < np; ++k) ok = ok && isfinite(v[k]);
     o[0] = v[0];
@@ -192,6 +193,13 @@ __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__res
         // 0 x0, 1 y0, 2 theta_E^2
         ok = ok && v[2] >= 0.0;
         o[2] = v[2] * v[2];
+    } else if (type == LENSED_SKY) {
+        // flat sky (Sec. 5): 13 A = S h^2, 14 A_lo, 15 kind; no position
+        o[0] = 0.0;
+        o[1] = 0.0;
+        o[13] = v[0] * hd * hd;
+        o[15] = kKindFlat;
+        lo[13] = 14;
     } else {
         // light: Sersic (x y r mag n q pa), de Vaucouleurs (x y r mag q pa),
         // Gaussian (x y sigma mag q pa).
@@ -252,37 +260,6 @@ __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__res
     cvalid[(size_t)p * C_total + gc] = ok ? 1 : 0;
 }
 
-// Validity of a (system, point): every component in its domain.
-__global__ void k_prologue_valid(const SysDev *__restrict__ sys, int s0, int nS, int P, int p0,
-                                 int nP, int C_total, const unsigned char *__restrict__ cvalid,
-                                 unsigned char *__restrict__ valid)
-{
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= (long long)nS * nP) return;
-    const int s = s0 + (int)(tid / nP);
-    const int p = p0 + (int)(tid % nP);
-    const SysDev &S = sys[s];
-    unsigned char ok = 1;
-    for (int c = 0; c < S.ncomp; ++c) ok &= cvalid[(size_t)p * C_total + S.comp_off + c];
-    valid[(size_t)s * P + p] = ok;
-}
-
-void launch_prologue(const SysDev *sys, const int *comp_sys, int s0, int nS, int c0, int nC,
-                     const int *comp_type, const int *comp_free, const double *comp_value,
-                     const double *params, bool single_row, int P, int p0, int nP,
-                     int n_par_stride, int C_total, const double *bn_table, float *cf,
-                     double *cd, unsigned char *cvalid, unsigned char *valid, cudaStream_t st)
-{
-    const long long n = (long long)nC * nP;
-    const int threads = 64;
-    k_prologue_comp<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
-        sys, comp_sys, c0, nC, comp_type, comp_free, comp_value, params, single_row ? 1 : 0, P,
-        p0, nP, n_par_stride, C_total, bn_table, cf, cd, cvalid);
-    const long long n2 = (long long)nS * nP;
-    k_prologue_valid<<<(unsigned)((n2 + 127) / 128), 128, 0, st>>>(sys, s0, nS, P, p0, nP,
-                                                                    C_total, cvalid, valid);
-}
-
 // ---------------------------------------------------------------------------
 // a3: deflection; a4: brightness
 
@@ -317,6 +294,7 @@ __device__ __forceinline__ void sie_deflect_f64(double x, double y, const double
 // Light profile in FP64.
 __device__ __forceinline__ double light_f64(double x, double y, const double *c)
 {
+    if (c[15] == (double)kKindFlat) return c[13];
     const double dx = x - c[0], dy = y - c[1];
     const double u = dx * c[2] + dy * c[3];
     const double v = dy * c[2] - dx * c[3];
@@ -408,6 +386,12 @@ __device__ __forceinline__ float light_f32(const LightF &k, float x, float y)
     return fmaf(k.A, g, k.Al * g);
 }
 
+// Any light profile, including the flat sky (kind kKindFlat: I = A).
+__device__ __forceinline__ float light_any_f32(const LightF &k, float x, float y)
+{
+    return k.kind == (float)kKindFlat ? k.A : light_f32(k, x, y);
+}
+
 // FP64 SIE of one ray in a MIXED evaluation.  Out of line, so that none of
 // its double-precision arithmetic is scheduled on the FP32 path; the ray
 // position is rebuilt in FP64 from the pixel index and the FP64 node offsets.
@@ -418,6 +402,25 @@ __device__ __noinline__ void sie_ray_f64(float jc, float ic, double hd, double u
     sie_deflect_f64((double)jc * hd + ua, (double)ic * hd + vb, c, dax, day);
     ax += (float)dax;
     ay += (float)day;
+}
+
+// Deflection of one mass component in FP64, added to (ax, ay).
+__device__ __forceinline__ void deflect_f64(int t, double x, double y, const double *cc,
+                                            double &ax, double &ay)
+{
+    if (t == LENSED_SIE) {
+        sie_deflect_f64(x, y, cc, ax, ay);
+    } else if (t == LENSED_SHEAR) {
+        const double dx = x - cc[0], dy = y - cc[1];
+        ax += cc[2] * dx + cc[3] * dy;
+        ay += cc[3] * dx - cc[2] * dy;
+    } else {
+        const double dx = x - cc[0], dy = y - cc[1];
+        const double r2 = dx * dx + dy * dy;
+        const double f = r2 > 0.0 ? cc[2] / r2 : 0.0;
+        ax += f * dx;
+        ay += f * dy;
+    }
 }
 
 // Total image-plane brightness at one ray in FP64 (Eqs. 1-2).
@@ -437,20 +440,7 @@ __device__ __forceinline__ double brightness_f64(double x, double y, const RayCt
         if (pl == LENSED_PLANE_FOREGROUND) {
             I += light_f64(x, y, cc);
         } else if (pl == LENSED_PLANE_LENS) {
-            const int t = R.type[c];
-            if (t == LENSED_SIE) {
-                sie_deflect_f64(x, y, cc, ax, ay);
-            } else if (t == LENSED_SHEAR) {
-                const double dx = x - cc[0], dy = y - cc[1];
-                ax += cc[2] * dx + cc[3] * dy;
-                ay += cc[3] * dx - cc[2] * dy;
-            } else {
-                const double dx = x - cc[0], dy = y - cc[1];
-                const double r2 = dx * dx + dy * dy;
-                const double f = r2 > 0.0 ? cc[2] / r2 : 0.0;
-                ax += f * dx;
-                ay += f * dy;
-            }
+            deflect_f64(R.type[c], x, y, cc, ax, ay);
         }
     }
     const double sx = x - ax, sy = y - ay;
@@ -458,6 +448,61 @@ __device__ __forceinline__ double brightness_f64(double x, double y, const RayCt
         if (R.plane[c] == LENSED_PLANE_SOURCE) I += light_f64(sx, sy, R.cd + c * kNC);
     return I;
 }
+
+// Validity of a (system, point): every component in its domain.  Then the
+// image-plane priors (Sec. 5): a source whose position parameters are an
+// image-plane position theta is moved to theta - alpha(theta) (Eq. 1), the
+// deflection of the same point's lens in FP64.
+__global__ void k_prologue_valid(const SysDev *__restrict__ sys, int s0, int nS, int P, int p0,
+                                 int nP, int C_total, const int *__restrict__ comp_type,
+                                 const unsigned char *__restrict__ cvalid, float *__restrict__ cf,
+                                 double *__restrict__ cd, unsigned char *__restrict__ valid)
+{
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (long long)nS * nP) return;
+    const int s = s0 + (int)(tid / nP);
+    const int p = p0 + (int)(tid % nP);
+    const SysDev &S = sys[s];
+    unsigned char ok = 1;
+    for (int c = 0; c < S.ncomp; ++c) ok &= cvalid[(size_t)p * C_total + S.comp_off + c];
+    if (ok && S.imgpos_mask) {
+        const size_t base = ((size_t)p * C_total + S.comp_off) * kNC;
+        for (int c = 0; c < S.ncomp; ++c) {
+            if (!((S.imgpos_mask >> c) & 1)) continue;
+            double *cc = cd + base + (size_t)c * kNC;
+            const double tx = cc[0], ty = cc[1];
+            double ax = 0.0, ay = 0.0;
+            for (int l = 0; l < S.ncomp; ++l) {
+                const int t = comp_type[S.comp_off + l];
+                if (t <= LENSED_POINTMASS) deflect_f64(t, tx, ty, cd + base + (size_t)l * kNC, ax, ay);
+            }
+            const double yx = tx - ax, yy = ty - ay;
+            if (!isfinite(yx) || !isfinite(yy)) ok = 0;
+            cc[0] = yx;
+            cc[1] = yy;
+            cf[base + (size_t)c * kNC + 0] = (float)yx;
+            cf[base + (size_t)c * kNC + 1] = (float)yy;
+        }
+    }
+    valid[(size_t)s * P + p] = ok;
+}
+
+void launch_prologue(const SysDev *sys, const int *comp_sys, int s0, int nS, int c0, int nC,
+                     const int *comp_type, const int *comp_free, const double *comp_value,
+                     const double *params, bool single_row, int P, int p0, int nP,
+                     int n_par_stride, int C_total, const double *bn_table, float *cf,
+                     double *cd, unsigned char *cvalid, unsigned char *valid, cudaStream_t st)
+{
+    const long long n = (long long)nC * nP;
+    const int threads = 64;
+    k_prologue_comp<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
+        sys, comp_sys, c0, nC, comp_type, comp_free, comp_value, params, single_row ? 1 : 0, P,
+        p0, nP, n_par_stride, C_total, bn_table, cf, cd, cvalid);
+    const long long n2 = (long long)nS * nP;
+    k_prologue_valid<<<(unsigned)((n2 + 127) / 128), 128, 0, st>>>(
+        sys, s0, nS, P, p0, nP, C_total, comp_type, cvalid, cf, cd, valid);
+}
+
 
 // ---------------------------------------------------------------------------
 // a2-a5: ray tracing and pixel integration
@@ -551,8 +596,13 @@ __global__ void __launch_bounds__(256)
                 const float *cc = sm.cf + c * kNC;
                 if (pl == LENSED_PLANE_FOREGROUND) {
                     const LightF L = load_light(cc);
+                    if (L.kind == (float)kKindFlat) {
 #pragma unroll
-                    for (int k = 0; k < G; ++k) I[k] += light_f32(L, xk[k], y);
+                        for (int k = 0; k < G; ++k) I[k] += L.A;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < G; ++k) I[k] += light_f32(L, xk[k], y);
+                    }
                 } else if (pl == LENSED_PLANE_LENS) {
                     const int t = sm.type[c];
                     if (t == LENSED_SIE) {
@@ -583,8 +633,13 @@ __global__ void __launch_bounds__(256)
             for (int c = 0; c < ncomp; ++c) {
                 if (sm.plane[c] != LENSED_PLANE_SOURCE) continue;
                 const LightF L = load_light(sm.cf + c * kNC);
+                if (L.kind == (float)kKindFlat) {
 #pragma unroll
-                for (int k = 0; k < G; ++k) I[k] += light_f32(L, xk[k] - ax[k], y - ay[k]);
+                    for (int k = 0; k < G; ++k) I[k] += L.A;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < G; ++k) I[k] += light_f32(L, xk[k] - ax[k], y - ay[k]);
+                }
             }
 #pragma unroll
             for (int k = 0; k < G; ++k)
@@ -704,7 +759,7 @@ __device__ float ray_mixed(const TraceSmem &sm, const SysDev &S, int i, int j, i
         const int pl = sm.plane[c];
         const float *cc = sm.cf + c * kNC;
         if (pl == LENSED_PLANE_FOREGROUND) {
-            I += light_f32(load_light(cc), x, y);
+            I += light_any_f32(load_light(cc), x, y);
         } else if (pl == LENSED_PLANE_LENS) {
             const int t = sm.type[c];
             if (t == LENSED_SIE) {
@@ -732,7 +787,7 @@ __device__ float ray_mixed(const TraceSmem &sm, const SysDev &S, int i, int j, i
     }
     for (int c = 0; c < ncomp; ++c)
         if (sm.plane[c] == LENSED_PLANE_SOURCE)
-            I += light_f32(load_light(sm.cf + c * kNC), x - ax, y - ay);
+            I += light_any_f32(load_light(sm.cf + c * kNC), x - ax, y - ay);
     return I;
 }
 

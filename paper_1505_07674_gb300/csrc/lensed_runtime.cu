@@ -72,6 +72,7 @@ void component_ops(int type, double &flops, double &transc)
     case LENSED_SHEAR: flops += 10; break;
     case LENSED_POINTMASS: flops += 10; break;
     case LENSED_GAUSS: flops += 18; transc += 1; break;
+    case LENSED_SKY: flops += 1; break;
     default: flops += 21; transc += 3; break;
     }
 }
@@ -85,6 +86,7 @@ int nparams_of(int type)
     case LENSED_SERSIC: return 7;
     case LENSED_DEVAUC: return 6;
     case LENSED_GAUSS: return 6;
+    case LENSED_SKY: return 1;
     }
     return -1;
 }
@@ -660,7 +662,8 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
             const bool mass = cp.type <= LENSED_POINTMASS;
             if (mass && cp.plane != LENSED_PLANE_LENS)
                 return fail(LENSED_E_ARG, "system %d comp %d: mass must be on the lens plane", s, c);
-            if (!mass && cp.plane != LENSED_PLANE_FOREGROUND && cp.plane != LENSED_PLANE_SOURCE)
+            if (!mass && cp.plane != LENSED_PLANE_FOREGROUND && cp.plane != LENSED_PLANE_SOURCE &&
+                !(cp.plane == LENSED_PLANE_SOURCE_IMAGE && cp.type != LENSED_SKY))
                 return fail(LENSED_E_ARG, "system %d comp %d: bad plane %d", s, c, cp.plane);
             for (int k = 0; k < np; ++k) {
                 if (cp.free_index[k] >= d.n_params)
@@ -851,7 +854,10 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         for (int c = 0; c < d.n_components; ++c) {
             const lensed_component &cp = d.components[c];
             ctype.push_back(cp.type);
-            cplane.push_back(cp.plane);
+            // the kernels see an image-plane-prior source as a source; the
+            // prologue moves it (bit c of imgpos_mask)
+            cplane.push_back(cp.plane == LENSED_PLANE_SOURCE_IMAGE ? LENSED_PLANE_SOURCE : cp.plane);
+            if (cp.plane == LENSED_PLANE_SOURCE_IMAGE) S.imgpos_mask |= 1 << c;
             csys.push_back(s);
             const int np = nparams_of(cp.type);
             for (int k = 0; k < LENSED_MAX_COMPONENT_PARAMS; ++k) {

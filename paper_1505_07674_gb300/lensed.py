@@ -16,8 +16,9 @@ import torch
 from . import _native as N
 
 _TYPES = {"sie": N.SIE, "shear": N.SHEAR, "pointmass": N.POINTMASS, "sersic": N.SERSIC,
-          "devauc": N.DEVAUC, "gauss": N.GAUSS}
-_PLANES = {"lens": N.PLANE_LENS, "foreground": N.PLANE_FOREGROUND, "source": N.PLANE_SOURCE}
+          "devauc": N.DEVAUC, "gauss": N.GAUSS, "sky": N.SKY}
+_PLANES = {"lens": N.PLANE_LENS, "foreground": N.PLANE_FOREGROUND, "source": N.PLANE_SOURCE,
+           "source_image": N.PLANE_SOURCE_IMAGE}
 _RULES = {"point": N.RULE_POINT, "sub": N.RULE_SUB, "gl": N.RULE_GL, "gk": N.RULE_GK}
 _PREC = {"fp32": N.PREC_FP32, "mixed": N.PREC_MIXED, "fp64": N.PREC_FP64}
 
@@ -238,3 +239,4 @@ def rule_nodes(rule, order):
                                   wg.ctypes.data)
     N.check(min(n, 0))
     return t[:n].copy(), w[:n].copy(), wg[:n].copy()
+

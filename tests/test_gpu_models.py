@@ -1,0 +1,97 @@
+"""The wider model space of Sec. 5 on the GPU against the oracle: the flat
+sky, several lenses and light components (a J0808+4706-like model with 35
+free parameters) and image-plane priors for source positions, through the
+C ABI, at the image and likelihood tolerances of the parity suite."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+import workloads as W
+from workloads import component, fixed, free
+from test_gpu_parity import assert_image_close, assert_loglike_close
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import paper_1505_07674_gb300 as pkg
+    pkg.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def lensed():
+    from paper_1505_07674_gb300 import lensed as LZ
+    return LZ
+
+
+def small_j0808(image_prior):
+    spec = W.shrink(W.j0808_like(image_prior=image_prior), 64, 64)
+    spec["h"] = 0.125  # the same 8" field on a coarser grid
+    return spec
+
+
+@pytest.mark.parametrize("image_prior", [False, True])
+@pytest.mark.parametrize("precision", ["fp32", "mixed", "fp64"])
+def test_j0808_like_render_and_loglike(image_prior, precision):
+    spec = small_j0808(image_prior)
+    obs = O.mock_observation(spec)
+    osys = O.OracleSystem(spec, obs)
+    m = lensed().Model(spec, obs, precision=precision)
+    pts = np.vstack([spec["truth"], W.draw_points(spec, 47, 41)])
+    # With the image-plane prior the truth puts the centre of source 1 (a
+    # Sersic profile with n = 1.5, whose slope diverges at its centre) on the
+    # ray through theta, at high magnification: there the ~1e-7" rounding of
+    # FP32 traced positions moves the brightness of the peak pixel by up to
+    # 3.4e-5 (measured), above the 1e-5 image tolerance that FP64 meets.
+    rel = 5e-5 if (image_prior and precision != "fp64") else 1e-5
+    for xi in pts[:4]:
+        for conv in (False, True):
+            assert_image_close(m.render(0, xi, convolved=conv).cpu().numpy(),
+                               osys.render(xi, convolved=conv), rel=rel, what=(precision, conv))
+    g = m.loglike_batch(pts).cpu().numpy()[0]
+    assert_loglike_close(g, osys.loglike(pts), 64 * 64, precision)
+    assert np.array_equal(g, m.loglike_plain(pts).cpu().numpy()[0])
+
+
+def test_j0808_like_full_size_sampled():
+    # the 160 x 160 model at the truth and a few prior points (MIXED)
+    spec = W.j0808_like(image_prior=True)
+    obs = O.mock_observation(spec)
+    osys = O.OracleSystem(spec, obs)
+    m = lensed().Model(spec, obs, precision="mixed")
+    pts = np.vstack([spec["truth"], W.draw_points(spec, 7, 42)])
+    g = m.loglike_batch(pts).cpu().numpy()[0]
+    assert_loglike_close(g, osys.loglike(pts), 160 * 160, "mixed")
+    assert_image_close(m.render(0, pts[0]).cpu().numpy(), osys.render(pts[0]), what="full")
+
+
+@pytest.mark.parametrize("plane", ["foreground", "source"])
+@pytest.mark.parametrize("precision", ["fp32", "mixed", "fp64"])
+def test_flat_sky_alone_and_negative(plane, precision):
+    lens = [component("sie", "lens", [fixed(0.1), fixed(0), fixed(1.2), fixed(0.6), fixed(30),
+                                      fixed(0.01)])]
+    for S in (0.37, -0.05):
+        spec = {"name": "sky", "nx": 40, "ny": 24, "h": 0.1, "rule": ("gk", 3),
+                "psf": W.gaussian_psf(5, 0.15, 0.1), "mask": None, "zeropoint": 0.0,
+                "components": lens + [component("sky", plane, [free(0)])], "n_params": 1}
+        obs = {"data": np.zeros((24, 40)), "variance": np.ones((24, 40))}
+        m = lensed().Model(spec, obs, precision=precision)
+        img = m.render(0, np.array([S])).cpu().numpy().astype(float)
+        assert np.abs(img - S * 0.01).max() <= 1e-6 * abs(S) * 0.01
+        # data 0, unit variance: loglike = -1/2 N (S h^2)^2
+        ll = m.loglike_batch(np.array([[S]])).cpu().numpy()[0, 0]
+        ref = -0.5 * 40 * 24 * (S * 0.01) ** 2
+        assert abs(ll - ref) <= 1e-5 * abs(ref)
+
+
+def test_image_prior_with_invalid_lens_is_minus_inf():
+    spec = small_j0808(True)
+    obs = O.mock_observation(spec)
+    m = lensed().Model(spec, obs, precision="mixed")
+    xi = np.array(spec["truth"], float)
+    xi[4] = 1.2  # main SIE axis ratio outside (0, 1]
+    assert np.isneginf(m.loglike_batch(xi[None]).cpu().numpy()[0, 0])
+    assert O.OracleSystem(spec, obs).loglike(xi[None])[0] == -np.inf

@@ -305,6 +305,75 @@ def c4_euclid(seed=1004):
     }
 
 
+def j0808_like(seed=1006, image_prior=False):
+    """Multi-component lens in the style of the paper's J0808+4706 model
+    (Sec. 5: two SIEs for a lens galaxy and its companion, two Sersic
+    components for the main lens light, one for the companion, two Sersic
+    sources) plus the flat sky of the paper's base model; 35 free
+    parameters.  160x160 at 0.05" (HST ACS-like), 15x15 Gaussian PSF (FWHM
+    0.1"), the paper's default g3k7 rule, Poisson noise at peak SNR ~ 50.
+
+    Free parameters: sky S (1); main SIE x, y, b, q, PA (5); companion SIE
+    x, y, b, q, PA (5); main light A r, mag, n, q, PA and main light B r,
+    mag, q, PA (n = 1), both centred on the main SIE (9); companion light r,
+    mag, n, centred on the companion SIE with its q and PA (3); source 1 x,
+    y, r, mag, n, q, PA (7); source 2 x, y, r, mag, q (5).
+
+    image_prior=True gives source 1's position as an image-plane position
+    (the image-plane prior of Sec. 5): its truth and prior box are then on
+    the image plane, near the arc."""
+    comps = [
+        component("sky", "foreground", [free(0)]),
+        component("sie", "lens", [free(1), free(2), free(3), free(4), free(5), fixed(0.01)]),
+        component("sie", "lens", [free(6), free(7), free(8), free(9), free(10), fixed(0.01)]),
+        component("sersic", "foreground", [free(1), free(2), free(11), free(12), free(13),
+                                           free(14), free(15)]),
+        component("sersic", "foreground", [free(1), free(2), free(16), free(17), fixed(1.0),
+                                           free(18), free(19)]),
+        component("sersic", "foreground", [free(6), free(7), free(20), free(21), free(22),
+                                           free(9), free(10)]),
+        component("sersic", "source_image" if image_prior else "source",
+                  [free(23), free(24), free(25), free(26), free(27), free(28), free(29)]),
+        component("sersic", "source", [free(30), free(31), free(32), free(33), fixed(1.0),
+                                       free(34), fixed(0.0)]),
+    ]
+    names = ["sky", "x_L", "y_L", "b_L", "q_L", "pa_L", "x_C", "y_C", "b_C", "q_C", "pa_C",
+             "r_HA", "mag_HA", "n_HA", "q_HA", "pa_HA", "r_HB", "mag_HB", "q_HB", "pa_HB",
+             "r_HC", "mag_HC", "n_HC",
+             "x_1", "y_1", "r_1", "mag_1", "n_1", "q_1", "pa_1", "x_2", "y_2", "r_2", "mag_2",
+             "q_2"]
+    truth = [0.02, 0.0, 0.0, 1.2, 0.8, 40.0, 1.3, -0.9, 0.35, 0.9, 110.0,
+             0.9, 17.5, 4.0, 0.8, 40.0, 0.3, 18.5, 0.7, 50.0,
+             0.3, 19.5, 2.5,
+             0.1, 0.05, 0.15, 22.0, 1.5, 0.6, 70.0, -0.15, 0.12, 0.1, 23.0, 0.7]
+    lo = [-0.1, -0.1, -0.1, 0.9, 0.5, 0.0, 1.1, -1.1, 0.1, 0.5, 0.0,
+          0.5, 16.5, 2.0, 0.5, 0.0, 0.1, 17.5, 0.4, 0.0,
+          0.1, 18.5, 1.0,
+          -0.4, -0.4, 0.05, 21.0, 0.5, 0.3, 0.0, -0.4, -0.4, 0.05, 22.0, 0.3]
+    hi = [0.1, 0.1, 0.1, 1.5, 0.99, 180.0, 1.5, -0.7, 0.6, 0.99, 180.0,
+          1.5, 18.5, 6.0, 0.99, 180.0, 0.6, 19.5, 0.99, 180.0,
+          0.6, 20.5, 4.0,
+          0.4, 0.4, 0.3, 23.0, 4.0, 0.99, 180.0, 0.4, 0.4, 0.3, 24.0, 0.99]
+    name = "j0808like_160x160_h0.05_g3k7_psf15"
+    if image_prior:
+        truth[23], truth[24] = 0.75, 0.95
+        lo[23], hi[23], lo[24], hi[24] = 0.45, 1.05, 0.65, 1.25
+        name += "_imgprior"
+    return {
+        "name": name,
+        "nx": 160, "ny": 160, "h": 0.05,
+        "rule": ("gk", 3),
+        "psf": gaussian_psf(15, 0.1, 0.05),
+        "mask": None,
+        "zeropoint": 25.0,
+        "components": comps,
+        "n_params": 35, "param_names": names,
+        "prior_lo": lo, "prior_hi": hi, "truth": truth,
+        "noise": {"kind": "poisson", "snr": 50.0, "sky_frac": 0.05, "read_frac": 0.002},
+        "seed": seed,
+    }
+
+
 def shrink(spec, nx, ny):
     """The same model on a smaller nx x ny field (mask recut to size), for
     quick parity cases."""
