@@ -45,6 +45,7 @@ WORKLOADS = {
     "c4": ("euclid_400x400_h0.1_18par_nested_sampling_2000live", 0),
     "c5": ("euclid_400x400_h0.1_18par_surrogate_prescreen_65536", 0),
     "j0808": ("j0808like_160x160_h0.05_2sie_sky_5sersic_imageprior_psf15_g3k7_1024pts_35par", 1024),
+    "rules": ("rule_comparison_120x120_sie_devauc_sersic_18par_point_sub2_sub4_g3k7_g5k11_g7k15", 0),
 }
 # image, rule and PSF of the throughput workloads (for the JSON config)
 SHAPES = {
@@ -73,7 +74,13 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
                     help="c2 (default, the benchmark), c1 or c3 (other configurations), "
                          "c4 (posterior run), c5 (surrogate pre-screen vs plain), j0808 "
-                         "(35-parameter multi-component model with sky and image-plane prior)")
+                         "(35-parameter multi-component model with sky and image-plane prior), "
+                         "rules (integration-rule comparison: posterior errors per rule)")
+    ap.add_argument("--mocks", type=int, default=12, help="mock systems (rules)")
+    ap.add_argument("--rules-live", type=int, default=400, help="live points (rules)")
+    ap.add_argument("--rules-noiseless", action="store_true",
+                    help="rules: noiseless mocks (noise model kept for the variance), so that "
+                         "the errors measure the integration rule alone")
     ap.add_argument("--live", type=int, default=2000, help="live points (c4, c5)")
     ap.add_argument("--oracle-points", type=int, default=384,
                     help="posterior points the CPU oracle re-evaluates (c4)")
@@ -288,6 +295,100 @@ def run_posterior(args):
     return 0
 
 
+RULE_SET = (("point", 1), ("sub", 2), ("sub", 4), ("gk", 3), ("gk", 5), ("gk", 7))
+RULE_NAMES = ("point", "sub2", "sub4", "g3k7", "g5k11", "g7k15")
+
+
+def run_rules(args):
+    """rules: the paper's integration-rule comparison (Sec. 4.5) on synthetic
+    mocks.  Each mock is rendered by the library in FP64 with a 16x16
+    Gauss-Legendre rule plus seeded noise, then reconstructed by nested
+    sampling once per rule (point, sub2, sub4, g3k7, g5k11, g7k15; MIXED
+    precision); the errors Delta = posterior mean - input value are reported
+    as mean and standard deviation over the mocks, per rule and parameter."""
+    import torch
+
+    import workloads as W
+    from paper_1505_07674_gb300 import build as build_lib
+    from paper_1505_07674_gb300 import lensed as LZ
+    from paper_1505_07674_gb300.posterior import GpuLikelihood
+    from paper_1505_07674_gb300.sampler import nested_sampling
+
+    torch.cuda.set_device(0)
+    build_lib()
+    deltas = {r: [] for r in RULE_NAMES}
+    means = {r: [] for r in RULE_NAMES}
+    evals = {r: 0 for r in RULE_NAMES}
+    like_s = {r: 0.0 for r in RULE_NAMES}
+    chi2 = {r: [] for r in RULE_NAMES}
+    psd = {r: [] for r in RULE_NAMES}
+    names = None
+    t0 = time.perf_counter()
+    sampler = ClockSampler(0)
+    sampler.start()
+    for k in range(args.mocks):
+        spec = W.rules_mock(k)
+        names = spec["param_names"]
+        zeros = {"data": np.zeros((spec["ny"], spec["nx"])),
+                 "variance": np.ones((spec["ny"], spec["nx"]))}
+        probe = LZ.Model(spec, zeros, precision="fp64")
+        noiseless = probe.render(0, np.asarray(spec["truth"])).double().cpu().numpy()
+        probe.close()
+        obs = W.add_noise(spec, noiseless, spec["seed"])
+        if args.rules_noiseless:
+            # the noise model's gain and offset, the noiseless image as data:
+            # the posterior mean then moves only by the rule's integration error
+            obs["data"] = noiseless
+        truth = np.asarray(spec["truth"])
+        for rule, rname in zip(RULE_SET, RULE_NAMES):
+            sr = dict(spec, rule=rule)
+            m = LZ.Model(sr, obs, precision=args.precision)
+            like = GpuLikelihood(m, sr)
+            res = nested_sampling(like, like.ndim, args.rules_live, seed=300 + k, dlogz=0.5,
+                                  max_evals=3_000_000)
+            post = like.to_params(res.posterior_mean())
+            psd[rname].append(res.posterior_sd() * (like.hi - like.lo))
+            d = post - truth
+            for j, nm in enumerate(names):
+                if nm.startswith("pa"):
+                    d[j] = (d[j] + 90.0) % 180.0 - 90.0  # position angles are periodic
+            deltas[rname].append(d)
+            means[rname].append(post)
+            evals[rname] += res["n_evals"]
+            like_s[rname] += like.seconds
+            chi2[rname].append(-2.0 * float(res["logl"].max()) / (spec["nx"] * spec["ny"]))
+            m.close()
+    clocks = sampler.stop()
+    summary = {}
+    ref_mean, ref_sd = np.asarray(means["g7k15"]), np.asarray(psd["g7k15"])
+    for rname in RULE_NAMES:
+        D = np.asarray(deltas[rname])
+        # shift of the posterior mean against the finest rule on the same
+        # mock, in units of that posterior's standard deviation: the part of
+        # the error that the rule causes
+        sh = np.asarray(means[rname]) - ref_mean
+        for j, nm in enumerate(names):
+            if nm.startswith("pa"):
+                sh[:, j] = (sh[:, j] + 90.0) % 180.0 - 90.0
+        summary[rname] = {
+            "delta_mean": dict(zip(names, np.round(D.mean(0), 5).tolist())),
+            "delta_sd": dict(zip(names, np.round(D.std(0), 5).tolist())),
+            "posterior_sd_mean": dict(zip(names, np.round(np.mean(psd[rname], 0), 5).tolist())),
+            "shift_vs_g7k15_in_sd": dict(zip(names, np.round(
+                np.mean(np.abs(sh) / np.maximum(ref_sd, 1e-12), 0), 3).tolist())),
+            "n_evals": evals[rname], "likelihood_s": round(like_s[rname], 2),
+            "min_chi2_per_pixel_median": round(float(np.median(chi2[rname])), 4),
+        }
+    line = {"metric": "integration-rule comparison: posterior-mean errors per rule",
+            "workload": WORKLOADS["rules"][0], "mocks": args.mocks, "n_live": args.rules_live,
+            "precision_mode": args.precision, "mock_rule": "gauss-legendre 16x16, FP64",
+            "noiseless_data": bool(args.rules_noiseless),
+            "rules": summary, "wall_s": round(time.perf_counter() - t0, 1), "clocks": clocks,
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_surrogate(args):
     """c5: wall time to the evidence estimate with the surrogate versus the
     plain batched run (same seed).  Two surrogate modes: retrained online
@@ -376,12 +477,15 @@ def main():
         return run_posterior(args)
     if args.workload == "c5":
         return run_surrogate(args)
+    if args.workload == "rules":
+        return run_rules(args)
 
     import torch
 
     import workloads as W
     from paper_1505_07674_gb300 import build as build_lib
     from paper_1505_07674_gb300 import lensed as LZ
+    from paper_1505_07674_gb300.shard import reduce_max, shard_range
 
     rank, world, local = dist_env()
     if world > 1:
@@ -409,9 +513,11 @@ def main():
         obs.append(W.add_noise(spec, noiseless, spec["seed"]))
     m = LZ.Model(specs, obs, precision=args.precision)
     npts = args.points if args.points != POINTS or args.workload == "c2" else default_pts
+    # weak scaling: world x npts seeded points, each rank its contiguous share
     pts = np.zeros((len(specs), npts, m.n_params_max))
+    lo_, hi_ = shard_range(world * npts, rank, world)
     for s_, spec in enumerate(specs):
-        pts[s_, :, :spec["n_params"]] = W.draw_points(spec, npts, 4242 + rank + 7919 * s_)
+        pts[s_, :, :spec["n_params"]] = W.draw_points(spec, world * npts, 4242 + 7919 * s_)[lo_:hi_]
     params = m.pack_params(pts)
     n_sys = len(specs)
     out = torch.empty((n_sys, npts), dtype=torch.float64, device="cuda")
@@ -447,10 +553,8 @@ def main():
         torch.cuda.synchronize()
         dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
         if world > 1:
-            t = torch.tensor([dev_ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dev_ms = reduce_max(dev_ms, device="cuda")
             torch.distributed.barrier()
-            dev_ms = float(t.item())
         ll = out.cpu().numpy()[0]
 
         # ---- per-stage timing of the same schedule (events around launches)
@@ -493,9 +597,7 @@ def main():
         m.loglike_batch_host(host_params, host_out, stream=stream)
     e2e_s = (time.perf_counter() - t0) / k_e2e
     if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = reduce_max(e2e_s, device="cuda")
 
     if rank != 0:
         torch.distributed.destroy_process_group()

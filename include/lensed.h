@@ -273,15 +273,23 @@ int lensed_loglike_batch_host(lensed_model *m, const double *params_host, int P,
 int lensed_loglike_batch_noalloc(lensed_model *m, const double *params, int P,
                                  double *out_loglike, void *stream);
 
-/* Time the candidate tile configurations on a batch of P points drawn
- * inside the given DEVICE parameter array (same layout as
- * lensed_loglike_batch) and keep the fastest for later batched calls.
- * Results do not depend on the choice.  Synchronous. */
+/* Time the candidate launch configurations (trace block size; PSF applied
+ * directly or, where the PSF has numerical rank <= 3, as separable passes)
+ * on a batch of P points drawn inside the given DEVICE parameter array (same
+ * layout as lensed_loglike_batch) and keep the fastest for later calls.  The
+ * trace block size never changes a result; the PSF mode changes the FP32
+ * summation order of Eq. 15 (differences at the float rounding level).
+ * Synchronous. */
 int lensed_autotune(lensed_model *m, const double *params, int P, void *stream);
 
-/* Index of the configuration the autotuner picked (-1: default) and its
- * description, for reports. */
+/* Index of the configuration in use (-1: default) and its description, for
+ * reports. */
 int lensed_tuned_config(const lensed_model *m, char *buf, int buflen);
+
+/* Use configuration `index` (0 .. n-1 as lensed_tuned_config numbers them,
+ * -1 = default) instead of the autotuner's choice; returns the number of
+ * configurations n, or LENSED_E_ARG for an index out of range. */
+int lensed_set_config(lensed_model *m, int index);
 
 /* Launch plan of one lensed_loglike_batch call with P points: number of
  * kernels it launches (*launches) and the number of points per scratch

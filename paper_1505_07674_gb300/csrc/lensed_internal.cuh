@@ -27,6 +27,10 @@ constexpr int kPsfThreads = (kTileW / kOutPerThread) * kTileH;  // 256
 constexpr int kKindPower = 0;  // Sersic / de Vaucouleurs: 2^-(2^(p2 lg2 R^2 + lc))
 constexpr int kKindGauss = 1;  // Gaussian: 2^-(k R^2)
 constexpr int kKindFlat = 2;   // flat sky: the constant A
+// Device plane of a foreground light component whose parameters are all
+// fixed: its pixel integral is the same for every parameter point, so it is
+// computed once per model (in FP64) and the ray kernels skip it.
+constexpr int kPlanePrecomputed = 4;
 
 // SIE evaluation in MIXED precision switches to FP64 for every pixel when
 // e = sqrt(1 - q^2) < kMixedRoundE, and for the pixels whose square comes
@@ -62,6 +66,9 @@ struct SysDev {
     int tiles_x, tiles_y;   // full tiling of the image
     double zeropoint;
     int imgpos_mask;        // bit c: component c is a source placed by an image-plane prior
+    long long pre_off;      // into the precomputed luminosity table, -1 if none
+    int psf_rank;           // > 0: the PSF is applied as a sum of psf_rank separable terms
+    int psf_sep_off;        // into the float PSF table: per term, column then row factor
 };
 
 // Trace-kernel block table entry: system and the range [start, end) of its
@@ -73,9 +80,14 @@ struct TraceBlock {
 
 // Quadrature nodes: 1-D offsets t*h from the pixel centre, and the 2-D
 // weights W_a W_b (float copy adjusted so that it sums to one).
+// pre_f / pre_d: per-pixel luminosity of the components that do not depend
+// on the parameter point (see kPlanePrecomputed), at SysDev::pre_off; NULL
+// while that table is being computed.
 struct NodeTables {
     const float *u, *w;
     const double *ud, *wd;
+    const float *pre_f;
+    const double *pre_d;
 };
 
 // PSF-kernel block table entry: system and tile origin.
@@ -87,6 +99,7 @@ struct PsfBlock {
 
 struct LaunchCfg {
     int trace_threads;  // threads per trace block, one pixel each
+    int psf_sep;        // 1: PSFs of low rank run as separable passes
 };
 
 // --- kernels launched from the runtime (defined in lensed_kernels.cu) ---
@@ -125,8 +138,9 @@ void launch_fix64(LaunchCfg cfg, const SysDev *sys, int s0, int nS, const int *c
 
 // a6-a7: PSF convolution of the tiles in the block table, then either the
 // masked chi^2 partial sums (partial != nullptr) or the convolved image
-// (out != nullptr, one point).
-void launch_psf(int precision, int q, int p_max, const SysDev *sys, const float *psf_f,
+// (out != nullptr, one point).  sep > 0 (FP32 modes): every system of the
+// table applies its PSF as SysDev::psf_rank <= sep separable terms.
+void launch_psf(int precision, int q, int sep, int p_max, const SysDev *sys, const float *psf_f,
                 const double *psf_d, const float *data, const float *weight,
                 const double *data_d, const double *weight_d,
                 const unsigned char *valid, int P, const PsfBlock *blocks, int n_blocks, int p0,

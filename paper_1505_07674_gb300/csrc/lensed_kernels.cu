@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(256)
     const float xc = fmaf(jc, S.h, jc * S.h_lo);
     const float yc = fmaf(ic, S.h, ic * S.h_lo);
 
-    float acc = 0.f;
+    float acc = (nodes.pre_f && S.pre_off >= 0) ? nodes.pre_f[S.pre_off + pix] : 0.f;
     for (int b = 0; b < nn; ++b) {
         const float y = yc + sm.u[b];
         for (int a0 = 0; a0 < nn; a0 += G) {
@@ -673,7 +673,7 @@ __global__ void __launch_bounds__(256)
     const int i = pix / nx, j = pix - (pix / nx) * nx;
     const double xc = ((double)j - (double)S.cx) * S.hd;
     const double yc = ((double)i - (double)S.cy) * S.hd;
-    double acc = 0.0;
+    double acc = (nodes.pre_d && S.pre_off >= 0) ? nodes.pre_d[S.pre_off + pix] : 0.0;
     for (int b = 0; b < nn; ++b) {
         const double y = yc + sm.ud[b];
         for (int a = 0; a < nn; ++a) acc += sm.wd[b * nn + a] * brightness_f64(xc + sm.ud[a], y, R);
@@ -805,7 +805,7 @@ constexpr int kFixRays = 1024;  // ray contributions staged per batch
 
 // Recompute the pixels of s_pix[0..n) (batches of kFixRays / (nn*nn)).
 __device__ void fix_pixels(const TraceSmem &sm, const SysDev &S, const int *s_pix, int n,
-                           float *s_ray, float *L)
+                           float *s_ray, float *L, const float *pre)
 {
     const int nn = S.nn, nr = nn * nn, nx = S.nx;
     const int per = kFixRays / nr;
@@ -818,7 +818,7 @@ __device__ void fix_pixels(const TraceSmem &sm, const SysDev &S, const int *s_pi
         }
         __syncthreads();
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
-            float acc = 0.f;
+            float acc = pre ? pre[s_pix[b0 + k]] : 0.f;
             for (int r = 0; r < nr; ++r) acc = fmaf(sm.w[r], s_ray[k * nr + r], acc);
             L[s_pix[b0 + k]] = acc;
         }
@@ -846,6 +846,7 @@ __global__ void __launch_bounds__(128)
     __syncthreads();
     const int ncomp = S.ncomp, nx = S.nx, ny = S.ny;
     float *L = Lbuf + (size_t)(p - p0) * L_stride + S.pix_off;
+    const float *pre = (nodes.pre_f && S.pre_off >= 0) ? nodes.pre_f + S.pre_off : nullptr;
     bool whole = false;
     for (int c = 0; c < ncomp; ++c)
         if (sm.type[c] == LENSED_SIE && sm.cd[c * kNC + 17] != 0.0) whole = true;
@@ -857,7 +858,7 @@ __global__ void __launch_bounds__(128)
             for (int k = threadIdx.x; k < m; k += blockDim.x)
                 s_pix[k] = need ? need[S.need_off + q0 + k] : q0 + k;
             __syncthreads();
-            fix_pixels(sm, S, s_pix, m, s_ray, L);
+            fix_pixels(sm, S, s_pix, m, s_ray, L, pre);
         }
         return;
     }
@@ -891,7 +892,7 @@ __global__ void __launch_bounds__(128)
             __syncthreads();
             const int n = s_n;
             __syncthreads();
-            fix_pixels(sm, S, s_pix, n, s_ray, L);
+            fix_pixels(sm, S, s_pix, n, s_ray, L, pre);
         }
     }
 }
@@ -1049,6 +1050,162 @@ __global__ void __launch_bounds__(kPsfThreads)
     }
 }
 
+// a6-a7 with a PSF of low numerical rank, F = sum_k c_k r_k^T (FP32 modes):
+// the staged tile + halo is convolved along rows with each r_k (pass 1, into
+// shared memory), then along columns with c_k (pass 2), which is the same
+// two-dimensional sum of Eq. 15 on the clamped tile, in (2q+1)(32+2p)/32 +
+// (2p+1) multiply-adds per term and output instead of (2p+1)(2q+1).  The
+// output mapping, the warp skip and the chi^2 reduction are those of k_psf.
+template <int Q>
+__global__ void __launch_bounds__(kPsfThreads)
+    k_psf_sep(const SysDev *__restrict__ sys, const float *__restrict__ psf,
+              const float *__restrict__ data, const float *__restrict__ weight,
+              const unsigned char *__restrict__ valid, int P, const PsfBlock *__restrict__ blocks,
+              int p0, const float *__restrict__ Lbuf, long long L_stride,
+              double *__restrict__ partial, int T_total, float *__restrict__ out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int W = 2 * Q + 1;
+    constexpr int WS = (W + 3) & ~3;
+    const PsfBlock pb = blocks[blockIdx.x];
+    const int p = p0 + blockIdx.y;
+    const SysDev &S = sys[pb.sys];
+    const bool ok = valid[(size_t)pb.sys * P + p] != 0;
+    const int Ph = S.psf_p, R = S.psf_rank;
+    const int rows = kTileH + 2 * Ph;
+    const int stride = psf_row_stride(Q);
+    const int nx = S.nx, ny = S.ny;
+    float *s_L = reinterpret_cast<float *>(smem_raw);
+    float *s_H = s_L + (size_t)rows * stride;        // [R][rows][kTileW]
+    float *s_c = s_H + (size_t)R * rows * kTileW;    // [R][2p+1]
+    float *s_r = s_c + R * (2 * Ph + 1);             // [R][WS]
+
+    if (!ok) {
+        if (out) {
+            for (int k = threadIdx.x; k < kTileW * kTileH; k += blockDim.x) {
+                const int i = pb.i0 + k / kTileW, j = pb.j0 + k % kTileW;
+                if (i < ny && j < nx) out[(size_t)i * nx + j] = __int_as_float(0x7fc00000);
+            }
+        }
+        return;
+    }
+    const float *fac = psf + S.psf_sep_off;
+    const int nf = 2 * Ph + 1 + W;
+    for (int k = threadIdx.x; k < R * (2 * Ph + 1); k += blockDim.x)
+        s_c[k] = fac[(k / (2 * Ph + 1)) * nf + k % (2 * Ph + 1)];
+    for (int k = threadIdx.x; k < R * WS; k += blockDim.x) {
+        const int t = k / WS, l = k - (k / WS) * WS;
+        s_r[k] = l < W ? fac[t * nf + 2 * Ph + 1 + l] : 0.f;
+    }
+    const float *L = Lbuf + (size_t)(p - p0) * L_stride + S.pix_off;
+    const int cols = kTileW + 2 * Q;
+    for (int k = threadIdx.x; k < rows * cols; k += blockDim.x) {
+        const int r = k / cols, c = k - (k / cols) * cols;
+        const int gi = min(max(pb.i0 - Ph + r, 0), ny - 1);
+        const int gj = min(max(pb.j0 - Q + c, 0), nx - 1);
+        s_L[r * stride + c] = L[(size_t)gi * nx + gj];
+    }
+    __syncthreads();
+
+    // pass 1: rows, kOutPerThread outputs per item
+    constexpr int kSeg = kTileW / kOutPerThread;
+    for (int it = threadIdx.x; it < R * rows * kSeg; it += blockDim.x) {
+        const int t = it / (rows * kSeg), rem = it - t * (rows * kSeg);
+        const int r = rem / kSeg, j0 = (rem - r * kSeg) * kOutPerThread;
+        const float *srow = s_L + r * stride + j0;
+        float lv[kOutPerThread + 2 * Q];
+#pragma unroll
+        for (int m = 0; m < kOutPerThread + 2 * Q; ++m) lv[m] = srow[m];
+        float acc[kOutPerThread];
+#pragma unroll
+        for (int o = 0; o < kOutPerThread; ++o) acc[o] = 0.f;
+#pragma unroll
+        for (int l = 0; l < W; ++l) {
+            const float f = s_r[t * WS + l];
+#pragma unroll
+            for (int o = 0; o < kOutPerThread; ++o) acc[o] = fmaf(f, lv[o + l], acc[o]);
+        }
+        float *h = s_H + ((size_t)t * rows + r) * kTileW + j0;
+#pragma unroll
+        for (int o = 0; o < kOutPerThread; ++o) h[o] = acc[o];
+    }
+    __syncthreads();
+
+    // pass 2: columns, with the output mapping of k_psf
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tr = (warp >> 2) * 16 + (lane >> 1);
+    const int tcol = (warp & 3) * 16 + (lane & 1) * kOutPerThread;
+    const int i = pb.i0 + tr;
+    const int jb = pb.j0 + tcol;
+    bool live = true;
+    if (partial) {
+        bool any = false;
+        if (i < ny)
+            for (int o = 0; o < kOutPerThread; ++o)
+                if (jb + o < nx && weight[S.pix_off + (size_t)i * nx + jb + o] > 0.f) any = true;
+        live = __any_sync(0xffffffffu, any);
+    }
+    float acc[kOutPerThread];
+#pragma unroll
+    for (int o = 0; o < kOutPerThread; ++o) acc[o] = 0.f;
+    for (int t = 0; live && t < R; ++t) {
+        for (int m = 0; m <= 2 * Ph; ++m) {
+            const float c = s_c[t * (2 * Ph + 1) + m];
+            const float4 *h4 = reinterpret_cast<const float4 *>(
+                s_H + ((size_t)t * rows + tr + m) * kTileW + tcol);
+            const float4 a = h4[0], b = h4[1];
+            acc[0] = fmaf(c, a.x, acc[0]);
+            acc[1] = fmaf(c, a.y, acc[1]);
+            acc[2] = fmaf(c, a.z, acc[2]);
+            acc[3] = fmaf(c, a.w, acc[3]);
+            acc[4] = fmaf(c, b.x, acc[4]);
+            acc[5] = fmaf(c, b.y, acc[5]);
+            acc[6] = fmaf(c, b.z, acc[6]);
+            acc[7] = fmaf(c, b.w, acc[7]);
+        }
+    }
+
+    if (partial) {
+        double chi = 0.0;
+        if (live && i < ny) {
+#pragma unroll
+            for (int o = 0; o < kOutPerThread; ++o) {
+                const int j = jb + o;
+                if (j < nx) {
+                    const size_t pix = S.pix_off + (size_t)i * nx + j;
+                    const float w = weight[pix];
+                    if (w > 0.f) {
+                        const float r = data[pix] - acc[o];
+                        chi += (double)(w * r * r);
+                    }
+                }
+            }
+        }
+        __shared__ double s_red[kPsfThreads / 32];
+        chi = warp_sum(chi);
+        if (lane == 0) s_red[warp] = chi;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kPsfThreads / 32; ++w) t += s_red[w];
+            partial[(size_t)p * T_total + pb.tile] = t;
+        }
+    } else if (out && i < ny) {
+#pragma unroll
+        for (int o = 0; o < kOutPerThread; ++o) {
+            const int j = jb + o;
+            if (j < nx) out[(size_t)i * nx + j] = acc[o];
+        }
+    }
+}
+
+// Largest dynamic shared memory of a k_psf_sep instance (P = Q = 15, rank 3).
+static constexpr int kPsfSepSmemMax =
+    ((kTileH + 2 * LENSED_MAX_PSF_HALF) * ((kTileW + 2 * LENSED_MAX_PSF_HALF + 3) & ~3) +
+     3 * (kTileH + 2 * LENSED_MAX_PSF_HALF) * kTileW + 3 * (2 * LENSED_MAX_PSF_HALF + 1) +
+     3 * ((2 * LENSED_MAX_PSF_HALF + 1 + 3) & ~3)) *
+    (int)sizeof(float);
+
 // Largest dynamic shared memory a k_psf instance can ask for (Q = P = 15, FP64).
 static constexpr int kPsfSmemMax =
     ((kTileH + 2 * LENSED_MAX_PSF_HALF) * ((kTileW + 2 * LENSED_MAX_PSF_HALF + 3) & ~3) +
@@ -1067,10 +1224,50 @@ static void psf_attr_all(std::integer_sequence<int, Qs...>)
     (psf_attr_t<T, Qs>(), ...);
 }
 
+template <int... Qs>
+static void psf_sep_attr_all(std::integer_sequence<int, Qs...>)
+{
+    (cudaFuncSetAttribute(k_psf_sep<Qs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          kPsfSepSmemMax),
+     ...);
+}
+
 void init_kernel_attributes()
 {
     psf_attr_all<float>(std::make_integer_sequence<int, LENSED_MAX_PSF_HALF + 1>{});
     psf_attr_all<double>(std::make_integer_sequence<int, LENSED_MAX_PSF_HALF + 1>{});
+    psf_sep_attr_all(std::make_integer_sequence<int, LENSED_MAX_PSF_HALF + 1>{});
+}
+
+// Separable launches: the group's largest p and rank size the shared memory.
+template <int Q>
+static void psf_sep_launch_t(int p_max, int r_max, const SysDev *sys, const float *psf,
+                             const float *data, const float *weight, const unsigned char *valid,
+                             int P, const PsfBlock *blocks, int n_blocks, int p0, int nP,
+                             const float *Lbuf, long long L_stride, double *partial, int T_total,
+                             float *out, cudaStream_t st)
+{
+    const int rows = kTileH + 2 * p_max;
+    const size_t smem = ((size_t)rows * psf_row_stride(Q) + (size_t)r_max * rows * kTileW +
+                         (size_t)r_max * (2 * p_max + 1) + (size_t)r_max * psf_tap_stride(Q)) *
+                        sizeof(float);
+    dim3 grid((unsigned)n_blocks, (unsigned)nP);
+    k_psf_sep<Q><<<grid, kPsfThreads, smem, st>>>(sys, psf, data, weight, valid, P, blocks, p0,
+                                                   Lbuf, L_stride, partial, T_total, out);
+}
+
+template <int... Qs>
+static void psf_sep_dispatch(std::integer_sequence<int, Qs...>, int q, int p_max, int r_max,
+                             const SysDev *sys, const float *psf, const float *data,
+                             const float *weight, const unsigned char *valid, int P,
+                             const PsfBlock *blocks, int n_blocks, int p0, int nP,
+                             const float *Lbuf, long long L_stride, double *partial,
+                             int T_total, float *out, cudaStream_t st)
+{
+    ((q == Qs ? psf_sep_launch_t<Qs>(p_max, r_max, sys, psf, data, weight, valid, P, blocks,
+                                     n_blocks, p0, nP, Lbuf, L_stride, partial, T_total, out, st)
+              : void()),
+     ...);
 }
 
 template <typename T, int Q>
@@ -1121,7 +1318,7 @@ static void psf_dispatch(int q, int p_max, const SysDev *sys, const T *psf, cons
 #undef LENSED_PSF_CASE
 }
 
-void launch_psf(int precision, int q, int p_max, const SysDev *sys, const float *psf_f,
+void launch_psf(int precision, int q, int sep, int p_max, const SysDev *sys, const float *psf_f,
                 const double *psf_d, const float *data, const float *weight,
                 const double *data_d, const double *weight_d,
                 const unsigned char *valid, int P, const PsfBlock *blocks, int n_blocks, int p0,
@@ -1129,7 +1326,11 @@ void launch_psf(int precision, int q, int p_max, const SysDev *sys, const float 
                 float *out, cudaStream_t st)
 {
     if (n_blocks <= 0 || nP <= 0) return;
-    if (precision == LENSED_PREC_FP64)
+    if (sep > 0 && precision != LENSED_PREC_FP64)
+        psf_sep_dispatch(std::make_integer_sequence<int, LENSED_MAX_PSF_HALF + 1>{}, q, p_max,
+                         sep, sys, psf_f, data, weight, valid, P, blocks, n_blocks, p0, nP,
+                         (const float *)Lbuf, L_stride, partial, T_total, out, st);
+    else if (precision == LENSED_PREC_FP64)
         psf_dispatch<double>(q, p_max, sys, psf_d, data_d, weight_d, valid, P, blocks, n_blocks, p0,
                              nP, (const double *)Lbuf, L_stride, partial, T_total, out, st);
     else

@@ -364,6 +364,7 @@ struct DevBuf {
 struct PsfGroup {
     int q, p_max;
     int off, count;  // into the PSF block table
+    int sep;         // largest separable rank in the group (0: direct convolution)
 };
 
 struct TraceGroup {
@@ -386,9 +387,12 @@ struct Candidate {
 };
 
 const Candidate kCandidates[] = {
-    {{128}, "trace blocks of 128 pixels"},
-    {{256}, "trace blocks of 256 pixels"},
-    {{64}, "trace blocks of 64 pixels"},
+    {{128, 0}, "trace blocks of 128 pixels, direct PSF"},
+    {{256, 0}, "trace blocks of 256 pixels, direct PSF"},
+    {{64, 0}, "trace blocks of 64 pixels, direct PSF"},
+    {{128, 1}, "trace blocks of 128 pixels, separable PSF where its rank allows"},
+    {{256, 1}, "trace blocks of 256 pixels, separable PSF where its rank allows"},
+    {{64, 1}, "trace blocks of 64 pixels, separable PSF where its rank allows"},
 };
 constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 
@@ -410,12 +414,16 @@ struct lensed_model {
     std::vector<int> n_nodes;         // per system
     std::vector<int> n_nodes_gauss;   // per system: Gauss nodes per axis (GK), else 0
     std::vector<int> psf_p, psf_q;    // per system
+    std::vector<int> psf_sep;         // per system: separable PSF rank, 0 = direct
     std::vector<int> tiles_all;       // per system: tiles_x * tiles_y
     std::vector<double> ray_flops, ray_transc;  // per system, per ray
 
     // device tables
     DevBuf<SysDev> sys, sys_gauss;
     DevBuf<int> comp_type, comp_plane, comp_free, comp_sys;
+    DevBuf<int> comp_plane_pre;        // planes for the one-off integration of fixed lights
+    DevBuf<float> pre_f;               // precomputed luminosities (FP32 modes)
+    DevBuf<double> pre_d;              // precomputed luminosities (FP64), then its float copy
     DevBuf<double> comp_value;
     DevBuf<float> data, weight;
     DevBuf<double> data_d, weight_d;  // FP64 mode
@@ -467,7 +475,10 @@ struct lensed_model {
 
     LaunchCfg cfg() const { return kCandidates[cfg_index < 0 ? 0 : cfg_index].cfg; }
     size_t elem() const { return precision == LENSED_PREC_FP64 ? sizeof(double) : sizeof(float); }
-    NodeTables nodes() const { return {node_u.p, node_w.p, node_ud.p, node_wd.p}; }
+    NodeTables nodes() const
+    {
+        return {node_u.p, node_w.p, node_ud.p, node_wd.p, pre_f.p, pre_d.p};
+    }
 
     void clear_graphs()
     {
@@ -589,7 +600,7 @@ void enqueue_batch(lensed_model *m, const double *params, int P, double *out, La
         if (tm) tm->end();
         if (tm) tm->begin(2);
         for (const PsfGroup &g : m->psf_groups)
-            launch_psf(m->precision, g.q, g.p_max, m->sys.p, m->psf_f.p, m->psf_d.p, m->data.p,
+            launch_psf(m->precision, g.q, cfg.psf_sep ? g.sep : 0, g.p_max, m->sys.p, m->psf_f.p, m->psf_d.p, m->data.p,
                        m->weight.p, m->data_d.p, m->weight_d.p, m->valid.p, P, m->psf_blocks.p + g.off, g.count, p0, nP,
                        m->Lbuf.p, m->total_pix, m->partial.p, m->T_total, nullptr, st);
         if (tm) tm->end();
@@ -612,6 +623,132 @@ int check_model(const lensed_model *m)
 // C ABI
 
 extern "C" const char *lensed_last_error(void) { return g_last_error.c_str(); }
+
+// Low-rank form of a normalised, flipped PSF F [m][n] (m = 2p+1 rows):
+// singular value decomposition by one-sided Jacobi rotations (Hestenes) in
+// double, then the fewest terms F ~ sum_k c_k r_k^T (c_k = sigma_k u_k,
+// r_k = v_k, at most kMaxSepRank) whose residual sum_ij |F - F_R| stays below
+// 1e-7 (the float rounding of the taps themselves).  Returns the number of
+// terms, 0 if none qualifies or the separable passes would not be cheaper.
+constexpr int kMaxSepRank = 3;
+static int psf_low_rank(const double *F, int m, int n, std::vector<double> &c,
+                        std::vector<double> &r)
+{
+    std::vector<double> U(F, F + (size_t)m * n), V((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j) V[(size_t)j * n + j] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        bool rotated = false;
+        for (int a = 0; a < n - 1; ++a)
+            for (int b = a + 1; b < n; ++b) {
+                double al = 0, be = 0, ga = 0;
+                for (int i = 0; i < m; ++i) {
+                    const double x = U[(size_t)i * n + a], y = U[(size_t)i * n + b];
+                    al += x * x;
+                    be += y * y;
+                    ga += x * y;
+                }
+                if (!(fabs(ga) > 1e-15 * sqrt(al * be))) continue;
+                rotated = true;
+                const double ze = (be - al) / (2 * ga);
+                const double t = (ze >= 0 ? 1.0 : -1.0) / (fabs(ze) + sqrt(1 + ze * ze));
+                const double cs = 1 / sqrt(1 + t * t), sn = cs * t;
+                for (int i = 0; i < m; ++i) {
+                    const double x = U[(size_t)i * n + a], y = U[(size_t)i * n + b];
+                    U[(size_t)i * n + a] = cs * x - sn * y;
+                    U[(size_t)i * n + b] = sn * x + cs * y;
+                }
+                for (int i = 0; i < n; ++i) {
+                    const double x = V[(size_t)i * n + a], y = V[(size_t)i * n + b];
+                    V[(size_t)i * n + a] = cs * x - sn * y;
+                    V[(size_t)i * n + b] = sn * x + cs * y;
+                }
+            }
+        if (!rotated) break;
+    }
+    // columns of U are sigma_j u_j; order by sigma
+    std::vector<int> ord(n);
+    std::vector<double> sig(n);
+    for (int j = 0; j < n; ++j) {
+        double s2 = 0;
+        for (int i = 0; i < m; ++i) s2 += U[(size_t)i * n + j] * U[(size_t)i * n + j];
+        sig[j] = sqrt(s2);
+        ord[j] = j;
+    }
+    std::sort(ord.begin(), ord.end(), [&](int x, int y) { return sig[x] > sig[y]; });
+    const int P = m / 2;
+    const double direct = (double)m * n;
+    for (int R = 1; R <= std::min(kMaxSepRank, n); ++R) {
+        double res = 0;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < n; ++j) {
+                double v = F[(size_t)i * n + j];
+                for (int k = 0; k < R; ++k)
+                    v -= U[(size_t)i * n + ord[k]] * V[(size_t)j * n + ord[k]];
+                res += fabs(v);
+            }
+        if (res > 1e-7) continue;
+        const double cost = R * (n * (kTileH + 2.0 * P) / kTileH + m);
+        if (cost > 0.6 * direct) return 0;
+        c.assign((size_t)R * m, 0.0);
+        r.assign((size_t)R * n, 0.0);
+        for (int k = 0; k < R; ++k) {
+            for (int i = 0; i < m; ++i) c[(size_t)k * m + i] = U[(size_t)i * n + ord[k]];
+            for (int j = 0; j < n; ++j) r[(size_t)k * n + j] = V[(size_t)j * n + ord[k]];
+        }
+        return R;
+    }
+    return 0;
+}
+
+// One-off FP64 pixel integrals of the foreground lights whose parameters are
+// all fixed (device plane kPlanePrecomputed): every evaluation starts each
+// pixel's sum from them instead of tracing those components again.  For a
+// Gauss-Kronrod system the embedded Gauss rule gets a table of its own.
+static int precompute_fixed_light(lensed_model *m, const std::vector<int> &cplane_pre)
+{
+    bool any = false;
+    for (auto &S : m->sys_h) any |= S.pre_off >= 0;
+    if (!any) return LENSED_OK;
+    const long long T = m->total_pix;
+    int rc;
+    DevBuf<double> zeros;
+    if ((rc = m->comp_plane_pre.upload(cplane_pre)) ||
+        (rc = zeros.upload(std::vector<double>(std::max(m->n_par_max, 1), 0.0))) ||
+        (rc = m->pre_d.alloc(2 * T)))
+        return rc;
+    CUDA_OK(cudaMemset(m->pre_d.p, 0, sizeof(double) * 2 * T));
+    // constants of every component at a dummy point (the fixed lights read
+    // no parameter), all systems marked valid for this pass
+    launch_prologue(m->sys.p, m->comp_sys.p, 0, m->n_sys, 0, m->C_total, m->comp_type.p,
+                    m->comp_free.p, m->comp_value.p, zeros.p, true, 1, 0, 1, m->n_par_max,
+                    m->C_total, m->bn_table.p, m->rcf.p, m->rcd.p, m->rcvalid.p, m->rvalid.p, 0);
+    CUDA_OK(cudaMemset(m->rvalid.p, 1, m->n_sys));
+    const NodeTables nodes{m->node_u.p, m->node_w.p, m->node_ud.p, m->node_wd.p, nullptr,
+                           nullptr};
+    const int n_blocks = m->render_trace_off.back() + m->render_trace_cnt.back();
+    for (int g = 0; g < 2; ++g) {
+        if (g == 1 && m->rLg.p == nullptr) break;  // no Gauss-Kronrod system
+        launch_trace(LENSED_PREC_FP64, m->cfg(), 1, g ? m->sys_gauss.p : m->sys.p,
+                     m->comp_type.p, m->comp_plane_pre.p, m->rcf.p, m->rcd.p, m->rvalid.p, 1,
+                     m->C_total, m->render_trace.p, n_blocks, nullptr, nodes, 0, 1,
+                     m->pre_d.p + g * T, 0, 0);
+    }
+    CUDA_OK(cudaGetLastError());
+    CUDA_OK(cudaDeviceSynchronize());
+    std::vector<double> hd(2 * T);
+    CUDA_OK(cudaMemcpy(hd.data(), m->pre_d.p, sizeof(double) * 2 * T, cudaMemcpyDeviceToHost));
+    std::vector<float> hf(hd.begin(), hd.end());
+    if ((rc = m->pre_f.upload(hf))) return rc;
+    // point the systems (and their Gauss shadows) at their tables
+    for (int s = 0; s < m->n_sys; ++s) {
+        if (m->sys_h[s].pre_off < 0) continue;
+        m->sys_h[s].pre_off = m->sys_h[s].pix_off;
+        m->sys_gauss_h[s].pre_off = m->n_nodes_gauss[s] > 0 ? T + m->sys_h[s].pix_off : -1;
+    }
+    if ((rc = m->sys.upload(m->sys_h)) || (rc = m->sys_gauss.upload(m->sys_gauss_h))) return rc;
+    if (m->precision != LENSED_PREC_FP64) m->pre_d.release();
+    return LENSED_OK;
+}
 
 extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_systems,
                                    int precision, lensed_model **out)
@@ -681,8 +818,9 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
 
     // ---- host tables
     std::vector<SysDev> sh(n_systems), shg(n_systems);
+    std::vector<int> sep_v(n_systems, 0);
     std::vector<int> nng_v(n_systems);
-    std::vector<int> ctype, cplane, cfree, csys;
+    std::vector<int> ctype, cplane, cplane_pre, cfree, csys;
     std::vector<double> cval;
     std::vector<float> data, weight, psf_f, node_u, node_w;
     std::vector<double> data_d, weight_d, psf_d, node_ud, node_wd;
@@ -698,6 +836,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         const int nx = d.nx, ny = d.ny, npix = nx * ny;
         SysDev &S = sh[s];
         memset(&S, 0, sizeof(S));
+        S.pre_off = -1;
         S.nx = nx;
         S.ny = ny;
         S.npix = npix;
@@ -771,6 +910,40 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         S.psf_q = Q;
         pp[s] = P;
         qq[s] = Q;
+        // low-rank PSF (FP32 modes): float factors appended to the table, the
+        // first column factor adjusted so that the float terms sum to one
+        S.psf_rank = 0;
+        if (d.psf && precision != LENSED_PREC_FP64) {
+            std::vector<double> cf_, rf_;
+            const int m_ = 2 * P + 1, n_ = 2 * Q + 1;
+            const int R = psf_low_rank(psf_d.data() + (psf_d.size() - (size_t)m_ * n_), m_, n_,
+                                       cf_, rf_);
+            if (R > 0) {
+                S.psf_rank = R;
+                S.psf_sep_off = (int)psf_f.size();
+                std::vector<float> cfl(cf_.begin(), cf_.end()), rfl(rf_.begin(), rf_.end());
+                double tot = 0, s_r0 = 0, s_c0 = 0;
+                for (int k = 0; k < R; ++k) {
+                    double sc = 0, sr = 0;
+                    for (int i = 0; i < m_; ++i) sc += cfl[(size_t)k * m_ + i];
+                    for (int j = 0; j < n_; ++j) sr += rfl[(size_t)k * n_ + j];
+                    tot += sc * sr;
+                    if (k == 0) s_r0 = sr, s_c0 = sc;
+                }
+                int imax = 0;
+                for (int i = 1; i < m_; ++i)
+                    if (fabs(cfl[i]) > fabs(cfl[imax])) imax = i;
+                if (s_r0 != 0.0) cfl[imax] = (float)(cfl[imax] - (tot - 1.0) / s_r0);
+                (void)s_c0;
+                for (int k = 0; k < R; ++k) {
+                    psf_f.insert(psf_f.end(), cfl.begin() + (size_t)k * m_,
+                                 cfl.begin() + (size_t)(k + 1) * m_);
+                    psf_f.insert(psf_f.end(), rfl.begin() + (size_t)k * n_,
+                                 rfl.begin() + (size_t)(k + 1) * n_);
+                }
+                sep_v[s] = R;
+            }
+        }
         // quadrature (Eq. 14): 1-D offsets t*h, 2-D weights W_a W_b; the float
         // weights are adjusted at the largest one so they sum to one in exact
         // arithmetic, leaving no coherent scale error
@@ -854,12 +1027,20 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         for (int c = 0; c < d.n_components; ++c) {
             const lensed_component &cp = d.components[c];
             ctype.push_back(cp.type);
+            const int np = nparams_of(cp.type);
+            // a foreground light with no free parameter is integrated once
+            // per model; the ray kernels skip it
+            bool fixed_fg = cp.plane == LENSED_PLANE_FOREGROUND;
+            for (int k = 0; k < np; ++k) fixed_fg = fixed_fg && cp.free_index[k] < 0;
             // the kernels see an image-plane-prior source as a source; the
             // prologue moves it (bit c of imgpos_mask)
-            cplane.push_back(cp.plane == LENSED_PLANE_SOURCE_IMAGE ? LENSED_PLANE_SOURCE : cp.plane);
+            cplane.push_back(fixed_fg ? kPlanePrecomputed
+                             : cp.plane == LENSED_PLANE_SOURCE_IMAGE ? LENSED_PLANE_SOURCE
+                                                                      : cp.plane);
+            cplane_pre.push_back(fixed_fg ? LENSED_PLANE_FOREGROUND : kPlanePrecomputed);
+            if (fixed_fg) S.pre_off = 0;  // placed below
             if (cp.plane == LENSED_PLANE_SOURCE_IMAGE) S.imgpos_mask |= 1 << c;
             csys.push_back(s);
-            const int np = nparams_of(cp.type);
             for (int k = 0; k < LENSED_MAX_COMPONENT_PARAMS; ++k) {
                 cfree.push_back(k < np ? cp.free_index[k] : -1);
                 cval.push_back(k < np && cp.free_index[k] < 0 ? cp.value[k] : 0.0);
@@ -868,11 +1049,14 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         comp_off += d.n_components;
         {
             double f = 6.0, tr = 0.0;
-            for (int c = 0; c < d.n_components; ++c) component_ops(d.components[c].type, f, tr);
+            for (int c = 0; c < d.n_components; ++c)
+                if (cplane[comp_off - d.n_components + c] != kPlanePrecomputed)
+                    component_ops(d.components[c].type, f, tr);
             ray_flops_v.push_back(f);
             ray_transc_v.push_back(tr);
         }
         S.pix_off = pix_off;
+        if (S.pre_off >= 0) S.pre_off = pix_off;
         pix_off += npix;
         // the embedded Gauss rule of a Gauss-Kronrod system as a system of
         // its own (same image, components and tables, Gauss nodes only) for
@@ -888,6 +1072,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
                 }
             append_rule(tg, wg, shg[s]);
             nng_v[s] = shg[s].nn;
+            if (shg[s].pre_off >= 0) shg[s].pre_off = -2;  // second table, placed after the loop
         }
     }
 
@@ -914,18 +1099,22 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
     // render tiles per system (all tiles)
     m->psf_sys_off.assign(n_systems, 0);
     m->psf_sys_cnt.assign(n_systems, 0);
-    for (int q = 0; q <= LENSED_MAX_PSF_HALF; ++q) {
-        PsfGroup g{q, 0, (int)m->psf_blocks_h.size(), 0};
-        for (int s = 0; s < n_systems; ++s) {
-            if (qq[s] != q || chi_tiles[s].empty()) continue;
-            m->psf_sys_off[s] = (int)m->psf_blocks_h.size();
-            m->psf_sys_cnt[s] = (int)chi_tiles[s].size();
-            m->psf_blocks_h.insert(m->psf_blocks_h.end(), chi_tiles[s].begin(), chi_tiles[s].end());
-            g.p_max = std::max(g.p_max, pp[s]);
+    for (int q = 0; q <= LENSED_MAX_PSF_HALF; ++q)
+        for (int sep = 0; sep <= 1; ++sep) {
+            PsfGroup g{q, 0, (int)m->psf_blocks_h.size(), 0, 0};
+            for (int s = 0; s < n_systems; ++s) {
+                if (qq[s] != q || (sep_v[s] > 0) != (sep == 1) || chi_tiles[s].empty()) continue;
+                m->psf_sys_off[s] = (int)m->psf_blocks_h.size();
+                m->psf_sys_cnt[s] = (int)chi_tiles[s].size();
+                m->psf_blocks_h.insert(m->psf_blocks_h.end(), chi_tiles[s].begin(),
+                                       chi_tiles[s].end());
+                g.p_max = std::max(g.p_max, pp[s]);
+                g.sep = std::max(g.sep, sep_v[s]);
+            }
+            g.count = (int)m->psf_blocks_h.size() - g.off;
+            if (g.count > 0) m->psf_groups.push_back(g);
         }
-        g.count = (int)m->psf_blocks_h.size() - g.off;
-        if (g.count > 0) m->psf_groups.push_back(g);
-    }
+    m->psf_sep = sep_v;
     m->render_psf_off.assign(n_systems, 0);
     m->render_psf_cnt.assign(n_systems, 0);
     for (int s = 0; s < n_systems; ++s) {
@@ -968,6 +1157,12 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
     for (int s = 0; s < n_systems; ++s) any_gk |= systems[s].rule == LENSED_RULE_GK;
     if ((rc = m->rL.alloc(total_pix * m->elem())) ||
         (any_gk && (rc = m->rLg.alloc(total_pix * m->elem())))) {
+        std::string msg = g_last_error;
+        delete m;
+        g_last_error = msg;
+        return rc;
+    }
+    if ((rc = precompute_fixed_light(m, cplane_pre))) {
         std::string msg = g_last_error;
         delete m;
         g_last_error = msg;
@@ -1039,7 +1234,9 @@ extern "C" int lensed_render(lensed_model *m, int system, const double *params, 
         launch_copy_image(m->precision, m->rL.p, S.pix_off, S.npix, m->rvalid.p + system,
                           out_image, st);
     } else {
-        launch_psf(m->precision, m->psf_q[system], m->psf_p[system], m->sys.p, m->psf_f.p,
+        launch_psf(m->precision, m->psf_q[system], m->cfg().psf_sep ? m->psf_sep[system] : 0,
+                   m->psf_p[system],
+                   m->sys.p, m->psf_f.p,
                    m->psf_d.p, m->data.p, m->weight.p, m->data_d.p, m->weight_d.p, m->rvalid.p, 1,
                    m->render_psf.p + m->render_psf_off[system], m->render_psf_cnt[system], 0, 1,
                    m->rL.p, m->total_pix, nullptr, 0, out_image, st);
@@ -1187,7 +1384,9 @@ extern "C" int lensed_loglike_plain(lensed_model *m, const double *params, int P
                              m->cd.p, m->valid.p, P, m->C_total, m->need.p, m->nodes(), p, 1,
                              m->Lbuf.p, m->total_pix, st);
             if (m->psf_sys_cnt[s] > 0)
-                launch_psf(m->precision, m->psf_q[s], m->psf_p[s], m->sys.p, m->psf_f.p,
+                launch_psf(m->precision, m->psf_q[s], cfg.psf_sep ? m->psf_sep[s] : 0, m->psf_p[s],
+                           m->sys.p,
+                           m->psf_f.p,
                            m->psf_d.p, m->data.p, m->weight.p, m->data_d.p, m->weight_d.p, m->valid.p, P,
                            m->psf_blocks.p + m->psf_sys_off[s], m->psf_sys_cnt[s], p, 1,
                            m->Lbuf.p, m->total_pix, m->partial.p, m->T_total, nullptr, st);
@@ -1305,6 +1504,18 @@ extern "C" int lensed_profile_batch(lensed_model *m, const double *params, int P
     return LENSED_OK;
 }
 
+extern "C" int lensed_set_config(lensed_model *m, int index)
+{
+    if (check_model(m)) return LENSED_E_ARG;
+    if (index < -1 || index >= kNumCandidates)
+        return fail(LENSED_E_ARG, "configuration %d out of range (-1..%d)", index,
+                    kNumCandidates - 1);
+    m->cfg_index = index;
+    int rc = build_trace_tables(m, m->cfg().trace_threads);
+    if (rc) return rc;
+    return kNumCandidates;
+}
+
 extern "C" int lensed_tuned_config(const lensed_model *m, char *buf, int buflen)
 {
     if (check_model(m)) return -1;
@@ -1405,7 +1616,7 @@ extern "C" int lensed_loglike_batch_noalloc(lensed_model *m, const double *param
                          valid, P, m->C_total, m->need.p, m->nodes(), p0, nP, Lbuf,
                          m->total_pix, st);
         for (const PsfGroup &g : m->psf_groups)
-            launch_psf(m->precision, g.q, g.p_max, m->sys.p, m->psf_f.p, m->psf_d.p, m->data.p,
+            launch_psf(m->precision, g.q, cfg.psf_sep ? g.sep : 0, g.p_max, m->sys.p, m->psf_f.p, m->psf_d.p, m->data.p,
                        m->weight.p, m->data_d.p, m->weight_d.p, valid, P,
                        m->psf_blocks.p + g.off, g.count, p0, nP, Lbuf, m->total_pix, partial,
                        m->T_total, nullptr, st);

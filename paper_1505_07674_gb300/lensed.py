@@ -222,6 +222,13 @@ class Model:
         names = ("prologue", "trace", "psf_chi2", "finalize")
         return {k: ms[i] for i, k in enumerate(names)}, nt.value, out
 
+    def set_config(self, index):
+        """Pin launch configuration `index` (-1: default); returns how many
+        there are."""
+        n = N.lib().lensed_set_config(self._h, int(index))
+        N.check(min(n, 0))
+        return n
+
     def tuned_config(self):
         buf = C.create_string_buffer(128)
         idx = N.lib().lensed_tuned_config(self._h, buf, 128)

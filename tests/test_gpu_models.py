@@ -95,3 +95,78 @@ def test_image_prior_with_invalid_lens_is_minus_inf():
     xi[4] = 1.2  # main SIE axis ratio outside (0, 1]
     assert np.isneginf(m.loglike_batch(xi[None]).cpu().numpy()[0, 0])
     assert O.OracleSystem(spec, obs).loglike(xi[None])[0] == -np.inf
+
+
+@pytest.mark.parametrize("rule", [("gl", 5), ("gk", 3)])
+@pytest.mark.parametrize("precision", ["fp32", "mixed", "fp64"])
+def test_fixed_foreground_light_integrated_once(rule, precision):
+    # A foreground light with no free parameter is integrated once per model;
+    # the same light given through a free parameter (same value) is traced
+    # with every ray.  Both match the oracle, on images, error maps and
+    # likelihoods.
+    base = W.shrink(W.c2_hst(), 64, 48)
+    base["rule"] = rule
+    fixed_spec = base
+    free_spec = dict(base)
+    comps = [dict(c) for c in base["components"]]
+    k_fg = [i for i, c in enumerate(comps) if c["plane"] == "foreground"][0]
+    params = list(comps[k_fg]["params"])
+    params[3] = free(base["n_params"])  # the magnitude, at its fixed value
+    comps[k_fg] = dict(comps[k_fg], params=params)
+    free_spec["components"] = comps
+    free_spec["n_params"] = base["n_params"] + 1
+    mag = base["components"][k_fg]["params"][3][1]
+    obs = O.mock_observation(fixed_spec)
+    pts = np.vstack([fixed_spec["truth"], W.draw_points(fixed_spec, 31, 51)])
+    pts_free = np.hstack([pts, np.full((len(pts), 1), mag)])
+    osys = O.OracleSystem(fixed_spec, obs)
+    mf = lensed().Model(fixed_spec, obs, precision=precision)
+    mv = lensed().Model(free_spec, obs, precision=precision)
+    ref = osys.loglike(pts)
+    a = mf.loglike_batch(pts).cpu().numpy()[0]
+    b = mv.loglike_batch(pts_free).cpu().numpy()[0]
+    n_unmasked = int((np.asarray(fixed_spec["mask"]) == 0).sum())
+    assert_loglike_close(a, ref, n_unmasked, precision)
+    assert_loglike_close(b, ref, n_unmasked, precision)
+    for xi, xf in zip(pts[:3], pts_free[:3]):
+        o = osys.render(xi, convolved=False)
+        assert_image_close(mf.render(0, xi, convolved=False).cpu().numpy(), o, what="fixed")
+        assert_image_close(mv.render(0, xf, convolved=False).cpu().numpy(), o, what="free")
+        if rule[0] == "gk":
+            e = osys.render_error(xi)
+            tol = 2 * (1e-5 * np.abs(o) + 1e-5 * np.abs(o).max())
+            assert np.all(np.abs(mf.render_error(0, xi).cpu().numpy() - e) <= tol)
+
+
+def _psf_cases():
+    h = 0.05
+    g1 = W.gaussian_psf(15, 0.12, h)
+    g2 = W.gaussian_psf(21, 0.1, h, halo_frac=0.1, halo_fwhm=0.5)
+    r = np.arange(13) - 6
+    xx, yy = np.meshgrid(r, r)
+    ell = np.exp(-(xx * xx / 8.0 + yy * yy / 3.0))                       # separable, rank 1
+    rot = np.exp(-((xx + yy) ** 2 / 10.0 + (xx - yy) ** 2 / 3.0))        # rotated: full rank
+    rnd = np.random.default_rng(9).random((9, 11)) + 0.1                # full rank, asymmetric
+    return {"gauss15": g1, "two_gauss21": g2, "ellipse13": ell, "rotated13": rot, "random9x11": rnd}
+
+
+@pytest.mark.parametrize("name", list(_psf_cases()))
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_low_rank_and_full_psfs(name, precision):
+    # PSFs of numerical rank 1-2 run as separable passes, the others as the
+    # direct convolution; both match the oracle's Eq. 15.
+    spec = W.shrink(W.c2_hst(), 96, 80)
+    spec["psf"] = _psf_cases()[name]
+    obs = O.mock_observation(spec)
+    osys = O.OracleSystem(spec, obs)
+    m = lensed().Model(spec, obs, precision=precision)
+    pts = np.vstack([spec["truth"], W.draw_points(spec, 15, 61)])
+    ref = osys.loglike(pts)
+    n_cfg = m.set_config(0)
+    for idx in range(n_cfg):  # direct and separable PSF configurations
+        m.set_config(idx)
+        for xi in pts[:2]:
+            assert_image_close(m.render(0, xi).cpu().numpy(), osys.render(xi), what=(name, idx))
+        g = m.loglike_batch(pts).cpu().numpy()[0]
+        assert_loglike_close(g, ref, int((np.asarray(spec["mask"]) == 0).sum()), precision)
+        assert np.array_equal(g, m.loglike_plain(pts).cpu().numpy()[0])
