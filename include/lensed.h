@@ -316,7 +316,10 @@ int lensed_profile_batch(lensed_model *m, const double *params, int P, double *o
  * order: W1 [H][n_in], b1 [H], W2 [H][H], b2 [H], W3 [H][H], b3 [H], w4 [H],
  * b4 [1], each W stored [out][in].  Inputs X are row-major [B][n_in] FP32
  * DEVICE arrays (the caller normalises them); targets t and outputs y are
- * [B] FP32 DEVICE arrays.  Errors: status codes, message from
+ * [B] FP32 DEVICE arrays.  The products run on the tensor cores
+ * (tcgen05.mma, accumulators in tensor memory); their waits are bounded, and
+ * an expired wait is reported as LENSED_E_TIMEOUT by the next
+ * lensed_mlp_get_params.  Errors: status codes, message from
  * lensed_mlp_last_error(). */
 typedef struct lensed_mlp lensed_mlp;
 

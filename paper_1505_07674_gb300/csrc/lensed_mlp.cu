@@ -7,11 +7,11 @@
 // exact likelihood judges every accepted point.  The paper has no such
 // component.
 //
-// Every matrix product runs through k_gemm: C[M][N] = A[M][K] B[N][K]^T with
-// BF16 operands staged in shared memory by cp.async (double-buffered, 64 x 64
-// output tile per 128-thread block, 32 x 32 per warp) and multiplied by
-// mma.sync m16n8k16 (FP32 accumulators), with fused epilogues: bias + SiLU
-// (forward), times SiLU'(z) (backward), or plain FP32.  Gradients of the
+// Every matrix product runs through k_gemm_tc: C[M][N] = A[M][K] B[N][K]^T
+// with BF16 operands staged in shared memory by cp.async (double-buffered,
+// 128 x 64 output tile per 128-thread block) and multiplied by tcgen05.mma
+// into an FP32 accumulator in tensor memory, with fused epilogues: bias +
+// SiLU (forward), times SiLU'(z) (backward), or plain FP32.  Gradients of the
 // weights are products over the batch, so the batch-major activations and
 // output gradients are transposed (k_transpose) to make the batch the
 // contraction axis.  Reductions (bias gradients, output layer, loss) run in a
@@ -34,7 +34,6 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int BM = 64, BN = 64, BK = 32, PADK = BK + 8;
 
 thread_local std::string g_mlp_error;
 
@@ -64,15 +63,6 @@ __device__ __forceinline__ float silu_grad(float z)
     return s * (1.f + z * (1.f - s));
 }
 
-__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], const uint32_t b[2])
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 // 16-byte global -> shared copy; src_bytes = 0 fills the destination with
 // zeros (rows beyond M or N).
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes)
@@ -82,114 +72,225 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src
                  "r"(src_bytes));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
 enum { EPI_F32 = 0, EPI_BIAS_SILU = 1, EPI_DSILU = 2 };
 
-// C = A B^T.  A: [M][lda] bf16 (K used), B: [N][ldb] bf16; K % 32 == 0,
-// lda, ldb multiples of 8.  Epilogues:
+// Every product is C = A B^T, A: [M][lda] bf16 (K used), B: [N][ldb] bf16;
+// K % 32 == 0, lda, ldb multiples of 8.  Epilogues:
 //   EPI_F32        Cf[m][n] = acc
 //   EPI_BIAS_SILU  z = acc + bias[n]; Zout[m][n] = z (if Zout); Hout = bf16(silu(z))
 //   EPI_DSILU      d = acc * silu'(Zin[m][n]); Zout[m][n] = d; Hout = bf16(d)
+// ---------------------------------------------------------------------------
+// The product on the 5th-generation tensor cores, with the 128 x 128 FP32
+// accumulator tile in tensor memory.  K is consumed in slices of 64 through a
+// ring of kStages shared-memory buffers: all threads stage a slice of A (128
+// rows) and B (128 rows) by cp.async in the canonical K-major layout without
+// swizzle (core matrices of 8 rows x 16 bytes; the next core matrix along K
+// 128 bytes on, along M/N 1024 bytes on; chunks beyond K or beyond M/N are
+// zero-filled), and one thread issues the slice's four tcgen05.mma (K = 16
+// each) and commits them to the buffer's mbarrier.  A buffer is refilled only
+// after the mbarrier shows that the products reading it have completed, so
+// the copies of the next slices overlap the tensor-core work.  The epilogue
+// reads the accumulators with tcgen05.ld (warp w owns rows 32w..32w+31) into
+// shared memory and applies the fused operation with coalesced row stores.
+// Every wait on an mbarrier is bounded: on expiry the block records the
+// failure in *err, waits (bounded) for its own tensor-core work, frees its
+// tensor memory and returns.
+constexpr int TM = 128, TN = 128, TK = 64, kStages = 3;
+constexpr uint32_t kTmemCols = TN;          // one FP32 column per output column
+constexpr int kSpinLimit = 1 << 24;         // mbarrier polls before giving up
+constexpr int kStageA = TM * TK, kStageB = TN * TK;  // bf16 elements per buffer
+constexpr size_t kGemmSmem = (size_t)kStages * (kStageA + kStageB) * sizeof(bf16);
+static_assert((size_t)TM * (TN + 1) * sizeof(float) <= kGemmSmem, "epilogue tile must fit the ring");
+
+__device__ __forceinline__ uint32_t saddr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = TN, M = TM.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
 template <int EPI>
 __global__ void __launch_bounds__(128)
-    k_gemm(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb, int M, int N,
-           int K, float *__restrict__ Cf, int ldc, const float *__restrict__ bias,
-           const float *__restrict__ Zin, float *__restrict__ Zout, bf16 *__restrict__ Hout)
+    k_gemm_tc(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb, int M,
+              int N, int K, float *__restrict__ Cf, int ldc, const float *__restrict__ bias,
+              const float *__restrict__ Zin, float *__restrict__ Zout, bf16 *__restrict__ Hout,
+              int *__restrict__ err)
 {
-    __shared__ __align__(16) bf16 As[2][BM][PADK];
-    __shared__ __align__(16) bf16 Bs[2][BN][PADK];
+    extern __shared__ __align__(128) unsigned char g_smem[];
+    bf16 *As = reinterpret_cast<bf16 *>(g_smem);
+    bf16 *Bs = As + kStages * kStageA;
+    __shared__ __align__(8) unsigned long long s_bar[kStages];
+    __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int group = lane >> 2, tig = lane & 3;
-    const int wm = warp >> 1, wn = warp & 1;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
 
-    float acc[2][4][4];
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(saddr(&s_tmem)), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < kStages; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&s_bar[b])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
 
-    auto load_tile = [&](int buf, int k0) {
-        // 64 rows x 32 bf16 = 4 chunks of 16 bytes per row; 256 chunks per
-        // operand, two per thread
+    // 16-byte chunk (row r, K chunk j) of a slice -> its core-matrix slot
+    auto load = [&](int stage, int k0) {
+        bf16 *a = As + stage * kStageA, *b = Bs + stage * kStageB;
 #pragma unroll
-        for (int it = 0; it < 2; ++it) {
-            const int ch = tid + it * 128;
-            const int r = ch >> 2, c = (ch & 3) * 8;
-            const int gm = m0 + r, gn = n0 + r;
-            cp_async16(&As[buf][r][c], A + (size_t)min(gm, M - 1) * lda + k0 + c, gm < M ? 16 : 0);
-            cp_async16(&Bs[buf][r][c], B + (size_t)min(gn, N - 1) * ldb + k0 + c, gn < N ? 16 : 0);
+        for (int it = 0; it < (TM * TK / 8) / 128; ++it) {
+            const int ch = tid + it * 128, r = ch >> 3, j = ch & 7;
+            const int gm = m0 + r, gk = k0 + j * 8;
+            const bool in = gm < M && gk < K;
+            cp_async16(a + (r >> 3) * 512 + j * 64 + (r & 7) * 8,
+                       A + (size_t)min(gm, M - 1) * lda + (in ? gk : 0), in ? 16 : 0);
         }
-        cp_async_commit();
+#pragma unroll
+        for (int it = 0; it < (TN * TK / 8) / 128; ++it) {
+            const int ch = tid + it * 128, r = ch >> 3, j = ch & 7;
+            const int gn = n0 + r, gk = k0 + j * 8;
+            const bool in = gn < N && gk < K;
+            cp_async16(b + (r >> 3) * 512 + j * 64 + (r & 7) * 8,
+                       B + (size_t)min(gn, N - 1) * ldb + (in ? gk : 0), in ? 16 : 0);
+        }
     };
 
-    const int nk = K / BK;
-    load_tile(0, 0);
-    for (int kt = 0; kt < nk; ++kt) {
-        const int buf = kt & 1;
-        if (kt + 1 < nk) {
-            load_tile(buf ^ 1, (kt + 1) * BK);
-            cp_async_wait1();
-        } else {
-            cp_async_wait0();
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int r = wm * 32 + mt * 16 + group;
-                af[mt][0] = *reinterpret_cast<const uint32_t *>(&As[buf][r][kk + tig * 2]);
-                af[mt][1] = *reinterpret_cast<const uint32_t *>(&As[buf][r + 8][kk + tig * 2]);
-                af[mt][2] = *reinterpret_cast<const uint32_t *>(&As[buf][r][kk + 8 + tig * 2]);
-                af[mt][3] = *reinterpret_cast<const uint32_t *>(&As[buf][r + 8][kk + 8 + tig * 2]);
-            }
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt) {
-                const int n = wn * 32 + nt * 8 + group;
-                bfr[nt][0] = *reinterpret_cast<const uint32_t *>(&Bs[buf][n][kk + tig * 2]);
-                bfr[nt][1] = *reinterpret_cast<const uint32_t *>(&Bs[buf][n][kk + 8 + tig * 2]);
-            }
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) mma_bf16_16816(acc[mt][nt], af[mt], bfr[nt]);
-        }
-        __syncthreads();
+    const int nk = (K + TK - 1) / TK;
+    bool ok = true;
+    int issued = 0;  // slices whose products were committed
+    for (int s = 0; s < kStages - 1; ++s) {
+        if (s < nk) load(s, s * TK);
+        cp_async_commit();
     }
-
+    for (int kt = 0; kt < nk && ok; ++kt) {
+        const int stage = kt % kStages;
+        asm volatile("cp.async.wait_group %0;" ::"n"(kStages - 2) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = saddr(As + stage * kStageA), b0 = saddr(Bs + stage * kStageB);
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int m = m0 + wm * 32 + mt * 16 + group + h * 8;
-                if (m >= M) continue;
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int n = n0 + wn * 32 + nt * 8 + tig * 2 + e;
-                    if (n >= N) continue;
-                    const float v = acc[mt][nt][h * 2 + e];
-                    const size_t o = (size_t)m * ldc + n;
-                    if (EPI == EPI_F32) {
-                        Cf[o] = v;
-                    } else if (EPI == EPI_BIAS_SILU) {
-                        const float z = v + bias[n];
-                        if (Zout) Zout[o] = z;
-                        Hout[o] = __float2bfloat16(silu(z));
-                    } else {
-                        const float d = v * silu_grad(Zin[o]);
-                        Zout[o] = d;
-                        Hout[o] = __float2bfloat16(d);
-                    }
-                }
+            for (int s = 0; s < TK / 16; ++s) {
+                const uint64_t ad = smem_desc(a0 + s * 256, 128, 1024);
+                const uint64_t bd = smem_desc(b0 + s * 256, 128, 1024);
+                const uint32_t acc = (kt > 0 || s > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                    ::"r"(tmem), "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+                    : "memory");
             }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                ::"r"(saddr(&s_bar[stage])) : "memory");
+        }
+        issued = kt + 1;
+        // refill the buffer of slice kt - 1 with slice kt + kStages - 1 once
+        // the products that read it are done
+        const int next = kt + kStages - 1;
+        if (next < nk) {
+            if (kt >= 1 && !mbar_wait(saddr(&s_bar[(kt - 1) % kStages]),
+                                      (uint32_t)(((kt - 1) / kStages) & 1))) {
+                ok = false;
+                atomicExch(err, 1);
+            }
+            if (ok) load(next % kStages, next * TK);
+        }
+        cp_async_commit();
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // the last slice's commit covers every earlier product
+    const bool done = issued > 0 && mbar_wait(saddr(&s_bar[(issued - 1) % kStages]),
+                                              (uint32_t)(((issued - 1) / kStages) & 1));
+    if (!done || !ok) atomicExch(err, 1);
+    // epilogue: accumulators -> shared memory (the ring is free now), then
+    // coalesced row-wise stores with the fused operation
+    float *stile = reinterpret_cast<float *>(g_smem);  // [TM][TN + 1]
+    if (done && ok) {
+        tc_fence_after();
+#pragma unroll 1
+        for (int c0 = 0; c0 < TN; c0 += 16) {
+            if (n0 + c0 >= N) break;
+            uint32_t v[16];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, "
+                "%9, %10, %11, %12, %13, %14, %15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                  "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                  "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float *dst = stile + (size_t)(warp * 32 + lane) * (TN + 1) + c0;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) dst[e] = __uint_as_float(v[e]);
+        }
+    }
+    __syncthreads();
+    if (done && ok) {
+        const int ncol = min(TN, N - n0);
+        for (int idx = tid; idx < TM * TN; idx += 128) {
+            const int r = idx / TN, c = idx - (idx / TN) * TN;
+            const int row = m0 + r, n = n0 + c;
+            if (row >= M || c >= ncol) continue;
+            const float acc = stile[(size_t)r * (TN + 1) + c];
+            const size_t o = (size_t)row * ldc + n;
+            if (EPI == EPI_F32) {
+                Cf[o] = acc;
+            } else if (EPI == EPI_BIAS_SILU) {
+                const float z = acc + bias[n];
+                if (Zout) Zout[o] = z;
+                Hout[o] = __float2bfloat16(silu(z));
+            } else {
+                const float d = acc * silu_grad(Zin[o]);
+                Zout[o] = d;
+                Hout[o] = __float2bfloat16(d);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols) : "memory");
+    }
 }
 
 // [R][C] bf16 -> [C][R] bf16 (32 x 32 tiles through shared memory)
@@ -356,22 +457,25 @@ struct lensed_mlp {
     Buf<bf16> W1b, W2b, W3b, WT;
     Buf<bf16> Xb, XbT, H1, H2, H3, HT, dZa, dZbuf, dZT;
     Buf<float> Z1, Z2, Z3, dZf, y, dy, lossrow, gW1, tmpcol;
+    Buf<int> err;  // set by a tensor-core wait that expired
 };
 
 namespace {
 
 int launch_gemm(int epi, const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K,
                 float *Cf, int ldc, const float *bias, const float *Zin, float *Zout, bf16 *Hout,
-                cudaStream_t st)
+                int *err, cudaStream_t st)
 {
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
     if (epi == EPI_F32)
-        k_gemm<EPI_F32><<<grid, 128, 0, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc, bias, Zin, Zout, Hout);
+        k_gemm_tc<EPI_F32><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc, bias,
+                                                         Zin, Zout, Hout, err);
     else if (epi == EPI_BIAS_SILU)
-        k_gemm<EPI_BIAS_SILU><<<grid, 128, 0, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc, bias, Zin, Zout,
-                                                   Hout);
+        k_gemm_tc<EPI_BIAS_SILU><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc,
+                                                               bias, Zin, Zout, Hout, err);
     else
-        k_gemm<EPI_DSILU><<<grid, 128, 0, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc, bias, Zin, Zout, Hout);
+        k_gemm_tc<EPI_DSILU><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc, bias,
+                                                           Zin, Zout, Hout, err);
     return LENSED_OK;
 }
 
@@ -388,11 +492,11 @@ void forward(lensed_mlp *m, const float *X, int B, float *y, bool keep_z, cudaSt
     const long long nx = (long long)Bp * m->kin;
     k_pack<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(X, B, m->n_in, Bp, m->kin, m->Xb.p);
     launch_gemm(EPI_BIAS_SILU, m->Xb.p, m->kin, m->W1b.p, m->kin, Bp, H, m->kin, nullptr, H,
-                m->p.p + m->o_b1, nullptr, keep_z ? m->Z1.p : nullptr, m->H1.p, st);
+                m->p.p + m->o_b1, nullptr, keep_z ? m->Z1.p : nullptr, m->H1.p, m->err.p, st);
     launch_gemm(EPI_BIAS_SILU, m->H1.p, H, m->W2b.p, H, Bp, H, H, nullptr, H, m->p.p + m->o_b2,
-                nullptr, keep_z ? m->Z2.p : nullptr, m->H2.p, st);
+                nullptr, keep_z ? m->Z2.p : nullptr, m->H2.p, m->err.p, st);
     launch_gemm(EPI_BIAS_SILU, m->H2.p, H, m->W3b.p, H, Bp, H, H, nullptr, H, m->p.p + m->o_b3,
-                nullptr, keep_z ? m->Z3.p : nullptr, m->H3.p, st);
+                nullptr, keep_z ? m->Z3.p : nullptr, m->H3.p, m->err.p, st);
     k_out<<<(B + 7) / 8, 256, 0, st>>>(m->H3.p, H, m->p.p + m->o_w4, m->p.p + m->o_b4, B, y);
 }
 
@@ -414,25 +518,25 @@ void gradient(lensed_mlp *m, const float *X, const float *t, int B, float *loss,
     transpose(m->dZa.p, Bp, H, m->dZT.p, st);
     transpose(m->H2.p, Bp, H, m->HT.p, st);
     launch_gemm(EPI_F32, m->dZT.p, Bp, m->HT.p, Bp, H, H, Bp, g + m->o_W3, H, nullptr, nullptr,
-                nullptr, nullptr, st);
+                nullptr, nullptr, m->err.p, st);
     k_colsum<<<(H + 127) / 128, 128, 0, st>>>(m->dZf.p, Bp, H, g + m->o_b3);
     transpose(m->W3b.p, H, H, m->WT.p, st);
     launch_gemm(EPI_DSILU, m->dZa.p, H, m->WT.p, H, Bp, H, H, nullptr, H, nullptr, m->Z2.p,
-                m->dZf.p, m->dZbuf.p, st);
+                m->dZf.p, m->dZbuf.p, m->err.p, st);
     // layer 2
     transpose(m->dZbuf.p, Bp, H, m->dZT.p, st);
     transpose(m->H1.p, Bp, H, m->HT.p, st);
     launch_gemm(EPI_F32, m->dZT.p, Bp, m->HT.p, Bp, H, H, Bp, g + m->o_W2, H, nullptr, nullptr,
-                nullptr, nullptr, st);
+                nullptr, nullptr, m->err.p, st);
     k_colsum<<<(H + 127) / 128, 128, 0, st>>>(m->dZf.p, Bp, H, g + m->o_b2);
     transpose(m->W2b.p, H, H, m->WT.p, st);
     launch_gemm(EPI_DSILU, m->dZbuf.p, H, m->WT.p, H, Bp, H, H, nullptr, H, nullptr, m->Z1.p,
-                m->dZf.p, m->dZa.p, st);
+                m->dZf.p, m->dZa.p, m->err.p, st);
     // layer 1: dW1 = dZ1^T X (padded to kin columns), db1
     transpose(m->dZa.p, Bp, H, m->dZT.p, st);
     transpose(m->Xb.p, Bp, m->kin, m->XbT.p, st);
     launch_gemm(EPI_F32, m->dZT.p, Bp, m->XbT.p, Bp, H, m->kin, Bp, m->gW1.p, m->kin, nullptr,
-                nullptr, nullptr, nullptr, st);
+                nullptr, nullptr, nullptr, m->err.p, st);
     k_copy_cols<<<(H * m->n_in + 255) / 256, 256, 0, st>>>(m->gW1.p, H, m->kin, m->n_in, g);
     k_colsum<<<(H + 127) / 128, 128, 0, st>>>(m->dZf.p, Bp, H, g + m->o_b1);
 }
@@ -457,6 +561,12 @@ extern "C" int lensed_mlp_create(int n_in, int hidden, int max_batch, lensed_mlp
     if (n_in < 1 || n_in > 64) return mfail(LENSED_E_ARG, "n_in = %d (1..64)", n_in);
     if (hidden < 64 || hidden % 64) return mfail(LENSED_E_ARG, "hidden = %d (multiple of 64)", hidden);
     if (max_batch < 1) return mfail(LENSED_E_ARG, "max_batch = %d", max_batch);
+    cudaFuncSetAttribute(k_gemm_tc<EPI_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kGemmSmem);
+    cudaFuncSetAttribute(k_gemm_tc<EPI_BIAS_SILU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kGemmSmem);
+    cudaFuncSetAttribute(k_gemm_tc<EPI_DSILU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kGemmSmem);
     lensed_mlp *m = new lensed_mlp();
     m->n_in = n_in;
     m->H = hidden;
@@ -483,13 +593,14 @@ extern "C" int lensed_mlp_create(int n_in, int hidden, int max_batch, lensed_mlp
         (rc = m->dZT.alloc(bh)) || (rc = m->Z1.alloc(bh)) || (rc = m->Z2.alloc(bh)) ||
         (rc = m->Z3.alloc(bh)) || (rc = m->dZf.alloc(bh)) || (rc = m->y.alloc(m->Bp)) ||
         (rc = m->dy.alloc(m->Bp)) || (rc = m->lossrow.alloc(m->Bp)) ||
-        (rc = m->gW1.alloc(H * m->kin)) || (rc = m->tmpcol.alloc(H))) {
+        (rc = m->gW1.alloc(H * m->kin)) || (rc = m->tmpcol.alloc(H)) || (rc = m->err.alloc(1))) {
         std::string msg = g_mlp_error;
         delete m;
         g_mlp_error = msg;
         return rc;
     }
     cudaMemset(m->p.p, 0, m->np * sizeof(float));
+    cudaMemset(m->err.p, 0, sizeof(int));
     cudaMemset(m->m.p, 0, m->np * sizeof(float));
     cudaMemset(m->v.p, 0, m->np * sizeof(float));
     if ((rc = refresh(m, nullptr))) {
@@ -531,6 +642,11 @@ extern "C" int lensed_mlp_get_params(const lensed_mlp *m, float *host_params)
 {
     if (!m || !host_params) return mfail(LENSED_E_ARG, "NULL argument");
     MCUDA(cudaDeviceSynchronize());
+    int err = 0;
+    MCUDA(cudaMemcpy(&err, m->err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err)
+        return mfail(LENSED_E_TIMEOUT, "a tensor-core wait expired in an earlier call; "
+                                       "its results are invalid");
     MCUDA(cudaMemcpy(host_params, m->p.p, m->np * sizeof(float), cudaMemcpyDeviceToHost));
     return LENSED_OK;
 }
