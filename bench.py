@@ -146,9 +146,9 @@ class ClockSampler:
 
 def trace_traffic(points_per_launch):
     """DRAM bytes of one trace launch from the committed ncu record (a
-    512-point capture of the same kernel, scaled by points: its traffic is
-    the per-point luminosity writes and reads, proportional to points), or
-    None when the kernel source changed since that capture."""
+    capture of one full 4,096-point launch of the same kernel; other point
+    counts scale by points), or None when the kernel source changed since
+    that capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_trace_rows_traffic.txt")
     src = os.path.join(ROOT, "paper_1505_07674_gb300", "csrc", "lensed_kernels.cu")
