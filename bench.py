@@ -585,6 +585,9 @@ def main():
             plain_ms = e0.elapsed_time(e1)
             bit_equal = bool(torch.equal(plain_out, out))
 
+    # ---- measured FP32 FMA and MUFU rates of this GPU (roofline context)
+    alu_peaks = LZ.measure_alu_peaks()
+
     # ---- end to end through the host-buffer C call (copies inside)
     host_params = torch.empty(params.shape, dtype=torch.float64).pin_memory()
     host_params.copy_(params.cpu())
@@ -614,6 +617,11 @@ def main():
     trace_ms = stage_ms["trace"] / max(trace_launches, 1)
     flops_launch = npts / max(trace_launches, 1) * rays_traced * m.flops_per_ray
     achieved = flops_launch / (trace_ms * 1e-3) / 1e12
+    mufu_launch = npts / max(trace_launches, 1) * rays_traced * m.transcendentals_per_ray
+    mufu_achieved = mufu_launch / (trace_ms * 1e-3) / 1e12
+    # GB300's special-function units issue 32 ex2 per SM per clock (the probe
+    # below measures 9.96e12/s at 2,070 MHz on 152 SMs)
+    mufu_peak = SMS * 32 * sm_mhz_peak * 1e6 / 1e12
     line = {
         "metric": METRIC,
         "value": evals_s, "unit": "evals/s",
@@ -649,7 +657,14 @@ def main():
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz_peak:.0f} MHz "
                                     f"(sm_max_mhz, {pk_src})",
                      "flops_per_ray": m.flops_per_ray,
-                     "trace_ms_per_launch": trace_ms},
+                     "trace_ms_per_launch": trace_ms,
+                     "fp32_measured_tflops": alu_peaks[0],
+                     "mufu": {"achieved": mufu_achieved, "unit": "Tops/s",
+                              "peak": mufu_peak,
+                              "frac": mufu_achieved / mufu_peak,
+                              "peak_source": f"152 SMs x 32 MUFU ops/clk x {sm_mhz_peak:.0f} MHz",
+                              "measured": alu_peaks[1],
+                              "transcendentals_per_ray": m.transcendentals_per_ray}},
         "clocks": clocks,
         "loglike_finite_frac": float(np.isfinite(ll).mean()),
     }

@@ -286,6 +286,13 @@ int lensed_autotune(lensed_model *m, const double *params, int P, void *stream);
  * reports. */
 int lensed_tuned_config(const lensed_model *m, char *buf, int buflen);
 
+/* Measured FP32 throughput of this GPU for the roofline (the paper has no
+ * counterpart): *fma_tflops = FP32 fused multiply-adds (2 flops each) per
+ * second, *mufu_tops = special-function (ex2) operations per second, both in
+ * units of 1e12, from probes of independent dependency chains over every SM.
+ * Synchronous; allocates a small scratch buffer. */
+int lensed_measure_alu_peaks(double *fma_tflops, double *mufu_tops, void *stream);
+
 /* Use configuration `index` (0 .. n-1 as lensed_tuned_config numbers them,
  * -1 = default) instead of the autotuner's choice; returns the number of
  * configurations n, or LENSED_E_ARG for an index out of range. */

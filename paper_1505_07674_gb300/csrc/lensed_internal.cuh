@@ -156,6 +156,9 @@ void launch_finalize(const SysDev *sys, const unsigned char *valid, int P,
 void launch_copy_image(int precision, const void *Lbuf, long long off, int npix,
                        const unsigned char *valid, float *out, cudaStream_t st);
 
+// Throughput probes (FMA or MUFU ex2 chains) for the measured ALU peaks.
+void launch_probe(int mufu, int blocks, int threads, int iters, float *sink, cudaStream_t st);
+
 // |L_K - L_G| of one system's pixels (the Gauss-Kronrod error estimate),
 // NaN if the point is invalid.
 void launch_error_image(int precision, const void *LK, const void *LG, long long off, int npix,

@@ -1245,6 +1245,44 @@ extern "C" int lensed_render(lensed_model *m, int system, const double *params, 
     return LENSED_OK;
 }
 
+extern "C" int lensed_measure_alu_peaks(double *fma_tflops, double *mufu_tops, void *stream)
+{
+    if (!fma_tflops || !mufu_tops) return fail(LENSED_E_ARG, "NULL output");
+    int dev = 0, sms = 0;
+    CUDA_OK(cudaGetDevice(&dev));
+    CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t st = (cudaStream_t)stream;
+    DevBuf<float> sink;
+    int rc = sink.alloc((size_t)sms * 8);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    CUDA_OK(cudaEventCreate(&e0));
+    CUDA_OK(cudaEventCreate(&e1));
+    const int blocks = sms * 8, threads = 256;
+    const int iters[2] = {1 << 14, 1 << 12};
+    double out[2];
+    for (int mufu = 0; mufu < 2; ++mufu) {
+        float best = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, st);
+            launch_probe(mufu, blocks, threads, iters[mufu], sink.p, st);
+            cudaEventRecord(e1, st);
+            CUDA_OK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) best = std::min(best, ms);  // the first launch warms up
+        }
+        const double ops = (double)blocks * threads * iters[mufu] * 8;
+        out[mufu] = ops * (mufu ? 1.0 : 2.0) / (best * 1e-3) / 1e12;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_OK(cudaGetLastError());
+    *fma_tflops = out[0];
+    *mufu_tops = out[1];
+    return LENSED_OK;
+}
+
 extern "C" int lensed_rule_nodes(int rule, int order, double *t, double *w, double *w_gauss)
 {
     if (!t || !w) return fail(LENSED_E_ARG, "t/w is NULL");

@@ -247,3 +247,10 @@ def rule_nodes(rule, order):
     N.check(min(n, 0))
     return t[:n].copy(), w[:n].copy(), wg[:n].copy()
 
+
+
+def measure_alu_peaks(stream=None):
+    """(FP32 FMA TFLOP/s, MUFU ex2 Tops/s) measured on the current GPU."""
+    a, b = C.c_double(), C.c_double()
+    N.check(N.lib().lensed_measure_alu_peaks(C.byref(a), C.byref(b), _stream_handle(stream)))
+    return a.value, b.value
