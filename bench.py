@@ -183,10 +183,43 @@ def cpu_baseline(spec, samples_points=96, seed=77):
     t0 = time.perf_counter()
     ref = osys.loglike(pts, nthreads=cores)
     dt = time.perf_counter() - t0
+    # one core, on the first few points of the same sample
+    n1 = max(2, samples_points // 16)
+    t1 = time.perf_counter()
+    osys.loglike(pts[:n1], nthreads=1)
+    dt1 = time.perf_counter() - t1
     out = {"value": samples_points / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
            "sample": f"{samples_points} of the workload's points (same image, mask, PSF, rule), "
-                     f"FP64 C oracle with OpenMP over points, {dt:.1f} s wall"}
+                     f"FP64 C oracle with OpenMP over points, {dt:.1f} s wall",
+           "single_core": {"value": n1 / dt1, "unit": "evals/s", "cores": 1,
+                           "sample": f"the first {n1} points of that sample"}}
     return out, obs, pts, ref
+
+
+def cpu_baseline_batch(specs, n_sys=8, n_pts=4, seed=78):
+    """Oracle timing on a seeded subsample of a multi-system workload (the
+    first n_sys systems, n_pts points each), all cores and one core."""
+    from oracle import oracle as O
+    import workloads as W
+
+    cores = os.cpu_count() or 1
+    systems = []
+    for spec in specs[:n_sys]:
+        obs = O.mock_observation(spec)
+        systems.append((O.OracleSystem(spec, obs), W.draw_points(spec, n_pts, seed)))
+    t0 = time.perf_counter()
+    for osys, pts in systems:
+        osys.loglike(pts, nthreads=cores)
+    dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    for osys, pts in systems[:max(1, n_sys // 4)]:
+        osys.loglike(pts, nthreads=1)
+    dt1 = time.perf_counter() - t1
+    n_all, n_one = len(systems) * n_pts, max(1, n_sys // 4) * n_pts
+    return {"value": n_all / dt, "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_pts} points of each of the first {len(systems)} systems, {dt:.1f} s wall",
+            "single_core": {"value": n_one / dt1, "unit": "evals/s", "cores": 1,
+                            "sample": f"the first {max(1, n_sys // 4)} of those systems"}}
 
 
 def run_reference(args):
@@ -677,6 +710,8 @@ def main():
         cb["max_abs_dlogl_gpu_vs_oracle"] = float(np.abs(g[ok] - ref[ok]).max())
         cb["max_rel_dlogl_gpu_vs_oracle"] = float((np.abs(g[ok] - ref[ok]) / np.abs(ref[ok])).max())
         line["cpu_baseline"] = cb
+    elif not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_batch(specs)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
