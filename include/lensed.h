@@ -112,8 +112,16 @@ enum { LENSED_RULE_POINT = 0, LENSED_RULE_SUB = 1, LENSED_RULE_GL = 2, LENSED_RU
  *   LENSED_PREC_MIXED  as FP32, but the SIE deflection is evaluated in FP64
  *                      for axis ratios close to 1 (e = sqrt(1-q^2) < 0.05)
  *                      and for rays within 2 s / q of the SIE centre
- *   LENSED_PREC_FP64   everything in FP64 (validation mode)              */
-enum { LENSED_PREC_FP32 = 0, LENSED_PREC_MIXED = 1, LENSED_PREC_FP64 = 2 };
+ *   LENSED_PREC_FP64   everything in FP64 (validation mode)
+ *   LENSED_PREC_MIXED_FF  as MIXED, and every ray whose FP32 source-plane
+ *                      position falls within one effective radius of a
+ *                      Sersic-type source (R < r) is re-traced with the lens
+ *                      equation in float-float arithmetic (~48 bits): the
+ *                      float grid of traced positions otherwise limits the
+ *                      log-likelihood to ~1e-2 absolute on steep, compact
+ *                      sources; this mode reaches ~1e-3 at 1.5-3x the cost */
+enum { LENSED_PREC_FP32 = 0, LENSED_PREC_MIXED = 1, LENSED_PREC_FP64 = 2,
+       LENSED_PREC_MIXED_FF = 3 };
 
 enum { LENSED_RENDER_UNCONVOLVED = 0, LENSED_RENDER_CONVOLVED = 1 };
 

@@ -18,7 +18,7 @@ STATUS = {0: "LENSED_OK", -1: "LENSED_E_ARG", -2: "LENSED_E_NOMEM", -3: "LENSED_
 SIE, SHEAR, POINTMASS, SERSIC, DEVAUC, GAUSS, SKY = 1, 2, 3, 4, 5, 6, 7
 PLANE_LENS, PLANE_FOREGROUND, PLANE_SOURCE, PLANE_SOURCE_IMAGE = 0, 1, 2, 3
 RULE_POINT, RULE_SUB, RULE_GL, RULE_GK = 0, 1, 2, 3
-PREC_FP32, PREC_MIXED, PREC_FP64 = 0, 1, 2
+PREC_FP32, PREC_MIXED, PREC_FP64, PREC_MIXED_FF = 0, 1, 2, 3
 RENDER_UNCONVOLVED, RENDER_CONVOLVED = 0, 1
 MAX_COMPONENT_PARAMS = 8
 MAX_RULE_ORDER = 16

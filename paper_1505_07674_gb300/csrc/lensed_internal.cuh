@@ -88,6 +88,7 @@ struct NodeTables {
     const double *ud, *wd;
     const float *pre_f;
     const double *pre_d;
+    int ff;  // LENSED_PREC_MIXED_FF: re-trace rays near source centres in float-float
 };
 
 // PSF-kernel block table entry: system and tile origin.

@@ -512,6 +512,8 @@ void launch_prologue(const SysDev *sys, const int *comp_sys, int s0, int nS, int
 struct TraceSmem {
     float cf[LENSED_MAX_COMPONENTS * kNC];
     double cd[LENSED_MAX_COMPONENTS * kNC];
+    float ch[LENSED_MAX_COMPONENTS * kNC], cl[LENSED_MAX_COMPONENTS * kNC];  // cd as float pairs
+    float uh[LENSED_MAX_RULE_ORDER], ul[LENSED_MAX_RULE_ORDER];            // ud as float pairs
     int type[LENSED_MAX_COMPONENTS], plane[LENSED_MAX_COMPONENTS];
     float u[LENSED_MAX_RULE_ORDER];
     double ud[LENSED_MAX_RULE_ORDER];
@@ -527,7 +529,12 @@ __device__ __forceinline__ void stage_point(TraceSmem &sm, const SysDev &S, cons
     const int ncomp = S.ncomp, nn = S.nn;
     for (int k = threadIdx.x; k < ncomp * kNC; k += blockDim.x) {
         sm.cf[k] = cf[cbase + k];
-        if (need_f64) sm.cd[k] = cd[cbase + k];
+        if (need_f64) {
+            const double v = cd[cbase + k];
+            sm.cd[k] = v;
+            sm.ch[k] = (float)v;
+            sm.cl[k] = (float)(v - (double)(float)v);
+        }
     }
     for (int k = threadIdx.x; k < ncomp; k += blockDim.x) {
         sm.type[k] = comp_type[S.comp_off + k];
@@ -535,13 +542,220 @@ __device__ __forceinline__ void stage_point(TraceSmem &sm, const SysDev &S, cons
     }
     for (int k = threadIdx.x; k < nn; k += blockDim.x) {
         sm.u[k] = nodes.u[S.node_off + k];
-        sm.ud[k] = nodes.ud[S.node_off + k];
+        const double v = nodes.ud[S.node_off + k];
+        sm.ud[k] = v;
+        sm.uh[k] = (float)v;
+        sm.ul[k] = (float)(v - (double)(float)v);
     }
     for (int k = threadIdx.x; k < nn * nn; k += blockDim.x) {
         if (w_f64) sm.wd[k] = nodes.wd[S.w2_off + k];
         else sm.w[k] = nodes.w[S.w2_off + k];
     }
 }
+
+// ---- float-float lens equation for the rays MIXED re-traces near the centre
+// of a source profile.  There the brightness is steep on the scale of the
+// float grid of the traced position (~1e-7 arcsec near the Einstein radius),
+// so the MIXED rule gives every ray that the FP32 pass sees inside one
+// effective radius of a Sersic-type source (R < r) a source-plane position in
+// float-float arithmetic (a value carried as an unevaluated sum hi + lo of
+// two floats, ~48 bits; Dekker 1971, Knuth's two-sum): the ray position, the
+// deflection of every lens component and y = x - alpha.  The light is then
+// evaluated in FP32 at that position.  FP64 would do the same at 1/64 of the
+// FP32 rate on this GPU.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_quick(float a, float b)  // |a| >= |b|
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_two_sum(float a, float b)
+{
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y)
+{
+    const ff s = ff_two_sum(x.hi, y.hi);
+    return ff_quick(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ ff ff_sub(ff x, ff y) { return ff_add(x, ff_neg(y)); }
+__device__ __forceinline__ ff ff_mul(ff x, ff y)
+{
+    const float p = x.hi * y.hi;
+    const float e = fmaf(x.hi, y.hi, -p);
+    return ff_quick(p, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e)));
+}
+__device__ __forceinline__ ff ff_mulf(ff x, float f)
+{
+    const float p = x.hi * f;
+    const float e = fmaf(x.hi, f, -p);
+    return ff_quick(p, fmaf(x.lo, f, e));
+}
+__device__ __forceinline__ ff ff_addf(ff x, float f) { return ff_add(x, ff{f, 0.f}); }
+// x / y for y != 0: three quotient digits, each from the exact remainder
+__device__ __forceinline__ ff ff_div(ff x, ff y)
+{
+    const float r = 1.f / y.hi;
+    const float q1 = x.hi * r;
+    ff rem = ff_sub(x, ff_mulf(y, q1));
+    const float q2 = rem.hi * r;
+    rem = ff_sub(rem, ff_mulf(y, q2));
+    const float q3 = rem.hi * r;
+    return ff_addf(ff_quick(q1, q2), q3);
+}
+// sqrt(x) for x >= 0: float root, then one correction from the exact residual
+__device__ __forceinline__ ff ff_sqrt(ff x)
+{
+    if (!(x.hi > 0.f)) return {0.f, 0.f};
+    const float s = sqrtf(x.hi);
+    const float p = s * s;
+    const ff sq{p, fmaf(s, s, -p)};
+    const ff d = ff_sub(x, sq);
+    return ff_quick(s, d.hi / (2.f * s));
+}
+
+// tan(k/16), k = 0..26, and tanh(k/16), k = 0..127, as float pairs (computed
+// by the runtime in long double): reduction points for atan and atanh.
+__constant__ float kTan16[27][2];
+__constant__ float kTanh16[128][2];
+
+// atan(t) = k/16 + atan(w), w = (t - tan(k/16)) / (1 + t tan(k/16)), k the
+// nearest multiple of 1/16 to atan(t), so |w| <= tan(1/32) and the series
+// w - w^3/3 + w^5/5 - w^7/7 leaves < 1e-13; its tail after w is applied in
+// float.  Odd in t.
+__device__ __forceinline__ ff ff_atan(ff t)
+{
+    const bool neg = t.hi < 0.f;
+    if (neg) t = ff_neg(t);
+    const int k = min(max(__float2int_rn(16.f * atanf(t.hi)), 0), 26);
+    const ff c{kTan16[k][0], kTan16[k][1]};
+    const ff w = ff_div(ff_sub(t, c), ff_addf(ff_mul(t, c), 1.f));
+    const float s = w.hi * w.hi;
+    const float tail = w.hi * s * fmaf(s, fmaf(s, -1.f / 7.f, 0.2f), -1.f / 3.f);
+    ff r = ff_addf(ff_add(ff{k * 0.0625f, 0.f}, w), tail);
+    return neg ? ff_neg(r) : r;
+}
+
+// atanh(z), |z| < 1: the same reduction with tanh(k/16) and
+// w = (z - tanh(k/16)) / (1 - z tanh(k/16)); series w + w^3/3 + w^5/5 + w^7/7.
+__device__ __forceinline__ ff ff_atanh(ff z)
+{
+    const bool neg = z.hi < 0.f;
+    if (neg) z = ff_neg(z);
+    const int k = min(max(__float2int_rn(16.f * atanhf(fminf(z.hi, 0.99999994f))), 0), 127);
+    const ff c{kTanh16[k][0], kTanh16[k][1]};
+    const ff w = ff_div(ff_sub(z, c), ff_add(ff{1.f, 0.f}, ff_neg(ff_mul(z, c))));
+    const float s = w.hi * w.hi;
+    const float tail = w.hi * s * fmaf(s, fmaf(s, 1.f / 7.f, 0.2f), 1.f / 3.f);
+    ff r = ff_addf(ff_add(ff{k * 0.0625f, 0.f}, w), tail);
+    return neg ? ff_neg(r) : r;
+}
+
+__device__ __forceinline__ ff ff_const(const TraceSmem &sm, int idx) { return {sm.ch[idx], sm.cl[idx]}; }
+
+// FP32 light profile at a given offset (dx, dy) from its centre.
+__device__ __forceinline__ float light_f32_at(const LightF &k, float dx, float dy)
+{
+    const float u = fmaf(dx, k.cs, fmaf(dy, k.sn, fmaf(dx, k.csl, dy * k.snl)));
+    const float v = fmaf(dy, k.cs, fmaf(-dx, k.sn, fmaf(dy, k.csl, -dx * k.snl)));
+    const float uu = u * u, vv = v * v;
+    const float rho2 = fmaf(k.qr, uu, fmaf(k.iqr, vv, fmaf(k.qrl, uu, k.iqrl * vv)));
+    const float f = (k.kind == (float)kKindGauss) ? rho2 : ex2f(k.p2 * lg2f(rho2));
+    const float t = fmaf(k.B, f, k.Bl * f);
+    const float g = ex2f(-t);
+    return fmaf(k.A, g, k.Al * g);
+}
+
+// Source-plane brightness of ray (a, b) of pixel (jc, ic) with the lens
+// equation in float-float (all lens components), the light in FP32.
+__device__ __noinline__ float source_brightness_ff(const TraceSmem &sm, int ncomp, float jc,
+                                                   float ic, float h, float h_lo, int a, int b)
+{
+    // ray position: (j - cx) h + t_a h, with h and the node offset as float pairs
+    ff x = ff_add(ff_add(ff{jc * h, fmaf(jc, h, -(jc * h))}, ff{jc * h_lo, 0.f}),
+                  ff{sm.uh[a], sm.ul[a]});
+    ff y = ff_add(ff_add(ff{ic * h, fmaf(ic, h, -(ic * h))}, ff{ic * h_lo, 0.f}),
+                  ff{sm.uh[b], sm.ul[b]});
+    ff ax{0.f, 0.f}, ay{0.f, 0.f};
+    for (int c = 0; c < ncomp; ++c) {
+        if (sm.plane[c] != LENSED_PLANE_LENS) continue;
+        const int o = c * kNC, t = sm.type[c];
+        const ff dx = ff_sub(x, ff_const(sm, o + 0)), dy = ff_sub(y, ff_const(sm, o + 1));
+        if (t == LENSED_SIE) {
+            const ff cs = ff_const(sm, o + 2), sn = ff_const(sm, o + 3);
+            const ff u = ff_add(ff_mul(dx, cs), ff_mul(dy, sn));
+            const ff v = ff_sub(ff_mul(dy, cs), ff_mul(dx, sn));
+            const ff psi = ff_sqrt(ff_add(ff_mul(ff_const(sm, o + 6),
+                                                 ff_add(ff_const(sm, o + 8), ff_mul(u, u))),
+                                          ff_mul(v, v)));
+            const ff du = ff_add(psi, ff_const(sm, o + 9));
+            const ff dv = ff_add(psi, ff_const(sm, o + 10));
+            if (!(du.hi > 0.f)) continue;  // exact centre of a coreless SIE
+            ff A1, A2;
+            if (sm.cd[o + 15] != 0.0) {
+                const ff zu = ff_div(u, du), zv = ff_div(v, dv);
+                const float e2 = sm.ch[o + 16];
+                const float su = e2 * zu.hi * zu.hi, sv = e2 * zv.hi * zv.hi;
+                A1 = ff_addf(zu, zu.hi * su * fmaf(su, 0.2f, -1.f / 3.f));
+                A2 = ff_addf(zv, zv.hi * sv * fmaf(sv, 0.2f, 1.f / 3.f));
+            } else {
+                const ff e = ff_const(sm, o + 11);
+                A1 = ff_atan(ff_div(ff_mul(e, u), du));
+                A2 = ff_atanh(ff_div(ff_mul(e, v), dv));
+            }
+            const ff pref = ff_const(sm, o + 13);
+            const ff au = ff_mul(pref, A1), av = ff_mul(pref, A2);
+            ax = ff_add(ax, ff_sub(ff_mul(au, cs), ff_mul(av, sn)));
+            ay = ff_add(ay, ff_add(ff_mul(au, sn), ff_mul(av, cs)));
+        } else if (t == LENSED_SHEAR) {
+            const ff g1 = ff_const(sm, o + 2), g2 = ff_const(sm, o + 3);
+            ax = ff_add(ax, ff_add(ff_mul(g1, dx), ff_mul(g2, dy)));
+            ay = ff_add(ay, ff_sub(ff_mul(g2, dx), ff_mul(g1, dy)));
+        } else {
+            const ff r2 = ff_add(ff_mul(dx, dx), ff_mul(dy, dy));
+            if (!(r2.hi > 0.f)) continue;
+            const ff f = ff_div(ff_const(sm, o + 2), r2);
+            ax = ff_add(ax, ff_mul(f, dx));
+            ay = ff_add(ay, ff_mul(f, dy));
+        }
+    }
+    const ff sx = ff_sub(x, ax), sy = ff_sub(y, ay);
+    float I = 0.f;
+    for (int c = 0; c < ncomp; ++c) {
+        if (sm.plane[c] != LENSED_PLANE_SOURCE) continue;
+        const int o = c * kNC;
+        const LightF L = load_light(sm.cf + o);
+        if (L.kind == (float)kKindFlat) {
+            I += L.A;
+            continue;
+        }
+        const ff ox = ff_sub(sx, ff_const(sm, o + 0)), oy = ff_sub(sy, ff_const(sm, o + 1));
+        I += light_f32_at(L, ox.hi + ox.lo, oy.hi + oy.lo);
+    }
+    return I;
+}
+
+// FP32 light of a source, also reporting (R / r)^2 of the ray.
+__device__ __forceinline__ float light_f32_rho(const LightF &k, float x, float y, float &rho2)
+{
+    const float dx = x - k.x0, dy = y - k.y0;
+    const float u = fmaf(dx, k.cs, fmaf(dy, k.sn, fmaf(dx, k.csl, dy * k.snl)));
+    const float v = fmaf(dy, k.cs, fmaf(-dx, k.sn, fmaf(dy, k.csl, -dx * k.snl)));
+    const float uu = u * u, vv = v * v;
+    rho2 = fmaf(k.qr, uu, fmaf(k.iqr, vv, fmaf(k.qrl, uu, k.iqrl * vv)));
+    const float f = (k.kind == (float)kKindGauss) ? rho2 : ex2f(k.p2 * lg2f(rho2));
+    const float t = fmaf(k.B, f, k.Bl * f);
+    const float g = ex2f(-t);
+    return fmaf(k.A, g, k.Al * g);
+}
+
+constexpr float kCuspRho2 = 1.f;  // MIXED re-traces rays with (R / r)^2 below this
+constexpr int kQCap = 2048;       // deferred float-float rays per trace block
 
 // a2-a5 in FP32 (also the first pass of MIXED): one thread per pixel; for
 // every row of the rule's node grid, G rays are traced together component by
@@ -562,15 +776,26 @@ __global__ void __launch_bounds__(256)
     if (!valid[(size_t)tb.sys * P + p]) return;
     const SysDev &S = sys[tb.sys];
     const size_t cbase = ((size_t)p * C_total + S.comp_off) * kNC;
-    stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, false, false, nodes);
+    // MIXED with at most 8 nodes per row defers its float-float re-traces to a
+    // block-wide queue (64-bit ray mask per pixel), processed by all lanes
+    // after the main loop; the others re-trace in place
+    constexpr bool kQueue = (MODE == LENSED_PREC_MIXED_FF) && EXACT;
+    __shared__ int q_n;
+    __shared__ unsigned short q_t[kQueue ? kQCap : 1];
+    __shared__ unsigned char q_r[kQueue ? kQCap : 1];
+    __shared__ float q_v[kQueue ? kQCap : 1];
+    stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, MODE == LENSED_PREC_MIXED_FF, false,
+                nodes);
+    if (kQueue && threadIdx.x == 0) q_n = 0;
     __syncthreads();
 
     const int idx = tb.start + threadIdx.x;
-    if (idx >= tb.end) return;
+    const bool active = idx < tb.end;
+    if (!kQueue && !active) return;
     const int ncomp = S.ncomp;
     const int nn = EXACT ? G : S.nn;
     const int nx = S.nx;
-    const int pix = need ? need[S.need_off + idx] : idx;
+    const int pix = active ? (need ? need[S.need_off + idx] : idx) : 0;
     const int i = pix / nx, j = pix - (pix / nx) * nx;
     // pixel centre (j - cx) h with h as a float pair: one rounding, no
     // coherent scale error
@@ -578,8 +803,9 @@ __global__ void __launch_bounds__(256)
     const float xc = fmaf(jc, S.h, jc * S.h_lo);
     const float yc = fmaf(ic, S.h, ic * S.h_lo);
 
-    float acc = (nodes.pre_f && S.pre_off >= 0) ? nodes.pre_f[S.pre_off + pix] : 0.f;
-    for (int b = 0; b < nn; ++b) {
+    float acc = (nodes.pre_f && S.pre_off >= 0 && active) ? nodes.pre_f[S.pre_off + pix] : 0.f;
+    unsigned long long mask = 0ull;  // rays deferred to the queue
+    for (int b = 0; active && b < nn; ++b) {
         const float y = yc + sm.u[b];
         for (int a0 = 0; a0 < nn; a0 += G) {
             float xk[G], ax[G], ay[G], I[G];
@@ -630,15 +856,43 @@ __global__ void __launch_bounds__(256)
                     }
                 }
             }
+            float Ifg[G];
+            bool near[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                Ifg[k] = I[k];
+                near[k] = false;
+            }
             for (int c = 0; c < ncomp; ++c) {
                 if (sm.plane[c] != LENSED_PLANE_SOURCE) continue;
                 const LightF L = load_light(sm.cf + c * kNC);
                 if (L.kind == (float)kKindFlat) {
 #pragma unroll
                     for (int k = 0; k < G; ++k) I[k] += L.A;
+                } else if (MODE == LENSED_PREC_MIXED_FF && L.kind == (float)kKindPower) {
+#pragma unroll
+                    for (int k = 0; k < G; ++k) {
+                        float r2;
+                        I[k] += light_f32_rho(L, xk[k] - ax[k], y - ay[k], r2);
+                        near[k] = near[k] || r2 < kCuspRho2;
+                    }
                 } else {
 #pragma unroll
                     for (int k = 0; k < G; ++k) I[k] += light_f32(L, xk[k] - ax[k], y - ay[k]);
+                }
+            }
+            if (MODE == LENSED_PREC_MIXED_FF) {
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    if (!near[k] || !(EXACT || a0 + k < nn)) continue;
+                    if (kQueue) {
+                        // the source part comes from the queue; keep the rest
+                        mask |= 1ull << (b * nn + k);
+                        I[k] = Ifg[k];
+                    } else {
+                        I[k] = Ifg[k] + source_brightness_ff(sm, ncomp, jc, ic, S.h, S.h_lo,
+                                                             a0 + k, b);
+                    }
                 }
             }
 #pragma unroll
@@ -646,7 +900,43 @@ __global__ void __launch_bounds__(256)
                 if (EXACT || a0 + k < nn) acc = fmaf(sm.w[b * nn + a0 + k], I[k], acc);
         }
     }
-    Lbuf[(size_t)(p - p0) * L_stride + S.pix_off + pix] = acc;
+    if (kQueue) {
+        // each pixel's deferred rays take consecutive slots in ray order
+        const int n_t = __popcll(mask);
+        const int base = n_t ? atomicAdd(&q_n, n_t) : 0;
+        const bool fits = base + n_t <= kQCap;
+        if (fits) {
+            unsigned long long m = mask;
+            for (int e = 0; m; ++e) {
+                const int r = __ffsll((long long)m) - 1;
+                m &= m - 1ull;
+                q_t[base + e] = (unsigned short)threadIdx.x;
+                q_r[base + e] = (unsigned char)r;
+            }
+        }
+        __syncthreads();
+        const int nq = min(q_n, kQCap);
+        for (int e = threadIdx.x; e < nq; e += blockDim.x) {
+            const int t = q_t[e], r = q_r[e];
+            const int pt = need ? need[S.need_off + tb.start + t] : tb.start + t;
+            const int it = pt / nx, jt = pt - (pt / nx) * nx;
+            q_v[e] = source_brightness_ff(sm, ncomp, (float)jt - S.cx, (float)it - S.cy, S.h,
+                                          S.h_lo, r % nn, r / nn);
+        }
+        __syncthreads();
+        if (active && n_t) {
+            unsigned long long m = mask;
+            for (int e = 0; m; ++e) {
+                const int r = __ffsll((long long)m) - 1;
+                m &= m - 1ull;
+                const float v = fits ? q_v[base + e]
+                                     : source_brightness_ff(sm, ncomp, jc, ic, S.h, S.h_lo,
+                                                            r % nn, r / nn);
+                acc = fmaf(sm.w[r], v, acc);
+            }
+        }
+    }
+    if (active) Lbuf[(size_t)(p - p0) * L_stride + S.pix_off + pix] = acc;
 }
 
 // a2-a5 in FP64 (validation mode): plain per-ray loop.
@@ -731,6 +1021,11 @@ void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const
         k_trace_f64<<<grid, cfg.trace_threads, 0, st>>>(sys, comp_type, comp_plane, cf, cd,
                                                          valid, P, C_total, blocks, need, nodes,
                                                          p0, (double *)Lbuf, L_stride);
+    } else if (precision == LENSED_PREC_MIXED_FF) {
+        trace_rows_dispatch<LENSED_PREC_MIXED_FF>(nn, cfg.trace_threads, sys, comp_type,
+                                                  comp_plane, cf, cd, valid, P, C_total, blocks,
+                                                  n_blocks, need, nodes, p0, nP, Lbuf, L_stride,
+                                                  st);
     } else {
         trace_rows_dispatch<LENSED_PREC_FP32>(nn, cfg.trace_threads, sys, comp_type, comp_plane,
                                               cf, cd, valid, P, C_total, blocks, n_blocks, need,
@@ -748,7 +1043,8 @@ void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const
 // the fixed node order.
 
 // Brightness of ray (a, b) of pixel (i, j) under the MIXED rule.
-__device__ float ray_mixed(const TraceSmem &sm, const SysDev &S, int i, int j, int a, int b)
+__device__ float ray_mixed(const TraceSmem &sm, const SysDev &S, int i, int j, int a, int b,
+                          bool ff)
 {
     const int ncomp = S.ncomp;
     const float jc = (float)j - S.cx, ic = (float)i - S.cy;
@@ -785,9 +1081,20 @@ __device__ float ray_mixed(const TraceSmem &sm, const SysDev &S, int i, int j, i
             }
         }
     }
-    for (int c = 0; c < ncomp; ++c)
-        if (sm.plane[c] == LENSED_PLANE_SOURCE)
-            I += light_any_f32(load_light(sm.cf + c * kNC), x - ax, y - ay);
+    const float Ifg = I;
+    bool near = false;
+    for (int c = 0; c < ncomp; ++c) {
+        if (sm.plane[c] != LENSED_PLANE_SOURCE) continue;
+        const LightF L = load_light(sm.cf + c * kNC);
+        if (ff && L.kind == (float)kKindPower) {
+            float r2;
+            I += light_f32_rho(L, x - ax, y - ay, r2);
+            near = near || r2 < kCuspRho2;
+        } else {
+            I += light_any_f32(L, x - ax, y - ay);
+        }
+    }
+    if (near) I = Ifg + source_brightness_ff(sm, ncomp, jc, ic, S.h, S.h_lo, a, b);
     return I;
 }
 
@@ -805,7 +1112,7 @@ constexpr int kFixRays = 1024;  // ray contributions staged per batch
 
 // Recompute the pixels of s_pix[0..n) (batches of kFixRays / (nn*nn)).
 __device__ void fix_pixels(const TraceSmem &sm, const SysDev &S, const int *s_pix, int n,
-                           float *s_ray, float *L, const float *pre)
+                           float *s_ray, float *L, const float *pre, bool ff)
 {
     const int nn = S.nn, nr = nn * nn, nx = S.nx;
     const int per = kFixRays / nr;
@@ -814,7 +1121,7 @@ __device__ void fix_pixels(const TraceSmem &sm, const SysDev &S, const int *s_pi
         for (int t = threadIdx.x; t < m * nr; t += blockDim.x) {
             const int pix = s_pix[b0 + t / nr], r = t % nr;
             const int i = pix / nx, j = pix - (pix / nx) * nx;
-            s_ray[t] = ray_mixed(sm, S, i, j, r % nn, r / nn);
+            s_ray[t] = ray_mixed(sm, S, i, j, r % nn, r / nn, ff);
         }
         __syncthreads();
         for (int k = threadIdx.x; k < m; k += blockDim.x) {
@@ -858,7 +1165,7 @@ __global__ void __launch_bounds__(128)
             for (int k = threadIdx.x; k < m; k += blockDim.x)
                 s_pix[k] = need ? need[S.need_off + q0 + k] : q0 + k;
             __syncthreads();
-            fix_pixels(sm, S, s_pix, m, s_ray, L, pre);
+            fix_pixels(sm, S, s_pix, m, s_ray, L, pre, nodes.ff != 0);
         }
         return;
     }
@@ -892,7 +1199,7 @@ __global__ void __launch_bounds__(128)
             __syncthreads();
             const int n = s_n;
             __syncthreads();
-            fix_pixels(sm, S, s_pix, n, s_ray, L, pre);
+            fix_pixels(sm, S, s_pix, n, s_ray, L, pre, nodes.ff != 0);
         }
     }
 }
@@ -1232,8 +1539,27 @@ static void psf_sep_attr_all(std::integer_sequence<int, Qs...>)
      ...);
 }
 
+// Reduction tables of the float-float atan / atanh (long double on the host).
+static void init_ff_tables()
+{
+    float t[27][2], th[128][2];
+    for (int k = 0; k < 27; ++k) {
+        const long double v = tanl(k / 16.0L);
+        t[k][0] = (float)v;
+        t[k][1] = (float)(v - (long double)t[k][0]);
+    }
+    for (int k = 0; k < 128; ++k) {
+        const long double v = tanhl(k / 16.0L);
+        th[k][0] = (float)v;
+        th[k][1] = (float)(v - (long double)th[k][0]);
+    }
+    cudaMemcpyToSymbol(kTan16, t, sizeof(t));
+    cudaMemcpyToSymbol(kTanh16, th, sizeof(th));
+}
+
 void init_kernel_attributes()
 {
+    init_ff_tables();
     psf_attr_all<float>(std::make_integer_sequence<int, LENSED_MAX_PSF_HALF + 1>{});
     psf_attr_all<double>(std::make_integer_sequence<int, LENSED_MAX_PSF_HALF + 1>{});
     psf_sep_attr_all(std::make_integer_sequence<int, LENSED_MAX_PSF_HALF + 1>{});

@@ -65,6 +65,12 @@ int fail(int code, const char *fmt, ...)
 //   Gaussian light: translate 2, rotate 6, R^2 5, scale 1, negate+exp2 2,
 //        amplitude 1, accumulate 1 -> 18, 1
 //   per ray: position 2, lens equation 2, weight product + accumulate 2 -> 6
+// MIXED and MIXED_FF both run the FP64 SIE fix-up pass.
+bool is_mixed(int precision)
+{
+    return precision == LENSED_PREC_MIXED || precision == LENSED_PREC_MIXED_FF;
+}
+
 void component_ops(int type, double &flops, double &transc)
 {
     switch (type) {
@@ -477,7 +483,8 @@ struct lensed_model {
     size_t elem() const { return precision == LENSED_PREC_FP64 ? sizeof(double) : sizeof(float); }
     NodeTables nodes() const
     {
-        return {node_u.p, node_w.p, node_ud.p, node_wd.p, pre_f.p, pre_d.p};
+        return {node_u.p, node_w.p, node_ud.p, node_wd.p, pre_f.p, pre_d.p,
+                precision == LENSED_PREC_MIXED_FF ? 1 : 0};
     }
 
     void clear_graphs()
@@ -593,7 +600,7 @@ void enqueue_batch(lensed_model *m, const double *params, int P, double *out, La
             launch_trace(m->precision, cfg, g.nn, m->sys.p, m->comp_type.p, m->comp_plane.p,
                          m->cf.p, m->cd.p, m->valid.p, P, m->C_total, m->trace_blocks.p + g.off,
                          g.count, m->need.p, m->nodes(), p0, nP, m->Lbuf.p, m->total_pix, st);
-        if (m->precision == LENSED_PREC_MIXED)
+        if (is_mixed(m->precision))
             launch_fix64(cfg, m->sys.p, 0, m->n_sys, m->comp_type.p, m->comp_plane.p, m->cf.p,
                          m->cd.p, m->valid.p, P, m->C_total, m->need.p, m->nodes(), p0, nP,
                          m->Lbuf.p, m->total_pix, st);
@@ -724,7 +731,7 @@ static int precompute_fixed_light(lensed_model *m, const std::vector<int> &cplan
                     m->C_total, m->bn_table.p, m->rcf.p, m->rcd.p, m->rcvalid.p, m->rvalid.p, 0);
     CUDA_OK(cudaMemset(m->rvalid.p, 1, m->n_sys));
     const NodeTables nodes{m->node_u.p, m->node_w.p, m->node_ud.p, m->node_wd.p, nullptr,
-                           nullptr};
+                           nullptr, 0};
     const int n_blocks = m->render_trace_off.back() + m->render_trace_cnt.back();
     for (int g = 0; g < 2; ++g) {
         if (g == 1 && m->rLg.p == nullptr) break;  // no Gauss-Kronrod system
@@ -756,7 +763,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
     g_last_error.clear();
     if (!out) return fail(LENSED_E_ARG, "out is NULL");
     if (!systems || n_systems < 1) return fail(LENSED_E_ARG, "need at least one system");
-    if (precision < LENSED_PREC_FP32 || precision > LENSED_PREC_FP64)
+    if (precision < LENSED_PREC_FP32 || precision > LENSED_PREC_MIXED_FF)
         return fail(LENSED_E_ARG, "unknown precision %d", precision);
 
     // ---- validate every descriptor before touching the device
@@ -1226,7 +1233,7 @@ extern "C" int lensed_render(lensed_model *m, int system, const double *params, 
                  m->rcd.p, m->rvalid.p, 1, m->C_total,
                  m->render_trace.p + m->render_trace_off[system], m->render_trace_cnt[system],
                  nullptr, m->nodes(), 0, 1, m->rL.p, m->total_pix, st);
-    if (m->precision == LENSED_PREC_MIXED)
+    if (is_mixed(m->precision))
         launch_fix64(m->cfg(), m->sys.p, system, 1, m->comp_type.p, m->comp_plane.p, m->rcf.p,
                      m->rcd.p, m->rvalid.p, 1, m->C_total, nullptr, m->nodes(), 0, 1, m->rL.p,
                      m->total_pix, st);
@@ -1322,7 +1329,7 @@ extern "C" int lensed_render_error(lensed_model *m, int system, const double *pa
                      m->rcd.p, m->rvalid.p, 1, m->C_total,
                      m->render_trace.p + m->render_trace_off[system], m->render_trace_cnt[system],
                      nullptr, m->nodes(), 0, 1, L, m->total_pix, st);
-        if (m->precision == LENSED_PREC_MIXED)
+        if (is_mixed(m->precision))
             launch_fix64(m->cfg(), sys, system, 1, m->comp_type.p, m->comp_plane.p, m->rcf.p,
                          m->rcd.p, m->rvalid.p, 1, m->C_total, nullptr, m->nodes(), 0, 1, L,
                          m->total_pix, st);
@@ -1417,7 +1424,7 @@ extern "C" int lensed_loglike_plain(lensed_model *m, const double *params, int P
                          m->cd.p, m->valid.p, P, m->C_total,
                          m->trace_blocks.p + m->trace_sys_off[s], m->trace_sys_cnt[s], m->need.p,
                          m->nodes(), p, 1, m->Lbuf.p, m->total_pix, st);
-            if (m->precision == LENSED_PREC_MIXED)
+            if (is_mixed(m->precision))
                 launch_fix64(cfg, m->sys.p, s, 1, m->comp_type.p, m->comp_plane.p, m->cf.p,
                              m->cd.p, m->valid.p, P, m->C_total, m->need.p, m->nodes(), p, 1,
                              m->Lbuf.p, m->total_pix, st);
@@ -1509,7 +1516,7 @@ extern "C" int lensed_batch_plan(lensed_model *m, int P, int *launches, int *chu
     if (rc) return rc;
     const int chunks = (P + m->chunk_P - 1) / m->chunk_P;
     *launches = 3 + chunks * ((int)m->trace_groups.size() + (int)m->psf_groups.size() +
-                              (m->precision == LENSED_PREC_MIXED ? 1 : 0));
+                              (is_mixed(m->precision) ? 1 : 0));
     *chunk_points = m->chunk_P;
     return LENSED_OK;
 }
@@ -1649,7 +1656,7 @@ extern "C" int lensed_loglike_batch_noalloc(lensed_model *m, const double *param
             launch_trace(m->precision, cfg, g.nn, m->sys.p, m->comp_type.p, m->comp_plane.p, cf,
                          cd, valid, P, m->C_total, m->trace_blocks.p + g.off, g.count, m->need.p,
                          m->nodes(), p0, nP, Lbuf, m->total_pix, st);
-        if (m->precision == LENSED_PREC_MIXED)
+        if (is_mixed(m->precision))
             launch_fix64(cfg, m->sys.p, 0, m->n_sys, m->comp_type.p, m->comp_plane.p, cf, cd,
                          valid, P, m->C_total, m->need.p, m->nodes(), p0, nP, Lbuf,
                          m->total_pix, st);

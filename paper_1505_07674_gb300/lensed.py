@@ -20,7 +20,8 @@ _TYPES = {"sie": N.SIE, "shear": N.SHEAR, "pointmass": N.POINTMASS, "sersic": N.
 _PLANES = {"lens": N.PLANE_LENS, "foreground": N.PLANE_FOREGROUND, "source": N.PLANE_SOURCE,
            "source_image": N.PLANE_SOURCE_IMAGE}
 _RULES = {"point": N.RULE_POINT, "sub": N.RULE_SUB, "gl": N.RULE_GL, "gk": N.RULE_GK}
-_PREC = {"fp32": N.PREC_FP32, "mixed": N.PREC_MIXED, "fp64": N.PREC_FP64}
+_PREC = {"fp32": N.PREC_FP32, "mixed": N.PREC_MIXED, "fp64": N.PREC_FP64,
+         "mixed_ff": N.PREC_MIXED_FF}
 
 
 def _stream_handle(stream):
