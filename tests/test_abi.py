@@ -60,6 +60,36 @@ int main(void){
     assert [int(x) for x in out] == got
 
 
+def test_enum_values_match_header():
+    # every constant the binding passes through the ABI, against the header's
+    import subprocess
+    import tempfile
+    names = {"LENSED_SIE": N.SIE, "LENSED_SHEAR": N.SHEAR, "LENSED_POINTMASS": N.POINTMASS,
+             "LENSED_SERSIC": N.SERSIC, "LENSED_DEVAUC": N.DEVAUC, "LENSED_GAUSS": N.GAUSS,
+             "LENSED_SKY": N.SKY, "LENSED_PLANE_LENS": N.PLANE_LENS,
+             "LENSED_PLANE_FOREGROUND": N.PLANE_FOREGROUND,
+             "LENSED_PLANE_SOURCE": N.PLANE_SOURCE,
+             "LENSED_PLANE_SOURCE_IMAGE": N.PLANE_SOURCE_IMAGE,
+             "LENSED_RULE_POINT": N.RULE_POINT, "LENSED_RULE_SUB": N.RULE_SUB,
+             "LENSED_RULE_GL": N.RULE_GL, "LENSED_RULE_GK": N.RULE_GK,
+             "LENSED_PREC_FP32": N.PREC_FP32, "LENSED_PREC_MIXED": N.PREC_MIXED,
+             "LENSED_PREC_FP64": N.PREC_FP64, "LENSED_PREC_MIXED_FF": N.PREC_MIXED_FF,
+             "LENSED_RENDER_UNCONVOLVED": N.RENDER_UNCONVOLVED,
+             "LENSED_RENDER_CONVOLVED": N.RENDER_CONVOLVED,
+             "LENSED_MAX_COMPONENT_PARAMS": N.MAX_COMPONENT_PARAMS,
+             "LENSED_MAX_RULE_ORDER": N.MAX_RULE_ORDER,
+             "LENSED_MAX_KRONROD_ORDER": N.MAX_KRONROD_ORDER}
+    src = '#include <stdio.h>\n#include "lensed.h"\nint main(void){\n'
+    src += "".join(f' printf("%d\\n", (int)({k}));\n' for k in names) + " return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "enums.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "enums")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    assert [int(x) for x in out] == list(names.values())
+
+
 def _desc(nx=8, ny=8, psf=(3, 3), comps=None, n_params=2, data=None, variance=True, gain=0.0):
     keep = []
     d = N.SystemDesc()
