@@ -147,20 +147,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_code_digest(path):
+    """sha256 of a CUDA source without its whole-line comments and trailing
+    blanks: a change of code invalidates a recorded profile, a change of
+    comments does not."""
+    import hashlib
+    lines = []
+    for line in open(path, encoding="utf-8"):
+        t = line.rstrip()
+        if t.lstrip().startswith("//") or not t:
+            continue
+        lines.append(t)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def trace_traffic(points_per_launch):
     """DRAM bytes of one trace launch from the committed ncu record (a
     capture of one full 4,096-point launch of the same kernel; other point
     counts scale by points), or None when the kernel source changed since
     that capture."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", "k_trace_rows_traffic.txt")
     src = os.path.join(ROOT, "paper_1505_07674_gb300", "csrc", "lensed_kernels.cu")
     try:
         rec = json.load(open(path))
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        digest = kernel_code_digest(src)
     except (OSError, ValueError):
         return None
-    if rec.get("source_sha256") != digest:
+    if rec.get("code_sha256") != digest:
         return None
     return rec["dram_bytes_per_point"] * points_per_launch
 

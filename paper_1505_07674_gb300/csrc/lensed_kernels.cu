@@ -1,20 +1,33 @@
 // Device kernels of the ray-tracing likelihood (sm_103a).
 //
-//   k_prologue  a1: per (system, point): resolve the free/fixed parameters,
-//               check the domain, precompute per-component constants
-//               (Sersic b_n by Newton on the incomplete gamma function, I_0
-//               from the magnitude, PA cosines, SIE prefactors) in FP64 and
-//               store FP32 and FP64 copies.
-//   k_trace     a2-a5: one thread per needed pixel; for every ray of the
+//   k_prologue_comp / k_prologue_valid
+//               a1: per (point, component): resolve the free/fixed
+//               parameters, check the domain, precompute the constants
+//               (Sersic b_n from a Chebyshev table in log n with a Newton
+//               fallback on the incomplete gamma function, I_0 from the
+//               magnitude, PA cosines, SIE prefactors) in FP64 with FP32
+//               copies; per (system, point): validity, and the image-plane
+//               priors (a source moved to theta - alpha(theta)).
+//   k_trace_rows
+//               a2-a5: one thread per needed pixel; for every ray of the
 //               quadrature rule: ray position (Eq. 14), deflection (Eq. 1),
 //               brightness at image and traced position (Eq. 2), weighted
-//               sum into the pixel luminosity (Eq. 3), all in registers.
-//   k_psf       a6-a7: a 64 x 32 output tile per block staged in shared
+//               sum into the pixel luminosity (Eq. 3), in registers, starting
+//               from the once-per-model integral of the fixed lights.
+//               MIXED_FF re-traces the rays near a source centre in
+//               float-float through a block-wide queue.
+//   k_trace_fix64, k_trace_f64
+//               MIXED: the pixels the FP64 SIE rule reaches; FP64 mode.
+//   k_psf, k_psf_sep
+//               a6-a7: a 64 x 32 output tile per block staged in shared
 //               memory with its clamped halo (Eq. 15), 8 outputs per thread
 //               with the PSF row and the image row segment held in
-//               registers; then the masked chi^2 of the tile (Eq. 17) as a
-//               warp-shuffle tree in FP64, or the convolved image.
+//               registers (or, for a PSF of rank <= 3, a row pass and a
+//               column pass per separable term); then the masked chi^2 of the
+//               tile (Eq. 17) as a warp-shuffle tree in FP64, or the image.
 //   k_finalize  a7: loglike = -1/2 sum of the tile partials, fixed order.
+//   k_error_image
+//               the Gauss-Kronrod error estimate |L_K - L_G| of a render.
 #include <math.h>
 
 #include <utility>
