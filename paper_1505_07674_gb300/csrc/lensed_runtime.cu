@@ -1,8 +1,10 @@
 // Host runtime of the ray-tracing likelihood: the C ABI of include/lensed.h.
 //
 // lensed_create_model validates the systems, prepares the per-pixel data,
-// weights and the normalised PSF (Sec. 3.1-3.3), the quadrature tables
-// (Eq. 14) and the work lists, and copies them to the device.  The
+// weights and the normalised PSF (Sec. 3.1-3.3; low-rank PSFs also as
+// separable factors), the quadrature tables (Eq. 14; Gauss-Legendre and
+// Gauss-Kronrod nodes computed here) and the work lists, copies them to the
+// device, and integrates the lights that no parameter moves once.  The
 // evaluation calls schedule the kernels of lensed_kernels.cu:
 //
 //   batched:  prologue(all points) -> for each point chunk: trace, psf ->
