@@ -46,6 +46,7 @@ WORKLOADS = {
     "c5": ("euclid_400x400_h0.1_18par_surrogate_prescreen_65536", 0),
     "j0808": ("j0808like_160x160_h0.05_2sie_sky_5sersic_imageprior_psf15_g3k7_1024pts_35par", 1024),
     "rules": ("rule_comparison_120x120_sie_devauc_sersic_18par_point_sub2_sub4_g3k7_g5k11_g7k15", 0),
+    "mlp": ("surrogate_mlp_18_256_256_256_1_silu_bf16_forward_65536_train_8192", 0),
 }
 # image, rule and PSF of the throughput workloads (for the JSON config)
 SHAPES = {
@@ -78,7 +79,8 @@ def parse():
                     help="c2 (default, the benchmark), c1 or c3 (other configurations), "
                          "c4 (posterior run), c5 (surrogate pre-screen vs plain), j0808 "
                          "(35-parameter multi-component model with sky and image-plane prior), "
-                         "rules (integration-rule comparison: posterior errors per rule)")
+                         "rules (integration-rule comparison: posterior errors per rule), "
+                         "mlp (surrogate network throughput on the tensor cores)")
     ap.add_argument("--mocks", type=int, default=12, help="mock systems (rules)")
     ap.add_argument("--rules-live", type=int, default=400, help="live points (rules)")
     ap.add_argument("--rules-noiseless", action="store_true",
@@ -344,6 +346,75 @@ def run_posterior(args):
     return 0
 
 
+def run_mlp(args):
+    """mlp: the surrogate network alone -- forward passes over 65,536
+    proposals (one pre-screen batch) and Adam steps on 8,192 pairs, timed
+    with CUDA events, L2 flushed between steps; roofline against the measured
+    BF16 tensor peak."""
+    import torch
+
+    from paper_1505_07674_gb300 import build as build_lib
+    from paper_1505_07674_gb300.surrogate import Surrogate
+
+    torch.cuda.set_device(0)
+    build_lib()
+    n_in, H, B, Bt = 18, 256, 65536, 8192
+    net = Surrogate(n_in, H, B)
+    rng = np.random.default_rng(3)
+    theta = np.zeros(net.n_params, dtype=np.float32)
+    o = 0
+    for rows, cols in ((H, n_in), (H, H), (H, H)):
+        theta[o:o + rows * cols] = rng.standard_normal(rows * cols) * np.sqrt(2.0 / cols)
+        o += rows * cols + rows
+    theta[o:o + H] = rng.standard_normal(H) * np.sqrt(1.0 / H)
+    net.set_params(theta)
+    X = torch.rand((B, n_in), device="cuda")
+    y = torch.empty(B, device="cuda")
+    Xt, t = torch.rand((Bt, n_in), device="cuda"), torch.rand(Bt, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        net.forward(X, out=y)
+        net.train_step(Xt, t, 1e-4)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    fwd, trn = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        net.forward(X, out=y)
+        e1.record()
+        net.train_step(Xt, t, 1e-4)
+        e2.record()
+        fwd.append((e0, e1))
+        trn.append((e1, e2))
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    f_ms = sum(a.elapsed_time(b) for a, b in fwd) / args.steps
+    t_ms = sum(a.elapsed_time(b) for a, b in trn) / args.steps
+    kin = 32  # layer 1's K, padded to the 32-element slice
+    f_flops = 2.0 * B * (kin * H + 2 * H * H)
+    pk, pk_src = peaks()
+    peak = float(pk.get("bf16_tflops", 1900.0))
+    line = {"metric": "surrogate forward proposals/s (one pre-screen batch of 65,536) and "
+                      "Adam step time (8,192 pairs)",
+            "value": B / (f_ms * 1e-3), "unit": "proposals/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": f_ms,
+            "higher_is_better": True, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+            "config": {"workload": WORKLOADS["mlp"][0], "l2": "flushed between steps"},
+            "train_step_ms": t_ms,
+            "roofline": {"bound": "tensor", "achieved": f_flops / (f_ms * 1e-3) / 1e12,
+                         "peak": peak, "unit": "TFLOP/s",
+                         "frac": f_flops / (f_ms * 1e-3) / 1e12 / peak,
+                         "peak_source": f"bf16_tflops ({pk_src})",
+                         "kernel": "k_gemm_tc (tcgen05.mma, TMEM accumulators)"},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 RULE_SET = (("point", 1), ("sub", 2), ("sub", 4), ("gk", 3), ("gk", 5), ("gk", 7))
 RULE_NAMES = ("point", "sub2", "sub4", "g3k7", "g5k11", "g7k15")
 
@@ -528,6 +599,8 @@ def main():
         return run_surrogate(args)
     if args.workload == "rules":
         return run_rules(args)
+    if args.workload == "mlp":
+        return run_mlp(args)
 
     import torch
 
