@@ -1,0 +1,32 @@
+"""Host-side pieces of the benchmark: the code digest that keys recorded
+profiles ignores comments but not code, and the recorded trace traffic is
+reported only for the kernel source it was captured on."""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_code_digest_ignores_comments_only(tmp_path):
+    a = tmp_path / "a.cu"
+    a.write_text("// header\nint f() { return 1; }\n\n   // note\nint g();\n")
+    b = tmp_path / "b.cu"
+    b.write_text("// another header\nint f() { return 1; }\nint g();   \n")
+    c = tmp_path / "c.cu"
+    c.write_text("int f() { return 2; }\nint g();\n")
+    assert bench.kernel_code_digest(a) == bench.kernel_code_digest(b)
+    assert bench.kernel_code_digest(a) != bench.kernel_code_digest(c)
+
+
+def test_recorded_traffic_matches_current_kernel_code():
+    rec = json.load(open(os.path.join(ROOT, "profiles", "k_trace_rows_traffic.txt")))
+    src = os.path.join(ROOT, "paper_1505_07674_gb300", "csrc", "lensed_kernels.cu")
+    assert rec["code_sha256"] == bench.kernel_code_digest(src)
+    full = bench.trace_traffic(rec["points"])
+    assert abs(full - rec["dram_bytes"]) <= 1e-6 * rec["dram_bytes"]
+    assert abs(bench.trace_traffic(512) - rec["dram_bytes_per_point"] * 512) < 1.0
