@@ -40,3 +40,38 @@ def test_j0808_like_has_35_free_parameters_and_the_paper_components():
         assert used == list(range(35))
         lo, hi = np.array(s["prior_lo"]), np.array(s["prior_hi"])
         assert np.all((np.array(s["truth"]) >= lo) & (np.array(s["truth"]) <= hi))
+
+
+def test_uneven_batch_follows_its_recipe():
+    specs = W.c3_batch(256)
+    assert len(specs) == 256
+    sizes, orders, psfs, pms = set(), set(), set(), 0
+    for s in specs:
+        assert 48 <= s["nx"] <= 320 and 48 <= s["ny"] <= 320
+        kind, order = s["rule"]
+        assert kind == "gl" and 3 <= order <= 7
+        n = s["psf"].shape[0]
+        assert s["psf"].shape == (n, n) and n % 2 == 1 and 7 <= n <= 31
+        types = [c["type"] for c in s["components"]]
+        assert types[:2] == ["sie", "shear"] and types[-1] == "sersic"
+        pms += "pointmass" in types
+        assert s["n_params"] in (13, 16)
+        lo, hi = np.array(s["prior_lo"]), np.array(s["prior_hi"])
+        assert np.all((np.array(s["truth"]) >= lo) & (np.array(s["truth"]) <= hi))
+        sizes.add((s["nx"], s["ny"])); orders.add(order); psfs.add(n)
+    # the batch is uneven in every respect it is meant to be
+    assert len(sizes) > 200 and orders == {3, 4, 5, 6, 7} and len(psfs) >= 10
+    assert 80 < pms < 176  # a point mass with probability 1/2
+
+
+def test_benchmark_workload_matches_its_description():
+    s = W.c2_hst()
+    assert (s["nx"], s["ny"], s["h"]) == (200, 200, 0.05) and s["rule"] == ("gl", 5)
+    assert s["psf"].shape == (21, 21) and s["n_params"] == 11
+    m = np.asarray(s["mask"])
+    x = (np.arange(200) - 99.5) * 0.05
+    r = np.hypot(*np.meshgrid(x, x))
+    assert np.array_equal(m == 0, (r >= 0.5) & (r <= 3.0))
+    t = dict(zip(s["param_names"], s["truth"]))
+    assert (t["b_L"], t["q_L"], t["pa_L"]) == (1.3624, 0.75, 45.0)
+    assert math.hypot(t["x_S"], t["y_S"]) <= 0.5 * 1.3624
