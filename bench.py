@@ -516,7 +516,7 @@ def run_surrogate(args):
     trained once on the (parameters, logL) pairs of an earlier run (at most
     2M).  In both the network is the first stage of delayed-acceptance walk
     steps: proposals it rejects skip the exact evaluation; the exact
-    likelihood judges every accepted point."""
+    likelihood decides every accepted point."""
     import torch
 
     import workloads as W

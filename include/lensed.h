@@ -323,7 +323,7 @@ int lensed_profile_batch(lensed_model *m, const double *params, int P, double *o
 /* ------------------------------------------------------------------------
  * Log-likelihood surrogate network (the paper has no counterpart; the
  * sampling driver uses it to pre-screen proposals, and the exact likelihood
- * judges every point it accepts):
+ * decides every point it accepts):
  *     h1 = silu(x W1^T + b1), h2 = silu(h1 W2^T + b2), h3 = silu(h2 W3^T + b3),
  *     y  = h3 . w4 + b4,   loss = mean over the batch of (y - t)^2 / 2.
  * BF16 weights and activations on the tensor cores, FP32 accumulation, FP32

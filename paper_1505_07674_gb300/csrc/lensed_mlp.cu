@@ -4,7 +4,7 @@
 //   y = h3 . w4 + b4;  loss = mean((y - t)^2) / 2.
 //
 // The likelihood driver uses it to pre-screen nested-sampling proposals; the
-// exact likelihood judges every accepted point.  The paper has no such
+// exact likelihood decides every accepted point.  The paper has no such
 // component.
 //
 // Every matrix product runs through k_gemm_tc: C[M][N] = A[M][K] B[N][K]^T

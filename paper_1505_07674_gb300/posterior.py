@@ -17,7 +17,7 @@ y = log(1 + L_ref - logL) (L_ref the best logL in the training data), which
 spreads the region near the top of the likelihood and compresses the far
 tails; a candidate is kept when its prediction is within `margin` (a multiple
 of the held-out residual scatter) of the threshold's y.  The exact likelihood
-judges every candidate that passes.
+decides every candidate that passes.
 """
 from __future__ import annotations
 

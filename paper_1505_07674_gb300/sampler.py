@@ -25,7 +25,7 @@ proposal the pre-screen places outside is rejected without an exact
 evaluation; one it lets through is evaluated exactly and accepted iff
 L > L*.  For the uniform target on the contour this chain samples exactly the
 part of the contour inside the pre-screen's region -- the whole contour when
-the margin-enlarged region contains it -- and every accepted point is judged
+the margin-enlarged region contains it -- and every accepted point is decided
 by the exact likelihood; the saving is the exact evaluations of the rejected
 proposals the pre-screen catches.
 """
