@@ -119,7 +119,11 @@ enum { LENSED_RULE_POINT = 0, LENSED_RULE_SUB = 1, LENSED_RULE_GL = 2, LENSED_RU
  *                      equation in float-float arithmetic (~48 bits): the
  *                      float grid of traced positions otherwise limits the
  *                      log-likelihood to ~1e-2 absolute on steep, compact
- *                      sources; this mode reaches ~1e-3 at 1.5-3x the cost */
+ *                      sources; this mode reaches ~1e-3 at 1.5-3x the cost.
+ *                      Its batched calls also keep a queue for the second
+ *                      pass of the re-traces (a 24-byte header per trace
+ *                      block and point, and 4 bytes per re-traced ray, at
+ *                      most 256 MiB) beside the image scratch. */
 enum { LENSED_PREC_FP32 = 0, LENSED_PREC_MIXED = 1, LENSED_PREC_FP64 = 2,
        LENSED_PREC_MIXED_FF = 3 };
 
@@ -282,12 +286,14 @@ int lensed_loglike_batch_noalloc(lensed_model *m, const double *params, int P,
                                  double *out_loglike, void *stream);
 
 /* Time the candidate launch configurations (trace block size; PSF applied
- * directly or, where the PSF has numerical rank <= 3, as separable passes)
- * on a batch of P points drawn inside the given DEVICE parameter array (same
- * layout as lensed_loglike_batch) and keep the fastest for later calls.  The
- * trace block size never changes a result; the PSF mode changes the FP32
- * summation order of Eq. 15 (differences at the float rounding level).
- * Synchronous. */
+ * directly or, where the PSF has numerical rank <= 3, as separable passes;
+ * for LENSED_PREC_MIXED_FF also whether the float-float re-traces run inside
+ * the trace blocks or in a second kernel) on a batch of P points drawn
+ * inside the given DEVICE parameter array (same layout as
+ * lensed_loglike_batch) and keep the fastest for later calls.  The trace
+ * block size and the place of the re-traces never change a result; the PSF
+ * mode changes the FP32 summation order of Eq. 15 (differences at the float
+ * rounding level).  Synchronous. */
 int lensed_autotune(lensed_model *m, const double *params, int P, void *stream);
 
 /* Index of the configuration in use (-1: default) and its description, for
@@ -303,7 +309,9 @@ int lensed_measure_alu_peaks(double *fma_tflops, double *mufu_tops, void *stream
 
 /* Use configuration `index` (0 .. n-1 as lensed_tuned_config numbers them,
  * -1 = default) instead of the autotuner's choice; returns the number of
- * configurations n, or LENSED_E_ARG for an index out of range. */
+ * configurations n (6, and 12 for LENSED_PREC_MIXED_FF, whose configurations
+ * 6 + k run configuration k with the float-float re-traces in a second
+ * kernel), or LENSED_E_ARG for an index out of range. */
 int lensed_set_config(lensed_model *m, int index);
 
 /* Launch plan of one lensed_loglike_batch call with P points: number of

@@ -101,6 +101,27 @@ struct PsfBlock {
 struct LaunchCfg {
     int trace_threads;  // threads per trace block, one pixel each
     int psf_sep;        // 1: PSFs of low rank run as separable passes
+    int ff_split;       // 1 (MIXED_FF): float-float re-traces in a second kernel
+};
+
+// A trace block's deferred float-float rays handed to the second pass: the
+// block's system, point, first need-list item, number of entries and offset
+// of its entries in FfQueue::ent.
+struct FfHeader {
+    int sys, p, start, n;
+    long long base;
+};
+
+// MIXED_FF second-pass queue of one trace launch.  cnt[0]: headers written,
+// cnt[1]: entries reserved, cnt[2]: headers taken by the second pass (all
+// three zeroed before the launch).  Entry: pixel slot in the block
+// (bits 0-15) | ray index in the rule grid (bits 16-23).  cnt == nullptr:
+// every block re-traces its own rays (no second pass).
+struct FfQueue {
+    unsigned long long *cnt;
+    FfHeader *hdr;
+    unsigned *ent;
+    long long hcap, ecap;
 };
 
 // --- kernels launched from the runtime (defined in lensed_kernels.cu) ---
@@ -117,12 +138,14 @@ void launch_prologue(const SysDev *sys, const int *comp_sys, int s0, int nS, int
 
 // a2-a5: pixel luminosities of the pixels in the block table, for points
 // p0 .. p0 + nP - 1, into Lbuf[(p - p0) * L_stride + pix_off + pix].  Every
-// system in the table has nn nodes per row of its rule.
+// system in the table has nn nodes per row of its rule.  MIXED_FF with
+// cfg.ff_split and a queue (q.cnt != nullptr): the float-float re-traces run
+// in a second kernel after the first (same results bit for bit).
 void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const int *comp_type,
                   const int *comp_plane, const float *cf, const double *cd,
                   const unsigned char *valid, int P, int C_total, const TraceBlock *blocks,
                   int n_blocks, const int *need, NodeTables nodes, int p0, int nP, void *Lbuf,
-                  long long L_stride, cudaStream_t st);
+                  long long L_stride, cudaStream_t st, FfQueue q = FfQueue{});
 
 // One-time kernel attributes (dynamic shared memory limits); call before
 // any launch or capture.

@@ -30,6 +30,7 @@
 //               the Gauss-Kronrod error estimate |L_K - L_G| of a render.
 #include <math.h>
 
+#include <algorithm>
 #include <utility>
 
 #include "lensed_internal.cuh"
@@ -781,7 +782,8 @@ __global__ void __launch_bounds__(256)
                  const int *__restrict__ comp_plane, const float *__restrict__ cf,
                  const double *__restrict__ cd, const unsigned char *__restrict__ valid, int P,
                  int C_total, const TraceBlock *__restrict__ blocks, const int *__restrict__ need,
-                 NodeTables nodes, int p0, float *__restrict__ Lbuf, long long L_stride)
+                 NodeTables nodes, int p0, float *__restrict__ Lbuf, long long L_stride,
+                 FfQueue fq)
 {
     __shared__ __align__(16) TraceSmem sm;
     const TraceBlock tb = blocks[blockIdx.x];
@@ -791,9 +793,11 @@ __global__ void __launch_bounds__(256)
     const size_t cbase = ((size_t)p * C_total + S.comp_off) * kNC;
     // MIXED with at most 8 nodes per row defers its float-float re-traces to a
     // block-wide queue (64-bit ray mask per pixel), processed by all lanes
-    // after the main loop; the others re-trace in place
+    // after the main loop, or handed to the second pass (k_retrace_ff) when
+    // the launch has a queue in global memory; the others re-trace in place
     constexpr bool kQueue = (MODE == LENSED_PREC_MIXED_FF) && EXACT;
-    __shared__ int q_n;
+    __shared__ int q_n, q_ok;
+    __shared__ long long q_base;
     __shared__ unsigned short q_t[kQueue ? kQCap : 1];
     __shared__ unsigned char q_r[kQueue ? kQCap : 1];
     __shared__ float q_v[kQueue ? kQCap : 1];
@@ -929,6 +933,31 @@ __global__ void __launch_bounds__(256)
         }
         __syncthreads();
         const int nq = min(q_n, kQCap);
+        if (fq.cnt) {
+            // hand the whole queue to the second pass when it fits there
+            if (threadIdx.x == 0) {
+                int ok = 0;
+                if (q_n > 0 && q_n <= kQCap) {
+                    const unsigned long long eb = atomicAdd(&fq.cnt[1], (unsigned long long)q_n);
+                    if (eb + (unsigned long long)q_n <= (unsigned long long)fq.ecap) {
+                        const unsigned long long hb = atomicAdd(&fq.cnt[0], 1ull);
+                        if (hb < (unsigned long long)fq.hcap) {
+                            fq.hdr[hb] = FfHeader{tb.sys, p, tb.start, q_n, (long long)eb};
+                            q_base = (long long)eb;
+                            ok = 1;
+                        }
+                    }
+                }
+                q_ok = ok;
+            }
+            __syncthreads();
+            if (q_ok) {
+                for (int e = threadIdx.x; e < nq; e += blockDim.x)
+                    fq.ent[q_base + e] = (unsigned)q_t[e] | ((unsigned)q_r[e] << 16);
+                if (active) Lbuf[(size_t)(p - p0) * L_stride + S.pix_off + pix] = acc;
+                return;
+            }
+        }
         for (int e = threadIdx.x; e < nq; e += blockDim.x) {
             const int t = q_t[e], r = q_r[e];
             const int pt = need ? need[S.need_off + tb.start + t] : tb.start + t;
@@ -950,6 +979,67 @@ __global__ void __launch_bounds__(256)
         }
     }
     if (active) Lbuf[(size_t)(p - p0) * L_stride + S.pix_off + pix] = acc;
+}
+
+// MIXED_FF second pass: the deferred float-float re-traces of the blocks
+// that handed their queue over (FfHeader per block).  Each CTA takes one
+// header at a time, stages that point's constants, re-traces the entries
+// with all its lanes (only this code runs here, so the rays of many blocks
+// fill whole warps), then adds each pixel's rays to its first-pass sum in ray
+// order -- the same arithmetic in the same order as the in-block path.
+constexpr int kFfThreads = 128;
+
+// SMs of the current device, read once per model (sizes the second pass's
+// persistent grid outside any stream capture)
+static int g_sm_count = 0;
+
+__global__ void __launch_bounds__(kFfThreads)
+    k_retrace_ff(const SysDev *__restrict__ sys, const int *__restrict__ comp_type,
+                 const int *__restrict__ comp_plane, const float *__restrict__ cf,
+                 const double *__restrict__ cd, int C_total, const int *__restrict__ need,
+                 NodeTables nodes, int p0, float *__restrict__ Lbuf, long long L_stride,
+                 FfQueue fq)
+{
+    __shared__ __align__(16) TraceSmem sm;
+    __shared__ unsigned q_e[kQCap];
+    __shared__ float q_v[kQCap];
+    __shared__ long long h_cur;
+    const long long nh = min((long long)fq.cnt[0], fq.hcap);
+    for (;;) {
+        __syncthreads();  // the previous header is done with the shared arrays
+        if (threadIdx.x == 0) h_cur = (long long)atomicAdd(&fq.cnt[2], 1ull);
+        __syncthreads();
+        const long long h = h_cur;
+        if (h >= nh) return;
+        const FfHeader H = fq.hdr[h];
+        const SysDev &S = sys[H.sys];
+        const size_t cbase = ((size_t)H.p * C_total + S.comp_off) * kNC;
+        stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, true, false, nodes);
+        const int n = min(H.n, kQCap);
+        for (int e = threadIdx.x; e < n; e += blockDim.x) q_e[e] = fq.ent[H.base + e];
+        __syncthreads();
+        const int nn = S.nn, nx = S.nx, ncomp = S.ncomp;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const int t = (int)(q_e[e] & 0xffffu), r = (int)(q_e[e] >> 16);
+            const int pt = need ? need[S.need_off + H.start + t] : H.start + t;
+            const int it = pt / nx, jt = pt - it * nx;
+            q_v[e] = source_brightness_ff(sm, ncomp, (float)jt - S.cx, (float)it - S.cy, S.h,
+                                          S.h_lo, r % nn, r / nn);
+        }
+        __syncthreads();
+        // a pixel's entries are consecutive and in ray order; the thread at
+        // the first of them adds the run
+        float *L = Lbuf + (size_t)(H.p - p0) * L_stride + S.pix_off;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+            const unsigned t = q_e[e] & 0xffffu;
+            if (e > 0 && (q_e[e - 1] & 0xffffu) == t) continue;
+            const int pt = need ? need[S.need_off + H.start + (int)t] : H.start + (int)t;
+            float acc = L[pt];
+            for (int k = e; k < n && (q_e[k] & 0xffffu) == t; ++k)
+                acc = fmaf(sm.w[q_e[k] >> 16], q_v[k], acc);
+            L[pt] = acc;
+        }
+    }
 }
 
 // a2-a5 in FP64 (validation mode): plain per-ray loop.
@@ -989,12 +1079,12 @@ static void trace_rows_t(int threads, const SysDev *sys, const int *comp_type,
                          const int *comp_plane, const float *cf, const double *cd,
                          const unsigned char *valid, int P, int C_total, const TraceBlock *blocks,
                          int n_blocks, const int *need, NodeTables nodes, int p0, int nP,
-                         void *Lbuf, long long L_stride, cudaStream_t st)
+                         void *Lbuf, long long L_stride, cudaStream_t st, FfQueue fq)
 {
     dim3 grid((unsigned)n_blocks, (unsigned)nP);
     k_trace_rows<MODE, G, EXACT><<<grid, threads, 0, st>>>(sys, comp_type, comp_plane, cf, cd,
                                                            valid, P, C_total, blocks, need, nodes,
-                                                           p0, (float *)Lbuf, L_stride);
+                                                           p0, (float *)Lbuf, L_stride, fq);
 }
 
 template <int MODE>
@@ -1003,11 +1093,11 @@ static void trace_rows_dispatch(int nn, int threads, const SysDev *sys, const in
                                 const unsigned char *valid, int P, int C_total,
                                 const TraceBlock *blocks, int n_blocks, const int *need,
                                 NodeTables nodes, int p0, int nP, void *Lbuf, long long L_stride,
-                                cudaStream_t st)
+                                cudaStream_t st, FfQueue fq)
 {
 #define LENSED_ROWS(GG, EX)                                                                  \
     trace_rows_t<MODE, GG, EX>(threads, sys, comp_type, comp_plane, cf, cd, valid, P, C_total, \
-                               blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st)
+                               blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st, fq)
     switch (nn) {
     case 1: LENSED_ROWS(1, true); break;
     case 2: LENSED_ROWS(2, true); break;
@@ -1026,7 +1116,7 @@ void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const
                   const int *comp_plane, const float *cf, const double *cd,
                   const unsigned char *valid, int P, int C_total, const TraceBlock *blocks,
                   int n_blocks, const int *need, NodeTables nodes, int p0, int nP, void *Lbuf,
-                  long long L_stride, cudaStream_t st)
+                  long long L_stride, cudaStream_t st, FfQueue q)
 {
     if (n_blocks <= 0 || nP <= 0) return;
     if (precision == LENSED_PREC_FP64) {
@@ -1035,14 +1125,23 @@ void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const
                                                          valid, P, C_total, blocks, need, nodes,
                                                          p0, (double *)Lbuf, L_stride);
     } else if (precision == LENSED_PREC_MIXED_FF) {
+        // the split needs the block-wide queue, i.e. at most 8 nodes per row
+        const bool split = cfg.ff_split && q.cnt && q.hdr && q.ent && nn >= 1 && nn <= 8;
+        if (split) cudaMemsetAsync(q.cnt, 0, 3 * sizeof(unsigned long long), st);
         trace_rows_dispatch<LENSED_PREC_MIXED_FF>(nn, cfg.trace_threads, sys, comp_type,
                                                   comp_plane, cf, cd, valid, P, C_total, blocks,
                                                   n_blocks, need, nodes, p0, nP, Lbuf, L_stride,
-                                                  st);
+                                                  st, split ? q : FfQueue{});
+        if (split) {
+            const long long want = (long long)std::max(g_sm_count, 1) * 8;
+            const unsigned grid = (unsigned)std::max(1LL, std::min(want, q.hcap));
+            k_retrace_ff<<<grid, kFfThreads, 0, st>>>(sys, comp_type, comp_plane, cf, cd, C_total,
+                                                     need, nodes, p0, (float *)Lbuf, L_stride, q);
+        }
     } else {
         trace_rows_dispatch<LENSED_PREC_FP32>(nn, cfg.trace_threads, sys, comp_type, comp_plane,
                                               cf, cd, valid, P, C_total, blocks, n_blocks, need,
-                                              nodes, p0, nP, Lbuf, L_stride, st);
+                                              nodes, p0, nP, Lbuf, L_stride, st, FfQueue{});
     }
 }
 
@@ -1572,6 +1671,9 @@ static void init_ff_tables()
 
 void init_kernel_attributes()
 {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
     init_ff_tables();
     psf_attr_all<float>(std::make_integer_sequence<int, LENSED_MAX_PSF_HALF + 1>{});
     psf_attr_all<double>(std::make_integer_sequence<int, LENSED_MAX_PSF_HALF + 1>{});

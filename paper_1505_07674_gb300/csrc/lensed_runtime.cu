@@ -394,15 +394,33 @@ struct Candidate {
     const char *name;
 };
 
+// The first kBaseCandidates apply to every precision; the rest only change
+// MIXED_FF (its float-float re-traces in a second kernel) and are offered
+// for that mode alone.
 const Candidate kCandidates[] = {
-    {{128, 0}, "trace blocks of 128 pixels, direct PSF"},
-    {{256, 0}, "trace blocks of 256 pixels, direct PSF"},
-    {{64, 0}, "trace blocks of 64 pixels, direct PSF"},
-    {{128, 1}, "trace blocks of 128 pixels, separable PSF where its rank allows"},
-    {{256, 1}, "trace blocks of 256 pixels, separable PSF where its rank allows"},
-    {{64, 1}, "trace blocks of 64 pixels, separable PSF where its rank allows"},
+    {{128, 0, 0}, "trace blocks of 128 pixels, direct PSF"},
+    {{256, 0, 0}, "trace blocks of 256 pixels, direct PSF"},
+    {{64, 0, 0}, "trace blocks of 64 pixels, direct PSF"},
+    {{128, 1, 0}, "trace blocks of 128 pixels, separable PSF where its rank allows"},
+    {{256, 1, 0}, "trace blocks of 256 pixels, separable PSF where its rank allows"},
+    {{64, 1, 0}, "trace blocks of 64 pixels, separable PSF where its rank allows"},
+    {{128, 0, 1}, "trace blocks of 128 pixels, direct PSF, float-float re-trace as a second pass"},
+    {{256, 0, 1}, "trace blocks of 256 pixels, direct PSF, float-float re-trace as a second pass"},
+    {{64, 0, 1}, "trace blocks of 64 pixels, direct PSF, float-float re-trace as a second pass"},
+    {{128, 1, 1}, "trace blocks of 128 pixels, separable PSF where its rank allows, "
+                  "float-float re-trace as a second pass"},
+    {{256, 1, 1}, "trace blocks of 256 pixels, separable PSF where its rank allows, "
+                  "float-float re-trace as a second pass"},
+    {{64, 1, 1}, "trace blocks of 64 pixels, separable PSF where its rank allows, "
+                 "float-float re-trace as a second pass"},
 };
-constexpr int kNumCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
+constexpr int kAllCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
+constexpr int kBaseCandidates = 6;
+constexpr int kMinTraceItems = 64;  // smallest trace block of any candidate
+
+// Second-pass queue entries per scratch chunk are capped at this many
+// (4 bytes each); blocks that find it full re-trace their rays themselves.
+constexpr long long kFfEntryCap = 64LL << 20;
 
 }  // namespace
 
@@ -468,6 +486,10 @@ struct lensed_model {
     DevBuf<double> partial;
     DevBuf<unsigned char> Lbuf;
     int chunk_P = 0;
+    // MIXED_FF second-pass queue (one trace launch at a time)
+    DevBuf<unsigned long long> ffq_cnt;
+    DevBuf<FfHeader> ffq_hdr;
+    DevBuf<unsigned> ffq_ent;
     // render buffers (one point)
     DevBuf<float> rcf;
     DevBuf<double> rcd;
@@ -482,6 +504,15 @@ struct lensed_model {
     unsigned long long graph_clock = 0;
 
     LaunchCfg cfg() const { return kCandidates[cfg_index < 0 ? 0 : cfg_index].cfg; }
+    int n_candidates() const
+    {
+        return precision == LENSED_PREC_MIXED_FF ? kAllCandidates : kBaseCandidates;
+    }
+    FfQueue ffq() const
+    {
+        if (!ffq_cnt.p) return FfQueue{};
+        return {ffq_cnt.p, ffq_hdr.p, ffq_ent.p, (long long)ffq_hdr.n, (long long)ffq_ent.n};
+    }
     size_t elem() const { return precision == LENSED_PREC_FP64 ? sizeof(double) : sizeof(float); }
     NodeTables nodes() const
     {
@@ -558,6 +589,20 @@ int ensure_capacity(lensed_model *m, int P)
     size_t chunk = std::max<size_t>(1, m->scratch_budget / std::max<size_t>(per_point, 1));
     chunk = std::min<size_t>(chunk, (size_t)P);
     if ((rc = m->Lbuf.alloc(chunk * per_point))) return rc;
+    if (m->precision == LENSED_PREC_MIXED_FF) {
+        // headers: one per trace block and point of a chunk at the smallest
+        // block size; entries: every traced ray of a chunk, capped
+        long long blocks = 0, rays = 0;
+        for (int s = 0; s < m->n_sys; ++s) {
+            blocks += (m->need_count[s] + kMinTraceItems - 1) / kMinTraceItems;
+            rays += (long long)m->need_count[s] * m->n_nodes[s] * m->n_nodes[s];
+        }
+        if ((rc = m->ffq_cnt.alloc(3))) return rc;
+        if ((rc = m->ffq_hdr.alloc((size_t)std::max(1LL, blocks * (long long)chunk)))) return rc;
+        if ((rc = m->ffq_ent.alloc(
+                 (size_t)std::max(1LL, std::min(rays * (long long)chunk, kFfEntryCap)))))
+            return rc;
+    }
     m->chunk_P = (int)chunk;
     m->cap_P = P;
     return LENSED_OK;
@@ -598,10 +643,13 @@ void enqueue_batch(lensed_model *m, const double *params, int P, double *out, La
     for (int p0 = 0; p0 < P; p0 += m->chunk_P) {
         const int nP = std::min(m->chunk_P, P - p0);
         if (tm) tm->begin(1);
+        // (a second pass, where launch_trace runs one, completes before the
+        // MIXED fix-up overwrites its pixels: both are on stream st)
         for (const TraceGroup &g : m->trace_groups)
             launch_trace(m->precision, cfg, g.nn, m->sys.p, m->comp_type.p, m->comp_plane.p,
                          m->cf.p, m->cd.p, m->valid.p, P, m->C_total, m->trace_blocks.p + g.off,
-                         g.count, m->need.p, m->nodes(), p0, nP, m->Lbuf.p, m->total_pix, st);
+                         g.count, m->need.p, m->nodes(), p0, nP, m->Lbuf.p, m->total_pix, st,
+                         m->ffq());
         if (is_mixed(m->precision))
             launch_fix64(cfg, m->sys.p, 0, m->n_sys, m->comp_type.p, m->comp_plane.p, m->cf.p,
                          m->cd.p, m->valid.p, P, m->C_total, m->need.p, m->nodes(), p0, nP,
@@ -1480,7 +1528,7 @@ extern "C" int lensed_autotune(lensed_model *m, const double *params, int P, voi
     float best = 1e30f;
     int best_i = 0;
     const int saved = m->cfg_index;
-    for (int i = 0; i < kNumCandidates; ++i) {
+    for (int i = 0; i < m->n_candidates(); ++i) {
         m->cfg_index = i;
         float t_min = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
@@ -1517,8 +1565,13 @@ extern "C" int lensed_batch_plan(lensed_model *m, int P, int *launches, int *chu
     int rc = ensure_capacity(m, P);
     if (rc) return rc;
     const int chunks = (P + m->chunk_P - 1) / m->chunk_P;
+    // a MIXED_FF second pass: one more kernel per trace group of at most 8
+    // nodes per row
+    int second = 0;
+    if (m->precision == LENSED_PREC_MIXED_FF && m->cfg().ff_split && m->ffq_cnt.p)
+        for (const TraceGroup &g : m->trace_groups) second += g.nn >= 1 && g.nn <= 8;
     *launches = 3 + chunks * ((int)m->trace_groups.size() + (int)m->psf_groups.size() +
-                              (is_mixed(m->precision) ? 1 : 0));
+                              (is_mixed(m->precision) ? 1 : 0) + second);
     *chunk_points = m->chunk_P;
     return LENSED_OK;
 }
@@ -1554,13 +1607,13 @@ extern "C" int lensed_profile_batch(lensed_model *m, const double *params, int P
 extern "C" int lensed_set_config(lensed_model *m, int index)
 {
     if (check_model(m)) return LENSED_E_ARG;
-    if (index < -1 || index >= kNumCandidates)
+    if (index < -1 || index >= m->n_candidates())
         return fail(LENSED_E_ARG, "configuration %d out of range (-1..%d)", index,
-                    kNumCandidates - 1);
+                    m->n_candidates() - 1);
     m->cfg_index = index;
     int rc = build_trace_tables(m, m->cfg().trace_threads);
     if (rc) return rc;
-    return kNumCandidates;
+    return m->n_candidates();
 }
 
 extern "C" int lensed_tuned_config(const lensed_model *m, char *buf, int buflen)

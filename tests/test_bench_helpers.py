@@ -23,10 +23,13 @@ def test_code_digest_ignores_comments_only(tmp_path):
     assert bench.kernel_code_digest(a) != bench.kernel_code_digest(c)
 
 
-def test_recorded_traffic_matches_current_kernel_code():
+def test_recorded_traffic_is_reported_only_for_the_captured_kernel_code():
     rec = json.load(open(os.path.join(ROOT, "profiles", "k_trace_rows_traffic.txt")))
     src = os.path.join(ROOT, "paper_1505_07674_gb300", "csrc", "lensed_kernels.cu")
-    assert rec["code_sha256"] == bench.kernel_code_digest(src)
+    if rec["code_sha256"] != bench.kernel_code_digest(src):
+        # the kernels changed since the capture: no traffic figure
+        assert bench.trace_traffic(rec["points"]) is None
+        return
     full = bench.trace_traffic(rec["points"])
     assert abs(full - rec["dram_bytes"]) <= 1e-6 * rec["dram_bytes"]
     assert abs(bench.trace_traffic(512) - rec["dram_bytes_per_point"] * 512) < 1.0

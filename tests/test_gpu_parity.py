@@ -123,6 +123,55 @@ def test_mixed_ff_meets_the_absolute_tolerance(c1):
     assert np.array_equal(g, m.loglike_plain(pts).cpu().numpy()[0])
 
 
+def _second_pass_cases():
+    return {
+        "c1": lambda: W.c1_small(),
+        "c2_96x80": lambda: W.shrink(W.c2_hst(), 96, 80),
+        "c3_six_systems": lambda: W.c3_batch(6),
+        "j0808_64x64_gk": lambda: W.shrink(W.j0808_like(image_prior=True), 64, 64),
+    }
+
+
+@pytest.mark.parametrize("case", list(_second_pass_cases()))
+def test_mixed_ff_second_pass_is_bit_identical(case):
+    # MIXED_FF offers each launch configuration twice: the float-float
+    # re-traces processed by the trace block itself, or handed to a second
+    # kernel.  Both do the same arithmetic in the same order, so every block
+    # size and PSF mode gives the same bits either way (and plain = batched).
+    specs = _second_pass_cases()[case]()
+    specs = specs if isinstance(specs, list) else [specs]
+    obs = [O.mock_observation(s) for s in specs]
+    m = lensed().Model(specs if len(specs) > 1 else specs[0],
+                       obs if len(obs) > 1 else obs[0], precision="mixed_ff")
+    n_par = max(s["n_params"] for s in specs)
+    P = 48
+    pts = np.zeros((len(specs), P, n_par))
+    for k, s in enumerate(specs):
+        pts[k, :, :s["n_params"]] = np.vstack([s["truth"], W.draw_points(s, P - 1, 70 + k)])
+    n_cfg = m.set_config(0)
+    assert n_cfg == 12
+    for i in range(6):
+        m.set_config(i)
+        a = m.loglike_batch(pts).cpu().numpy()
+        launches_a, _ = m.batch_plan(P)
+        m.set_config(i + 6)
+        b = m.loglike_batch(pts).cpu().numpy()
+        launches_b, _ = m.batch_plan(P)
+        assert launches_b > launches_a
+        assert np.array_equal(a, b), (case, i, np.abs(a - b).max())
+        assert np.array_equal(b, m.loglike_plain(pts).cpu().numpy()), (case, i)
+    assert np.isfinite(a).mean() > 0.5
+
+
+def test_second_pass_configurations_are_offered_for_mixed_ff_only(c1):
+    spec, obs, _ = c1
+    for precision, n in (("fp32", 6), ("mixed", 6), ("mixed_ff", 12), ("fp64", 6)):
+        m = lensed().Model(spec, obs, precision=precision)
+        assert m.set_config(-1) == n
+        with pytest.raises(Exception):
+            m.set_config(n)
+
+
 def test_c1_batched_equals_plain_bit_for_bit(c1):
     spec, obs, _ = c1
     m = lensed().Model(spec, obs, precision="mixed")
