@@ -75,6 +75,9 @@ def parse():
                     help="points per step (profiling of small cases only; the benchmark "
                          "workload is 4096)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-point pass")
+    ap.add_argument("--config", type=int, default=None,
+                    help="pin launch configuration N (lensed_set_config numbering) instead "
+                         "of autotuning (profiling of one configuration)")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
                     help="c2 (default, the benchmark), c1 or c3 (other configurations), "
                          "c4 (posterior run), c5 (surrogate pre-screen vs plain), j0808 "
@@ -647,7 +650,10 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     with torch.cuda.stream(stream):
-        m.autotune(params, stream=stream)
+        if args.config is None:
+            m.autotune(params, stream=stream)
+        else:
+            m.set_config(args.config)
         tuned = m.tuned_config()
         launches, chunk = m.batch_plan(npts)
         for _ in range(max(3, args.warmup)):
