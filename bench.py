@@ -152,18 +152,38 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_code_digest(path):
+def kernel_code_digest(path, skip=None):
     """sha256 of a CUDA source without its whole-line comments and trailing
     blanks: a change of code invalidates a recorded profile, a change of
-    comments does not."""
+    comments does not.  skip = (first, stop): the lines from the line equal
+    to `first` up to the line equal to `stop` are left out, when both occur
+    exactly once and in that order (otherwise nothing is left out)."""
     import hashlib
+    src = [line.rstrip() for line in open(path, encoding="utf-8")]
+    lo = hi = -1
+    if skip and src.count(skip[0]) == 1 and src.count(skip[1]) == 1:
+        lo, hi = src.index(skip[0]), src.index(skip[1])
+        if hi < lo:
+            lo = hi = -1
     lines = []
-    for line in open(path, encoding="utf-8"):
-        t = line.rstrip()
-        if t.lstrip().startswith("//") or not t:
+    for k, t in enumerate(src):
+        if lo <= k < hi or t.lstrip().startswith("//") or not t:
             continue
         lines.append(t)
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
+# The PSF kernels (k_psf, k_psf_sep and their helpers) sit between these two
+# lines of lensed_kernels.cu; the trace kernels' traffic record does not
+# depend on them.
+PSF_SECTION = ("// a6-a7: PSF convolution and masked chi^2",
+               "// Reduction tables of the float-float atan / atanh (long double on the host).")
+
+
+def trace_code_digest(src):
+    """Digest of the trace kernels' source: lensed_kernels.cu without its PSF
+    kernels."""
+    return kernel_code_digest(src, skip=PSF_SECTION)
 
 
 def trace_traffic(points_per_launch):
@@ -175,7 +195,7 @@ def trace_traffic(points_per_launch):
     src = os.path.join(ROOT, "paper_1505_07674_gb300", "csrc", "lensed_kernels.cu")
     try:
         rec = json.load(open(path))
-        digest = kernel_code_digest(src)
+        digest = trace_code_digest(src)
     except (OSError, ValueError):
         return None
     if rec.get("code_sha256") != digest:
