@@ -7,15 +7,18 @@
 // device, and integrates the lights that no parameter moves once.  The
 // evaluation calls schedule the kernels of lensed_kernels.cu:
 //
-//   batched:  prologue(all points) -> for each point chunk: trace, psf ->
-//             finalize, captured once per (P, pointers, tile configuration)
-//             into a CUDA graph and replayed with one graph launch;
-//   plain:    for each system and point: prologue, trace, psf, finalize,
-//             each a separate launch (the per-point scheduling of the
-//             paper's code), no graph.
+//   batched:  prologue(all points) -> for each point chunk: trace (and, in
+//             MIXED_FF when the configuration asks for it, the second pass
+//             of the float-float re-traces), the MIXED fix-up, psf ->
+//             finalize, captured once per (P, pointers, launch
+//             configuration) into a CUDA graph and replayed with one graph
+//             launch;
+//   plain:    for each system and point: prologue, trace, fix-up, psf,
+//             finalize, each a separate launch (the per-point scheduling of
+//             the paper's code), no graph.
 //
-// Both run the same kernels on the same per-pixel work, so their results
-// are bit-identical.
+// Both do the same arithmetic in the same order on the same per-pixel work,
+// so their results are bit-identical.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
