@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(256)
     if (!valid[(size_t)tb.sys * P + p]) return;
     const SysDev &S = sys[tb.sys];
     const size_t cbase = ((size_t)p * C_total + S.comp_off) * kNC;
-    // MIXED with at most 8 nodes per row defers its float-float re-traces to a
+    // MIXED_FF with at most 8 nodes per row defers its float-float re-traces to a
     // block-wide queue (64-bit ray mask per pixel), processed by all lanes
     // after the main loop, or handed to the second pass (k_retrace_ff) when
     // the launch has a queue in global memory; the others re-trace in place
