@@ -269,8 +269,13 @@ int lensed_loglike_batch_host(lensed_model *m, const double *params_host, int P,
  * until the process exits.  The paper has no counterpart; it is a property
  * of this library's interface.
  *   - Same arguments and results as lensed_loglike_batch (params and
- *     out_loglike are caller-owned DEVICE arrays), launched directly on
- *     stream without a graph.
+ *     out_loglike are caller-owned DEVICE arrays), bit for bit, launched
+ *     directly on stream without a graph.
+ *   - It uses the model's launch configuration except that, in
+ *     LENSED_PREC_MIXED_FF, the float-float re-traces always run inside
+ *     the trace blocks (the second-pass queue would need memory of its own);
+ *     both forms give the same bits, so only the speed can differ from the
+ *     configuration lensed_tuned_config reports.
  *   - P is limited by the array: the per-point scratch of all P points plus
  *     the pixel luminosities of at least one point must fit in 32 MiB;
  *     larger requests return LENSED_E_ARG with the limit in the message.
@@ -353,7 +358,8 @@ typedef struct lensed_mlp lensed_mlp;
 int lensed_mlp_create(int n_in, int hidden, int max_batch, lensed_mlp **out);
 void lensed_mlp_destroy(lensed_mlp *m);                       /* NULL-safe */
 long long lensed_mlp_param_count(const lensed_mlp *m);
-/* HOST arrays of lensed_mlp_param_count floats; setting resets Adam. */
+/* HOST arrays of lensed_mlp_param_count floats; setting resets Adam and
+ * clears a recorded expired wait (see lensed_mlp_get_params). */
 int lensed_mlp_set_params(lensed_mlp *m, const float *host_params);
 int lensed_mlp_get_params(const lensed_mlp *m, float *host_params);
 /* y[0..B) = network(X[0..B)); asynchronous on stream. */
@@ -367,6 +373,27 @@ int lensed_mlp_gradient(lensed_mlp *m, const float *X, const float *t, int B, fl
 int lensed_mlp_train_step(lensed_mlp *m, const float *X, const float *t, int B, float lr,
                           float *loss, void *stream);
 const char *lensed_mlp_last_error(void);
+
+/* Fault-injection hooks for tests of the error paths (the paper has no
+ * counterpart).  They cause no GPU fault: the failures are made on the host
+ * or by a wait that is allowed to give up early.
+ *   lensed_debug_fail_alloc(after): process-wide; after >= 0 lets `after`
+ *     more device allocations of the library (models and networks) succeed
+ *     and refuses every later one with LENSED_E_NOMEM, before cudaMalloc
+ *     is called; after < 0 switches the injection off.  Returns the number
+ *     of device buffers the library holds at that moment (for leak checks).
+ *     A refused lensed_create_model / lensed_mlp_create frees what it had
+ *     allocated; a refused per-batch allocation leaves the model usable.
+ *   lensed_mlp_debug_spin_limit(m, polls): the pipeline waits of the
+ *     network's later tensor-core products give up after `polls` polls of
+ *     their mbarrier (0: at once) instead of ~16M.  A product whose wait
+ *     gives up waits with the full limit for the tensor-core work it has
+ *     already issued, frees its tensor memory, writes no output and records
+ *     the expiry, which the next lensed_mlp_get_params reports as
+ *     LENSED_E_TIMEOUT; lensed_mlp_set_params clears it.  Values above the
+ *     default are clamped to it. */
+long long lensed_debug_fail_alloc(long long after);
+int lensed_mlp_debug_spin_limit(lensed_mlp *m, int polls);
 
 /* Thread-local message of the last failing call ("" if none). */
 const char *lensed_last_error(void);

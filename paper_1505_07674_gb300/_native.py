@@ -33,7 +33,8 @@ EXPORTS = ("lensed_create_model", "lensed_destroy", "lensed_model_info_get", "le
            "lensed_profile_batch", "lensed_loglike_batch_noalloc",
            "lensed_mlp_create", "lensed_mlp_destroy", "lensed_mlp_param_count",
            "lensed_mlp_set_params", "lensed_mlp_get_params", "lensed_mlp_forward",
-           "lensed_mlp_gradient", "lensed_mlp_train_step", "lensed_mlp_last_error")
+           "lensed_mlp_gradient", "lensed_mlp_train_step", "lensed_mlp_last_error",
+           "lensed_debug_fail_alloc", "lensed_mlp_debug_spin_limit")
 
 
 class Component(C.Structure):
@@ -103,6 +104,9 @@ def lib():
         L.lensed_mlp_forward.argtypes = [vp, vp, C.c_int, vp, vp]
         L.lensed_mlp_gradient.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp]
         L.lensed_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, vp, vp]
+        L.lensed_debug_fail_alloc.argtypes = [C.c_longlong]
+        L.lensed_debug_fail_alloc.restype = C.c_longlong
+        L.lensed_mlp_debug_spin_limit.argtypes = [vp, C.c_int]
         L.lensed_mlp_last_error.restype = C.c_char_p
         L.lensed_mlp_last_error.argtypes = []
         L.lensed_last_error.restype = C.c_char_p

@@ -124,6 +124,14 @@ struct FfQueue {
     long long hcap, ecap;
 };
 
+// True when the test hook lensed_debug_fail_alloc says the next device
+// allocation must fail (every allocator of the library asks before
+// cudaMalloc).  Defined in lensed_runtime.cu.
+bool alloc_failure_injected();
+// Count of live device buffers of the library (+1 per allocation, -1 per
+// free), reported by lensed_debug_fail_alloc.
+void note_buffers(int delta);
+
 // --- kernels launched from the runtime (defined in lensed_kernels.cu) ---
 
 // a1: per (system, point) packed constants and validity.

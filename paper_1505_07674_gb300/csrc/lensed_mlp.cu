@@ -30,6 +30,13 @@
 
 #include "lensed.h"
 
+namespace lensed {
+// lensed_runtime.cu: the test hook lensed_debug_fail_alloc and its count of
+// live device buffers
+bool alloc_failure_injected();
+void note_buffers(int delta);
+}
+
 namespace {
 
 typedef __nv_bfloat16 bf16;
@@ -94,8 +101,10 @@ enum { EPI_F32 = 0, EPI_BIAS_SILU = 1, EPI_DSILU = 2 };
 // reads the accumulators with tcgen05.ld (warp w owns rows 32w..32w+31) into
 // shared memory and applies the fused operation with coalesced row stores.
 // Every wait on an mbarrier is bounded: on expiry the block records the
-// failure in *err, waits (bounded) for its own tensor-core work, frees its
-// tensor memory and returns.
+// failure in *err, waits (bounded, with the full limit) for its own
+// tensor-core work, frees its tensor memory and returns.  `spin` is the poll
+// limit of the pipeline waits (kSpinLimit unless a test lowers it to drive
+// the expiry path).
 constexpr int TM = 128, TN = 128, TK = 64, kStages = 3;
 constexpr uint32_t kTmemCols = TN;          // one FP32 column per output column
 constexpr int kSpinLimit = 1 << 24;         // mbarrier polls before giving up
@@ -121,9 +130,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
                             ((uint32_t)(TM >> 4) << 24);
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit)
 {
-    for (int it = 0; it < kSpinLimit; ++it) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -144,7 +153,7 @@ __global__ void __launch_bounds__(128)
     k_gemm_tc(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb, int M,
               int N, int K, float *__restrict__ Cf, int ldc, const float *__restrict__ bias,
               const float *__restrict__ Zin, float *__restrict__ Zout, bf16 *__restrict__ Hout,
-              int *__restrict__ err)
+              int *__restrict__ err, int spin)
 {
     extern __shared__ __align__(128) unsigned char g_smem[];
     bf16 *As = reinterpret_cast<bf16 *>(g_smem);
@@ -225,20 +234,27 @@ __global__ void __launch_bounds__(128)
         // the products that read it are done
         const int next = kt + kStages - 1;
         if (next < nk) {
-            if (kt >= 1 && !mbar_wait(saddr(&s_bar[(kt - 1) % kStages]),
-                                      (uint32_t)(((kt - 1) / kStages) & 1))) {
+            bool w = true;
+            if (kt >= 1)
+                w = mbar_wait(saddr(&s_bar[(kt - 1) % kStages]),
+                              (uint32_t)(((kt - 1) / kStages) & 1), spin);
+            // one decision for the whole block, so no thread leaves the
+            // loop while another waits at its barrier
+            if (!__syncthreads_and(w)) {
                 ok = false;
-                atomicExch(err, 1);
+                if (tid == 0) atomicExch(err, 1);
             }
             if (ok) load(next % kStages, next * TK);
         }
         cp_async_commit();
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-    // the last slice's commit covers every earlier product
-    const bool done = issued > 0 && mbar_wait(saddr(&s_bar[(issued - 1) % kStages]),
-                                              (uint32_t)(((issued - 1) / kStages) & 1));
-    if (!done || !ok) atomicExch(err, 1);
+    // the last slice's commit covers every earlier product (always the full
+    // limit: tensor memory is freed only after the block's products are done)
+    const bool done = __syncthreads_and(
+        issued > 0 && mbar_wait(saddr(&s_bar[(issued - 1) % kStages]),
+                                (uint32_t)(((issued - 1) / kStages) & 1), kSpinLimit));
+    if ((!done || !ok) && tid == 0) atomicExch(err, 1);
     // epilogue: accumulators -> shared memory (the ring is free now), then
     // coalesced row-wise stores with the fused operation
     float *stile = reinterpret_cast<float *>(g_smem);  // [TM][TN + 1]
@@ -427,20 +443,27 @@ template <typename T>
 struct Buf {
     T *p = nullptr;
     size_t n = 0;
-    ~Buf()
+    ~Buf() { release(); }
+    void release()
     {
-        if (p) cudaFree(p);
+        if (p) {
+            cudaFree(p);
+            lensed::note_buffers(-1);
+        }
+        p = nullptr;
     }
     int alloc(size_t count)
     {
-        if (p) cudaFree(p);
-        p = nullptr;
+        release();
         n = 0;
+        if (lensed::alloc_failure_injected())
+            return mfail(LENSED_E_NOMEM, "cudaMalloc: refused by the injected allocation failure");
         cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
         if (e != cudaSuccess) {
             p = nullptr;
             return mfail(LENSED_E_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
         }
+        lensed::note_buffers(1);
         n = count;
         return LENSED_OK;
     }
@@ -458,24 +481,25 @@ struct lensed_mlp {
     Buf<bf16> Xb, XbT, H1, H2, H3, HT, dZa, dZbuf, dZT;
     Buf<float> Z1, Z2, Z3, dZf, y, dy, lossrow, gW1, tmpcol;
     Buf<int> err;  // set by a tensor-core wait that expired
+    int spin = kSpinLimit;  // poll limit of the GEMM pipeline waits
 };
 
 namespace {
 
 int launch_gemm(int epi, const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K,
                 float *Cf, int ldc, const float *bias, const float *Zin, float *Zout, bf16 *Hout,
-                int *err, cudaStream_t st)
+                int *err, cudaStream_t st, int spin = kSpinLimit)
 {
     dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
     if (epi == EPI_F32)
         k_gemm_tc<EPI_F32><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc, bias,
-                                                         Zin, Zout, Hout, err);
+                                                         Zin, Zout, Hout, err, spin);
     else if (epi == EPI_BIAS_SILU)
         k_gemm_tc<EPI_BIAS_SILU><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc,
-                                                               bias, Zin, Zout, Hout, err);
+                                                               bias, Zin, Zout, Hout, err, spin);
     else
         k_gemm_tc<EPI_DSILU><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc, bias,
-                                                           Zin, Zout, Hout, err);
+                                                           Zin, Zout, Hout, err, spin);
     return LENSED_OK;
 }
 
@@ -492,11 +516,11 @@ void forward(lensed_mlp *m, const float *X, int B, float *y, bool keep_z, cudaSt
     const long long nx = (long long)Bp * m->kin;
     k_pack<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(X, B, m->n_in, Bp, m->kin, m->Xb.p);
     launch_gemm(EPI_BIAS_SILU, m->Xb.p, m->kin, m->W1b.p, m->kin, Bp, H, m->kin, nullptr, H,
-                m->p.p + m->o_b1, nullptr, keep_z ? m->Z1.p : nullptr, m->H1.p, m->err.p, st);
+                m->p.p + m->o_b1, nullptr, keep_z ? m->Z1.p : nullptr, m->H1.p, m->err.p, st, m->spin);
     launch_gemm(EPI_BIAS_SILU, m->H1.p, H, m->W2b.p, H, Bp, H, H, nullptr, H, m->p.p + m->o_b2,
-                nullptr, keep_z ? m->Z2.p : nullptr, m->H2.p, m->err.p, st);
+                nullptr, keep_z ? m->Z2.p : nullptr, m->H2.p, m->err.p, st, m->spin);
     launch_gemm(EPI_BIAS_SILU, m->H2.p, H, m->W3b.p, H, Bp, H, H, nullptr, H, m->p.p + m->o_b3,
-                nullptr, keep_z ? m->Z3.p : nullptr, m->H3.p, m->err.p, st);
+                nullptr, keep_z ? m->Z3.p : nullptr, m->H3.p, m->err.p, st, m->spin);
     k_out<<<(B + 7) / 8, 256, 0, st>>>(m->H3.p, H, m->p.p + m->o_w4, m->p.p + m->o_b4, B, y);
 }
 
@@ -518,25 +542,25 @@ void gradient(lensed_mlp *m, const float *X, const float *t, int B, float *loss,
     transpose(m->dZa.p, Bp, H, m->dZT.p, st);
     transpose(m->H2.p, Bp, H, m->HT.p, st);
     launch_gemm(EPI_F32, m->dZT.p, Bp, m->HT.p, Bp, H, H, Bp, g + m->o_W3, H, nullptr, nullptr,
-                nullptr, nullptr, m->err.p, st);
+                nullptr, nullptr, m->err.p, st, m->spin);
     k_colsum<<<(H + 127) / 128, 128, 0, st>>>(m->dZf.p, Bp, H, g + m->o_b3);
     transpose(m->W3b.p, H, H, m->WT.p, st);
     launch_gemm(EPI_DSILU, m->dZa.p, H, m->WT.p, H, Bp, H, H, nullptr, H, nullptr, m->Z2.p,
-                m->dZf.p, m->dZbuf.p, m->err.p, st);
+                m->dZf.p, m->dZbuf.p, m->err.p, st, m->spin);
     // layer 2
     transpose(m->dZbuf.p, Bp, H, m->dZT.p, st);
     transpose(m->H1.p, Bp, H, m->HT.p, st);
     launch_gemm(EPI_F32, m->dZT.p, Bp, m->HT.p, Bp, H, H, Bp, g + m->o_W2, H, nullptr, nullptr,
-                nullptr, nullptr, m->err.p, st);
+                nullptr, nullptr, m->err.p, st, m->spin);
     k_colsum<<<(H + 127) / 128, 128, 0, st>>>(m->dZf.p, Bp, H, g + m->o_b2);
     transpose(m->W2b.p, H, H, m->WT.p, st);
     launch_gemm(EPI_DSILU, m->dZbuf.p, H, m->WT.p, H, Bp, H, H, nullptr, H, nullptr, m->Z1.p,
-                m->dZf.p, m->dZa.p, m->err.p, st);
+                m->dZf.p, m->dZa.p, m->err.p, st, m->spin);
     // layer 1: dW1 = dZ1^T X (padded to kin columns), db1
     transpose(m->dZa.p, Bp, H, m->dZT.p, st);
     transpose(m->Xb.p, Bp, m->kin, m->XbT.p, st);
     launch_gemm(EPI_F32, m->dZT.p, Bp, m->XbT.p, Bp, H, m->kin, Bp, m->gW1.p, m->kin, nullptr,
-                nullptr, nullptr, nullptr, m->err.p, st);
+                nullptr, nullptr, nullptr, m->err.p, st, m->spin);
     k_copy_cols<<<(H * m->n_in + 255) / 256, 256, 0, st>>>(m->gW1.p, H, m->kin, m->n_in, g);
     k_colsum<<<(H + 127) / 128, 128, 0, st>>>(m->dZf.p, Bp, H, g + m->o_b1);
 }
@@ -625,12 +649,22 @@ extern "C" void lensed_mlp_destroy(lensed_mlp *m)
 
 extern "C" long long lensed_mlp_param_count(const lensed_mlp *m) { return m ? (long long)m->np : -1; }
 
+extern "C" int lensed_mlp_debug_spin_limit(lensed_mlp *m, int polls)
+{
+    if (!m) return mfail(LENSED_E_ARG, "NULL argument");
+    if (polls < 0) return mfail(LENSED_E_ARG, "polls = %d must be >= 0", polls);
+    m->spin = polls > kSpinLimit ? kSpinLimit : polls;
+    return LENSED_OK;
+}
+
 extern "C" int lensed_mlp_set_params(lensed_mlp *m, const float *host_params)
 {
     if (!m || !host_params) return mfail(LENSED_E_ARG, "NULL argument");
+    MCUDA(cudaDeviceSynchronize());
     MCUDA(cudaMemcpy(m->p.p, host_params, m->np * sizeof(float), cudaMemcpyHostToDevice));
     MCUDA(cudaMemset(m->m.p, 0, m->np * sizeof(float)));
     MCUDA(cudaMemset(m->v.p, 0, m->np * sizeof(float)));
+    MCUDA(cudaMemset(m->err.p, 0, sizeof(int)));  // a fresh state: no expired wait
     m->step = 0;
     int rc = refresh(m, nullptr);
     if (rc) return rc;

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -34,6 +35,25 @@
 #include "lensed_internal.cuh"
 
 using namespace lensed;
+
+// Allocation-failure injection for tests (lensed_debug_fail_alloc): -1 off,
+// else how many more device allocations may succeed before every later one
+// is refused.
+static std::atomic<long long> g_alloc_budget{-1};
+// Device buffers the library holds (models and networks), for leak checks.
+static std::atomic<long long> g_live_buffers{0};
+
+void lensed::note_buffers(int delta) { g_live_buffers += delta; }
+
+bool lensed::alloc_failure_injected()
+{
+    long long b = g_alloc_budget.load();
+    while (b >= 0) {
+        if (b == 0) return true;
+        if (g_alloc_budget.compare_exchange_weak(b, b - 1)) return false;
+    }
+    return false;
+}
 
 namespace {
 
@@ -346,7 +366,10 @@ struct DevBuf {
     ~DevBuf() { release(); }
     void release()
     {
-        if (p) cudaFree(p);
+        if (p) {
+            cudaFree(p);
+            note_buffers(-1);
+        }
         p = nullptr;
         n = 0;
     }
@@ -354,12 +377,16 @@ struct DevBuf {
     {
         release();
         if (count == 0) count = 1;
+        if (lensed::alloc_failure_injected())
+            return fail(LENSED_E_NOMEM, "cudaMalloc(%zu bytes): refused by the injected "
+                                        "allocation failure", count * sizeof(T));
         cudaError_t e = cudaMalloc(&p, count * sizeof(T));
         if (e != cudaSuccess) {
             p = nullptr;
             return fail(LENSED_E_NOMEM, "cudaMalloc(%zu bytes): %s", count * sizeof(T),
                         cudaGetErrorString(e));
         }
+        note_buffers(1);
         n = count;
         return LENSED_OK;
     }
@@ -582,6 +609,10 @@ int ensure_capacity(lensed_model *m, int P)
     if (P <= m->cap_P) return LENSED_OK;
     cudaDeviceSynchronize();
     m->clear_graphs();
+    // no capacity until every buffer below is in place: a failed allocation
+    // leaves the model valid, and the next call allocates again
+    m->cap_P = 0;
+    m->chunk_P = 0;
     int rc;
     if ((rc = m->cf.alloc((size_t)P * m->C_total * kNC))) return rc;
     if ((rc = m->cd.alloc((size_t)P * m->C_total * kNC))) return rc;
@@ -683,6 +714,12 @@ int check_model(const lensed_model *m)
 // C ABI
 
 extern "C" const char *lensed_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" long long lensed_debug_fail_alloc(long long after)
+{
+    g_alloc_budget.store(after < 0 ? -1 : after);
+    return g_live_buffers.load();
+}
 
 // Low-rank form of a normalised, flipped PSF F [m][n] (m = 2p+1 rows):
 // singular value decomposition by one-sided Jacobi rotations (Hestenes) in
@@ -1710,6 +1747,9 @@ extern "C" int lensed_loglike_batch_noalloc(lensed_model *m, const double *param
                     m->C_total, m->bn_table.p, cf, cd, cvalid, valid, st);
     for (int p0 = 0; p0 < P; p0 += chunk) {
         const int nP = std::min(chunk, P - p0);
+        // no second-pass queue here (it lives in model-owned memory): in
+        // MIXED_FF the trace blocks always re-trace their own rays, which
+        // gives the same bits as the second pass would
         for (const TraceGroup &g : m->trace_groups)
             launch_trace(m->precision, cfg, g.nn, m->sys.p, m->comp_type.p, m->comp_plane.p, cf,
                          cd, valid, P, m->C_total, m->trace_blocks.p + g.off, g.count, m->need.p,

@@ -6,8 +6,12 @@ all of the GPU's memory for its own pool, or a service with a device-memory
 budget fixed at start-up.  Its scratch is a fixed 32 MiB array inside the
 library.  These tests call it through the C ABI and check it against
 lensed_loglike_batch on the same points, on two calls in a row (the second
-call reuses the array the first one left behind), and that an oversized
-request is refused with a clear message.  This file is collected last.
+call reuses the array the first one left behind), in every precision mode:
+the two calls run the same kernels with the same fixed-order reductions, so
+the results must be equal bit for bit (in MIXED_FF also when the model's
+configuration hands the float-float re-traces to a second kernel, which
+this call never does).  An oversized request must be refused with a clear
+message.  This file is collected last.
 """
 import ctypes as C
 
@@ -38,30 +42,31 @@ def _noalloc(m, params, out):
     return rc, N.lib().lensed_last_error().decode()
 
 
-def _close(a, b):
-    # the tolerance of the parity tests, and -inf where the batched call has it
-    assert np.array_equal(np.isneginf(a), np.isneginf(b))
-    ok = np.isfinite(a)
-    assert np.all(np.abs(a[ok] - b[ok]) <= np.maximum(1e-3, 1e-5 * np.abs(a[ok])))
-
-
-@pytest.mark.parametrize("which,P", [("c1", 96), ("c2", 256)])
-def test_noalloc_matches_batched_on_two_calls(which, P):
+@pytest.mark.parametrize("which,P,precision,config", [
+    ("c1", 96, "fp32", None), ("c1", 96, "mixed", None), ("c1", 96, "fp64", None),
+    ("c1", 96, "mixed_ff", None), ("c1", 96, "mixed_ff", 7),
+    ("c2", 256, "mixed", None), ("c2", 256, "mixed_ff", 7),
+])
+def test_noalloc_equals_batched_on_two_calls(which, P, precision, config):
     from paper_1505_07674_gb300 import lensed as LZ
     spec = W.c1_small() if which == "c1" else W.c2_hst()
     obs = O.mock_observation(spec)
-    m = LZ.Model(spec, obs, precision="mixed")
+    m = LZ.Model(spec, obs, precision=precision)
+    if config is not None:
+        m.set_config(config)  # 7: trace blocks of 256, re-traces in a second kernel
     pts = W.draw_points(spec, P, 99)
-    pts[3, 3] = 1.5  # one point outside the domain
+    pts[3, spec["param_names"].index("q_L")] = 1.5  # one point outside the domain
     params = m.pack_params(pts)
     ref = m.loglike_batch(params).cpu().numpy()
+    assert np.isneginf(ref[0, 3]) and np.isfinite(ref).sum() == P - 1
     out = torch.full((1, P), 7.0, dtype=torch.float64, device="cuda")
     for _ in range(2):
         out.fill_(7.0)
         rc, msg = _noalloc(m, params, out)
         assert rc == 0, msg
         torch.cuda.synchronize()
-        _close(ref, out.cpu().numpy())
+        got = out.cpu().numpy()
+        assert np.array_equal(ref, got), (precision, np.nanmax(np.abs(ref - got)))
     m.close()
 
 
