@@ -374,6 +374,35 @@ int lensed_mlp_train_step(lensed_mlp *m, const float *X, const float *t, int B, 
                           float *loss, void *stream);
 const char *lensed_mlp_last_error(void);
 
+/* Proposals for the nested-sampling driver (Sec. 3.2 samples the prior
+ * inside the current likelihood contour; the network's pre-screen is this
+ * library's own addition): n candidates, numbered first .. first+n-1 of the
+ * counter-based stream `seed` (Philox4x32-10), each a uniform draw inside
+ * the ellipsoid v = center + chol z, |z| <= 1.  v lives in the sampler's
+ * unit-cube coordinates with each periodic axis shifted by shift[j] (0 on
+ * the other axes); the candidate's point is u = v + shift wrapped into
+ * [0, 1), which keeps the draws uniform and lets a likelihood contour that
+ * straddles the ends of a periodic parameter's range be bounded by one
+ * ellipsoid.  A candidate survives when v lies inside the open unit cube
+ * and, if m is not NULL, the network's output at x = x_whiten (u - x_center)
+ * is below y_cut (the caller's threshold in the network's output units).
+ *   d = the dimension (1..32; m's n_in when m is given);
+ *   center [d], chol [d][d] (row-major, lower triangle read), shift [d] (or
+ *   NULL: no shift), x_center [d], x_whiten [d][d] (row-major): DEVICE
+ *   float arrays, caller-owned (the candidates are drawn in FP32 and
+ *   returned as doubles);
+ *   u_out [n][d] DEVICE doubles, idx_out [n] DEVICE ints, n_out DEVICE int:
+ *   the survivors' points and candidate numbers (relative to `first`) in the
+ *   first *n_out rows, in no particular order (sort by idx_out for a
+ *   reproducible order; each candidate's point is a function of its number
+ *   alone).  Asynchronous on stream; grows the network's screening scratch
+ *   (synchronising the stream) when n exceeds every earlier n. */
+int lensed_mlp_screen_ellipsoid(lensed_mlp *m, int d, int n, unsigned long long seed,
+                                unsigned long long first, const float *center,
+                                const float *chol, const float *shift,
+                                const float *x_center, const float *x_whiten, float y_cut,
+                                double *u_out, int *idx_out, int *n_out, void *stream);
+
 /* Fault-injection hooks for tests of the error paths (the paper has no
  * counterpart).  They cause no GPU fault: the failures are made on the host
  * or by a wait that is allowed to give up early.

@@ -34,7 +34,8 @@ EXPORTS = ("lensed_create_model", "lensed_destroy", "lensed_model_info_get", "le
            "lensed_mlp_create", "lensed_mlp_destroy", "lensed_mlp_param_count",
            "lensed_mlp_set_params", "lensed_mlp_get_params", "lensed_mlp_forward",
            "lensed_mlp_gradient", "lensed_mlp_train_step", "lensed_mlp_last_error",
-           "lensed_debug_fail_alloc", "lensed_mlp_debug_spin_limit")
+           "lensed_debug_fail_alloc", "lensed_mlp_debug_spin_limit",
+           "lensed_mlp_screen_ellipsoid")
 
 
 class Component(C.Structure):
@@ -104,6 +105,9 @@ def lib():
         L.lensed_mlp_forward.argtypes = [vp, vp, C.c_int, vp, vp]
         L.lensed_mlp_gradient.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp]
         L.lensed_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, vp, vp]
+        L.lensed_mlp_screen_ellipsoid.argtypes = [vp, C.c_int, C.c_int, C.c_ulonglong,
+                                                  C.c_ulonglong, vp, vp, vp, vp, vp, C.c_float,
+                                                  vp, vp, vp, vp]
         L.lensed_debug_fail_alloc.argtypes = [C.c_longlong]
         L.lensed_debug_fail_alloc.restype = C.c_longlong
         L.lensed_mlp_debug_spin_limit.argtypes = [vp, C.c_int]

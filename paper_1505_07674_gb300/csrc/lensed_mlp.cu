@@ -153,9 +153,18 @@ __global__ void __launch_bounds__(128)
     k_gemm_tc(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb, int M,
               int N, int K, float *__restrict__ Cf, int ldc, const float *__restrict__ bias,
               const float *__restrict__ Zin, float *__restrict__ Zout, bf16 *__restrict__ Hout,
-              int *__restrict__ err, int spin)
+              int *__restrict__ err, int spin, int kchunk)
 {
     extern __shared__ __align__(128) unsigned char g_smem[];
+    if (kchunk > 0) {
+        // split-K (EPI_F32 only): block z contracts K range [z kchunk, (z+1) kchunk)
+        // into its own [M][ldc] slab of Cf; a fixed-order sum follows
+        const int kz = blockIdx.z * kchunk;
+        A += kz;
+        B += kz;
+        K = min(kchunk, K - kz);
+        Cf += (size_t)blockIdx.z * M * ldc;
+    }
     bf16 *As = reinterpret_cast<bf16 *>(g_smem);
     bf16 *Bs = As + kStages * kStageA;
     __shared__ __align__(8) unsigned long long s_bar[kStages];
@@ -369,33 +378,61 @@ __global__ void k_out_back(const float *__restrict__ y, const float *__restrict_
     dZb[i] = __float2bfloat16(g);
 }
 
-// out[n] = sum_m in[m][n] (fixed order), fp32 in
-__global__ void k_colsum(const float *__restrict__ in, int M, int N, float *__restrict__ out)
+// Column sums out[n] = sum_m w[m] in[m][n] (w = 1 when NULL) in two passes
+// with a fixed order: block (x, y) sums rows [y R, (y+1) R) of 32 columns
+// (8 row lanes per column, then the 8 lane sums in order) into part[y][n];
+// k_colsum_final adds the parts in order.
+constexpr int kColParts = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_colsum_part(const T *__restrict__ in, const float *__restrict__ w, int M, int N, int R,
+                  float *__restrict__ part)
+{
+    __shared__ float t[8][33];
+    const int n = blockIdx.x * 32 + threadIdx.x;
+    const int m0 = blockIdx.y * R, m1 = min(M, m0 + R);
+    float s = 0.f;
+    if (n < N)
+        for (int m = m0 + threadIdx.y; m < m1; m += 8) {
+            const float v = (float)in[(size_t)m * N + n];
+            s = w ? fmaf(v, w[m], s) : s + v;
+        }
+    t[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && n < N) {
+        float r = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r += t[k][threadIdx.x];
+        part[(size_t)blockIdx.y * N + n] = r;
+    }
+}
+
+__global__ void k_colsum_final(const float *__restrict__ part, int S, int N,
+                               float *__restrict__ out)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     float s = 0.f;
-    for (int m = 0; m < M; ++m) s += in[(size_t)m * N + n];
+    for (int z = 0; z < S; ++z) s += part[(size_t)z * N + n];
     out[n] = s;
 }
 
-// dw4[k] = sum_m h3[m][k] dy[m]
-__global__ void k_dw4(const bf16 *__restrict__ H3, const float *__restrict__ dy, int Bp, int H,
-                      float *__restrict__ dw4)
+// out[0] = sum of n values: 1024 threads, strided lane sums, then a fixed
+// shared-memory tree
+__global__ void __launch_bounds__(1024) k_sum(const float *__restrict__ in, int n,
+                                              float *__restrict__ out)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= H) return;
+    __shared__ float t[1024];
     float s = 0.f;
-    for (int m = 0; m < Bp; ++m) s += __bfloat162float(H3[(size_t)m * H + k]) * dy[m];
-    dw4[k] = s;
-}
-
-__global__ void k_sum(const float *__restrict__ in, int n, float *__restrict__ out)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    float s = 0.f;
-    for (int i = 0; i < n; ++i) s += in[i];
-    out[0] = s;
+    for (int i = threadIdx.x; i < n; i += 1024) s += in[i];
+    t[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if (threadIdx.x < w) t[threadIdx.x] += t[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = t[0];
 }
 
 // copy the first c columns of [R][ld] into [R][c]
@@ -469,6 +506,146 @@ struct Buf {
     }
 };
 
+// ---------------------------------------------------------------------------
+// Proposals for the nested-sampling driver, drawn uniformly inside an
+// ellipsoid and pre-screened by the network.
+//
+// Counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror & Shaw, "Parallel
+// random numbers: as easy as 1, 2, 3", SC'11), written from its published
+// definition: ten rounds of two 32x32->64-bit products with the multipliers
+// 0xD2511F53 and 0xCD9E8D57, the key bumped by the Weyl constants 0x9E3779B9
+// and 0xBB67AE85 between rounds.  Candidate i of a stream draws the counters
+// (i, j, 0, 0), j = 0, 1, ..., under the key (seed low, seed high), so every
+// candidate is reproducible on its own.
+struct Philox4 {
+    uint32_t v[4];
+};
+
+__device__ __forceinline__ Philox4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t k0,
+                                                 uint32_t k1)
+{
+    uint32_t x0 = c0, x1 = c1, x2 = 0u, x3 = 0u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * x0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * x2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+        x1 = (uint32_t)p1;
+        x3 = (uint32_t)p0;
+        x0 = n0;
+        x2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return {{x0, x1, x2, x3}};
+}
+
+// 24-bit uniform in (0, 1)
+__device__ __forceinline__ float u01f(uint32_t x)
+{
+    return ((float)(x >> 8) + 0.5f) * (1.f / 16777216.f);
+}
+
+constexpr int kMaxScreenDim = 32;
+
+// Candidate `i` of stream `seed`: v = c + L z, z uniform in the unit ball
+// (Gaussian direction by Box-Muller, radius U^(1/d)), in coordinates whose
+// periodic axes are shifted by `shift` (0 on the others); returns whether v
+// lies inside the open unit cube, and u = v + shift wrapped into [0, 1), the
+// point in the sampler's coordinates (shifting and wrapping a periodic axis
+// preserves the uniform measure).  FP32: a proposal needs no more than float
+// resolution, and the sampler uses the point exactly as drawn.
+__device__ bool ellipsoid_point(int d, unsigned long long seed, unsigned long long i,
+                                const float *__restrict__ c, const float *__restrict__ L,
+                                const float *__restrict__ shift, float *u)
+{
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    float z[kMaxScreenDim];
+    // d normals (Box-Muller pairs) and one uniform for the radius, four
+    // uniforms per Philox call
+    const int n_u = 2 * ((d + 1) / 2) + 1;
+    float uu[kMaxScreenDim + 4];
+    for (int j = 0; 4 * j < n_u; ++j) {
+        const Philox4 r = philox4x32_10((uint32_t)i, (uint32_t)(i >> 32) ^ ((uint32_t)j << 16), k0,
+                                        k1);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) uu[4 * j + e] = u01f(r.v[e]);
+    }
+    float n2 = 0.f;
+    for (int j = 0; j < d; j += 2) {
+        const float rr = sqrtf(-2.f * logf(uu[j]));
+        float sn, cs;
+        sincospif(2.f * uu[j + 1], &sn, &cs);
+        z[j] = rr * cs;
+        n2 += z[j] * z[j];
+        if (j + 1 < d) {
+            z[j + 1] = rr * sn;
+            n2 += z[j + 1] * z[j + 1];
+        }
+    }
+    const float rad = exp2f(log2f(uu[n_u - 1]) / (float)d) * rsqrtf(n2);
+    bool inside = true;
+    for (int j = 0; j < d; ++j) {
+        float a = 0.f;
+        for (int k = 0; k <= j; ++k) a = fmaf(L[j * d + k], z[k], a);
+        a = fmaf(a, rad, c[j]);
+        inside = inside && a > 0.f && a < 1.f;
+        if (shift) {
+            a += shift[j];
+            if (a >= 1.f) a -= 1.f;
+        }
+        u[j] = a;
+    }
+    return inside;
+}
+
+// Network inputs of candidates [first, first + n): X[i] = A (u_i - xc), and
+// whether u_i lies inside the unit cube.
+__global__ void k_ell_draw(int d, int n, unsigned long long seed, unsigned long long first,
+                           const float *__restrict__ c, const float *__restrict__ L,
+                           const float *__restrict__ shift, const float *__restrict__ xc,
+                           const float *__restrict__ A, float *__restrict__ X,
+                           unsigned char *__restrict__ inside)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float u[kMaxScreenDim];
+    inside[i] = ellipsoid_point(d, seed, first + i, c, L, shift, u) ? 1 : 0;
+    for (int j = 0; j < d; ++j) u[j] -= xc[j];
+    for (int j = 0; j < d; ++j) {
+        float a = 0.f;
+        for (int k = 0; k < d; ++k) a = fmaf(A[j * d + k], u[k], a);
+        X[(size_t)i * d + j] = a;
+    }
+}
+
+// Survivors: inside the cube and (screened) with network output below the
+// cut.  Each takes a slot by an atomic counter (the host restores the
+// candidate order from idx_out) and gets its point recomputed.
+__global__ void k_ell_select(int d, int n, unsigned long long seed, unsigned long long first,
+                             const float *__restrict__ c, const float *__restrict__ L,
+                             const float *__restrict__ shift,
+                             const unsigned char *__restrict__ inside,
+                             const float *__restrict__ y, float y_cut, double *__restrict__ u_out,
+                             int *__restrict__ idx_out, int *__restrict__ n_out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float u[kMaxScreenDim];
+    bool keep;
+    if (inside) {
+        keep = inside[i] && y[i] < y_cut;  // NaN outputs are screened out
+        if (keep) ellipsoid_point(d, seed, first + i, c, L, shift, u);
+    } else {
+        keep = ellipsoid_point(d, seed, first + i, c, L, shift, u);
+    }
+    if (!keep) return;
+    const int slot = atomicAdd(n_out, 1);
+    idx_out[slot] = i;
+    for (int j = 0; j < d; ++j) u_out[(size_t)slot * d + j] = (double)u[j];
+}
+
 }  // namespace
 
 struct lensed_mlp {
@@ -480,8 +657,13 @@ struct lensed_mlp {
     Buf<bf16> W1b, W2b, W3b, WT;
     Buf<bf16> Xb, XbT, H1, H2, H3, HT, dZa, dZbuf, dZT;
     Buf<float> Z1, Z2, Z3, dZf, y, dy, lossrow, gW1, tmpcol;
+    Buf<float> ws;    // split-K partial weight gradients [kMaxSplit][H][max(H, kin)]
+    Buf<float> part;  // column-sum parts [kColParts][H]
     Buf<int> err;  // set by a tensor-core wait that expired
     int spin = kSpinLimit;  // poll limit of the GEMM pipeline waits
+    // proposal screening scratch (grown on demand)
+    Buf<float> sX, sy;
+    Buf<unsigned char> sin;
 };
 
 namespace {
@@ -493,14 +675,44 @@ int launch_gemm(int epi, const bf16 *A, int lda, const bf16 *B, int ldb, int M, 
     dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
     if (epi == EPI_F32)
         k_gemm_tc<EPI_F32><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc, bias,
-                                                         Zin, Zout, Hout, err, spin);
+                                                         Zin, Zout, Hout, err, spin, 0);
     else if (epi == EPI_BIAS_SILU)
         k_gemm_tc<EPI_BIAS_SILU><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc,
-                                                               bias, Zin, Zout, Hout, err, spin);
+                                                               bias, Zin, Zout, Hout, err, spin, 0);
     else
         k_gemm_tc<EPI_DSILU><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, Cf, ldc, bias,
-                                                           Zin, Zout, Hout, err, spin);
+                                                           Zin, Zout, Hout, err, spin, 0);
     return LENSED_OK;
+}
+
+// Weight gradient C[M][N] = A B^T with a long contraction (K = the batch):
+// split into S <= kMaxSplit ranges of >= 4 K-slices, one block row per range
+// (so M/TM x N/TN x S blocks keep the tensor cores of many SMs busy), the
+// partial products summed in range order (deterministic).
+constexpr int kMaxSplit = 32;
+
+__global__ void k_splitk_sum(const float *__restrict__ ws, int S, int M, int N,
+                             float *__restrict__ C, int ldc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * N) return;
+    const int r = i / N, c = i - (i / N) * N;
+    float s = 0.f;
+    for (int z = 0; z < S; ++z) s += ws[(size_t)z * M * N + i];
+    C[(size_t)r * ldc + c] = s;
+}
+
+void launch_wgrad(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K, float *C,
+                  int ldc, float *ws, int *err, cudaStream_t st, int spin)
+{
+    const int slices = (K + TK - 1) / TK;
+    const int S = std::max(1, std::min(kMaxSplit, slices / 4));
+    const int kchunk = (slices + S - 1) / S * TK;
+    const int Sz = (K + kchunk - 1) / kchunk;
+    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, Sz);
+    k_gemm_tc<EPI_F32><<<grid, 128, kGemmSmem, st>>>(A, lda, B, ldb, M, N, K, ws, N, nullptr,
+                                                     nullptr, nullptr, nullptr, err, spin, kchunk);
+    k_splitk_sum<<<(M * N + 255) / 256, 256, 0, st>>>(ws, Sz, M, N, C, ldc);
 }
 
 void transpose(const bf16 *in, int R, int C, bf16 *out, cudaStream_t st)
@@ -524,6 +736,16 @@ void forward(lensed_mlp *m, const float *X, int B, float *y, bool keep_z, cudaSt
     k_out<<<(B + 7) / 8, 256, 0, st>>>(m->H3.p, H, m->p.p + m->o_w4, m->p.p + m->o_b4, B, y);
 }
 
+// out[n] = sum_m w[m] in[m][n] over M rows (w NULL: 1), fixed order
+template <typename T>
+void colsum(lensed_mlp *m, const T *in, const float *w, int M, int N, float *out, cudaStream_t st)
+{
+    const int R = (M + kColParts - 1) / kColParts;
+    const int S = (M + R - 1) / R;
+    k_colsum_part<T><<<dim3((N + 31) / 32, S), dim3(32, 8), 0, st>>>(in, w, M, N, R, m->part.p);
+    k_colsum_final<<<(N + 127) / 128, 128, 0, st>>>(m->part.p, S, N, out);
+}
+
 // loss and gradient of rows [0, B) into m->g and loss (device scalar)
 void gradient(lensed_mlp *m, const float *X, const float *t, int B, float *loss, cudaStream_t st)
 {
@@ -535,34 +757,34 @@ void gradient(lensed_mlp *m, const float *X, const float *t, int B, float *loss,
     k_out_back<<<(unsigned)((nbh + 255) / 256), 256, 0, st>>>(m->y.p, t, B, Bp, H,
                                                                m->p.p + m->o_w4, m->Z3.p, m->dy.p,
                                                                m->lossrow.p, m->dZf.p, m->dZa.p);
-    k_sum<<<1, 32, 0, st>>>(m->lossrow.p, Bp, loss);
-    k_dw4<<<(H + 127) / 128, 128, 0, st>>>(m->H3.p, m->dy.p, Bp, H, g + m->o_w4);
-    k_sum<<<1, 32, 0, st>>>(m->dy.p, Bp, g + m->o_b4);
+    k_sum<<<1, 1024, 0, st>>>(m->lossrow.p, Bp, loss);
+    colsum(m, m->H3.p, m->dy.p, Bp, H, g + m->o_w4, st);  // dw4 = sum_m dy[m] h3[m]
+    k_sum<<<1, 1024, 0, st>>>(m->dy.p, Bp, g + m->o_b4);
     // layer 3: dW3 = dZ3^T H2, db3, dZ2 = (dZ3 W3) * silu'(Z2)
     transpose(m->dZa.p, Bp, H, m->dZT.p, st);
     transpose(m->H2.p, Bp, H, m->HT.p, st);
-    launch_gemm(EPI_F32, m->dZT.p, Bp, m->HT.p, Bp, H, H, Bp, g + m->o_W3, H, nullptr, nullptr,
-                nullptr, nullptr, m->err.p, st, m->spin);
-    k_colsum<<<(H + 127) / 128, 128, 0, st>>>(m->dZf.p, Bp, H, g + m->o_b3);
+    launch_wgrad(m->dZT.p, Bp, m->HT.p, Bp, H, H, Bp, g + m->o_W3, H, m->ws.p, m->err.p, st,
+                 m->spin);
+    colsum(m, m->dZf.p, nullptr, Bp, H, g + m->o_b3, st);
     transpose(m->W3b.p, H, H, m->WT.p, st);
     launch_gemm(EPI_DSILU, m->dZa.p, H, m->WT.p, H, Bp, H, H, nullptr, H, nullptr, m->Z2.p,
                 m->dZf.p, m->dZbuf.p, m->err.p, st, m->spin);
     // layer 2
     transpose(m->dZbuf.p, Bp, H, m->dZT.p, st);
     transpose(m->H1.p, Bp, H, m->HT.p, st);
-    launch_gemm(EPI_F32, m->dZT.p, Bp, m->HT.p, Bp, H, H, Bp, g + m->o_W2, H, nullptr, nullptr,
-                nullptr, nullptr, m->err.p, st, m->spin);
-    k_colsum<<<(H + 127) / 128, 128, 0, st>>>(m->dZf.p, Bp, H, g + m->o_b2);
+    launch_wgrad(m->dZT.p, Bp, m->HT.p, Bp, H, H, Bp, g + m->o_W2, H, m->ws.p, m->err.p, st,
+                 m->spin);
+    colsum(m, m->dZf.p, nullptr, Bp, H, g + m->o_b2, st);
     transpose(m->W2b.p, H, H, m->WT.p, st);
     launch_gemm(EPI_DSILU, m->dZbuf.p, H, m->WT.p, H, Bp, H, H, nullptr, H, nullptr, m->Z1.p,
                 m->dZf.p, m->dZa.p, m->err.p, st, m->spin);
     // layer 1: dW1 = dZ1^T X (padded to kin columns), db1
     transpose(m->dZa.p, Bp, H, m->dZT.p, st);
     transpose(m->Xb.p, Bp, m->kin, m->XbT.p, st);
-    launch_gemm(EPI_F32, m->dZT.p, Bp, m->XbT.p, Bp, H, m->kin, Bp, m->gW1.p, m->kin, nullptr,
-                nullptr, nullptr, nullptr, m->err.p, st, m->spin);
+    launch_wgrad(m->dZT.p, Bp, m->XbT.p, Bp, H, m->kin, Bp, m->gW1.p, m->kin, m->ws.p, m->err.p,
+                 st, m->spin);
     k_copy_cols<<<(H * m->n_in + 255) / 256, 256, 0, st>>>(m->gW1.p, H, m->kin, m->n_in, g);
-    k_colsum<<<(H + 127) / 128, 128, 0, st>>>(m->dZf.p, Bp, H, g + m->o_b1);
+    colsum(m, m->dZf.p, nullptr, Bp, H, g + m->o_b1, st);
 }
 
 int refresh(lensed_mlp *m, cudaStream_t st)
@@ -617,7 +839,9 @@ extern "C" int lensed_mlp_create(int n_in, int hidden, int max_batch, lensed_mlp
         (rc = m->dZT.alloc(bh)) || (rc = m->Z1.alloc(bh)) || (rc = m->Z2.alloc(bh)) ||
         (rc = m->Z3.alloc(bh)) || (rc = m->dZf.alloc(bh)) || (rc = m->y.alloc(m->Bp)) ||
         (rc = m->dy.alloc(m->Bp)) || (rc = m->lossrow.alloc(m->Bp)) ||
-        (rc = m->gW1.alloc(H * m->kin)) || (rc = m->tmpcol.alloc(H)) || (rc = m->err.alloc(1))) {
+        (rc = m->gW1.alloc(H * m->kin)) || (rc = m->tmpcol.alloc(H)) || (rc = m->err.alloc(1)) ||
+        (rc = m->ws.alloc((size_t)kMaxSplit * H * std::max<size_t>(H, m->kin))) ||
+        (rc = m->part.alloc((size_t)kColParts * H))) {
         std::string msg = g_mlp_error;
         delete m;
         g_mlp_error = msg;
@@ -725,6 +949,47 @@ extern "C" int lensed_mlp_train_step(lensed_mlp *m, const float *X, const float 
     const int n = std::max(m->H * m->kin, m->H * m->H);
     k_refresh<<<(n + 255) / 256, 256, 0, st>>>(m->p.p, m->n_in, m->kin, m->H, m->W1b.p, m->W2b.p,
                                                 m->W3b.p);
+    MCUDA(cudaGetLastError());
+    return LENSED_OK;
+}
+
+extern "C" int lensed_mlp_screen_ellipsoid(lensed_mlp *m, int d, int n, unsigned long long seed,
+                                           unsigned long long first, const float *center,
+                                           const float *chol, const float *shift,
+                                           const float *x_center, const float *x_whiten,
+                                           float y_cut, double *u_out, int *idx_out, int *n_out,
+                                           void *stream)
+{
+    if (d < 1 || d > kMaxScreenDim) return mfail(LENSED_E_ARG, "d = %d (1..%d)", d, kMaxScreenDim);
+    if (n < 0) return mfail(LENSED_E_ARG, "n = %d", n);
+    if (!center || !chol || !u_out || !idx_out || !n_out) return mfail(LENSED_E_ARG, "NULL argument");
+    if (m && (m->n_in != d || !x_center || !x_whiten))
+        return mfail(LENSED_E_ARG, "the network takes %d inputs and needs x_center, x_whiten",
+                     m->n_in);
+    cudaStream_t st = (cudaStream_t)stream;
+    MCUDA(cudaMemsetAsync(n_out, 0, sizeof(int), st));
+    if (n == 0) return LENSED_OK;
+    const int threads = 128, blocks = (n + threads - 1) / threads;
+    if (!m) {
+        k_ell_select<<<blocks, threads, 0, st>>>(d, n, seed, first, center, chol, shift, nullptr,
+                                                 nullptr, 0.f, u_out, idx_out, n_out);
+        MCUDA(cudaGetLastError());
+        return LENSED_OK;
+    }
+    if (m->sy.n < (size_t)n) {
+        MCUDA(cudaStreamSynchronize(st));
+        int rc;
+        if ((rc = m->sX.alloc((size_t)n * d)) || (rc = m->sy.alloc(n)) || (rc = m->sin.alloc(n)))
+            return rc;
+    }
+    k_ell_draw<<<blocks, threads, 0, st>>>(d, n, seed, first, center, chol, shift, x_center,
+                                           x_whiten, m->sX.p, m->sin.p);
+    for (int b0 = 0; b0 < n; b0 += m->maxB) {
+        const int nb = std::min(m->maxB, n - b0);
+        forward(m, m->sX.p + (size_t)b0 * d, nb, m->sy.p + b0, false, st);
+    }
+    k_ell_select<<<blocks, threads, 0, st>>>(d, n, seed, first, center, chol, shift, m->sin.p,
+                                             m->sy.p, y_cut, u_out, idx_out, n_out);
     MCUDA(cudaGetLastError());
     return LENSED_OK;
 }

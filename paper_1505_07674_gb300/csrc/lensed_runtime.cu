@@ -448,6 +448,10 @@ constexpr int kAllCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 constexpr int kBaseCandidates = 6;
 constexpr int kMinTraceItems = 64;  // smallest trace block of any candidate
 
+// Instantiated graphs kept per model (keyed by point count, buffers and
+// configuration; the least recently used is dropped beyond this).
+constexpr size_t kGraphCache = 32;
+
 // Second-pass queue entries per scratch chunk are capped at this many
 // (4 bytes each); blocks that find it full re-trace their rays themselves.
 constexpr long long kFfEntryCap = 64LL << 20;
@@ -1457,7 +1461,7 @@ static int run_batch(lensed_model *m, const double *params, int P, double *out, 
     for (auto &g : m->graphs)
         if (g.P == P && g.params == params && g.out == out && g.cfg == m->cfg_index) hit = &g;
     if (!hit) {
-        if (m->graphs.size() >= 8) {
+        if (m->graphs.size() >= kGraphCache) {
             auto old = std::min_element(m->graphs.begin(), m->graphs.end(),
                                         [](const GraphEntry &a, const GraphEntry &b) {
                                             return a.age < b.age;

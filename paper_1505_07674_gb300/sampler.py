@@ -54,15 +54,24 @@ class Result(dict):
 
 
 def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks=20,
-                    prescreen=None, max_evals=None, callback=None, on_round=None):
+                    prescreen=None, max_evals=None, callback=None, on_round=None,
+                    bounded=None, accept_target=0.4, screened_accept_target=None):
     """Run nested sampling.
 
     loglike(U) -> logL for a float64 array U [B, ndim] in the unit cube (one
     batched evaluation).  prescreen(U, threshold) -> boolean mask of the
     proposals worth an exact evaluation (or None); a pre-screen whose
     attribute `active` is False is skipped for that round.  on_round(live_u,
-    live_l, threshold) is called before each round's replacements.  Stops
-    when the live points can add at most dlogz to log Z (or after max_evals
+    live_l, threshold) is called before each round's replacements.
+    bounded(live_u, live_l, threshold, k) -> (U [m], logL [m], exact
+    evaluations, proposals screened out) or None: independent draws from the
+    prior inside the contour L > threshold (m <= k of them) made some other
+    way (e.g. rejection from a bounding region); the walks replace the rest.
+    The walks' step scale adapts towards an acceptance of accept_target, or
+    of screened_accept_target in rounds where a pre-screen is active: a
+    proposal the screen rejects costs no exact evaluation, so larger steps
+    (more rejections, farther moves) are cheap there.  Stops when the live
+    points can add at most dlogz to log Z (or after max_evals
     evaluations)."""
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
@@ -105,22 +114,40 @@ def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks
             it += 1
         if on_round is not None:
             on_round(live_u[kept], live_l[kept], lstar)
-        # k constrained random walks from surviving points
+        # independent draws inside the contour, where a bounded sampler
+        # offers them; constrained random walks for the rest
+        n_b = 0
+        if bounded is not None:
+            got = bounded(live_u, live_l, lstar, k)
+            if got is not None:
+                bu, bl, be, bs = got
+                n_b = len(bu)
+                live_u[gone[:n_b]] = bu
+                live_l[gone[:n_b]] = bl
+                n_evals += be
+                n_screened += bs
+        if n_b == k:
+            if callback:
+                callback(it, n_evals, logz, lstar)
+            continue
+        gone = gone[n_b:]
+        kw = len(gone)
+        # kw constrained random walks from surviving points
         cov = np.cov(live_u[kept].T) + 1e-12 * np.eye(ndim)
         chol = np.linalg.cholesky(cov)
         screen = prescreen if (prescreen is not None and
                                getattr(prescreen, "active", True)) else None
-        start = kept[rng.integers(0, len(kept), size=k)]
+        start = kept[rng.integers(0, len(kept), size=kw)]
         cu, cl = live_u[start].copy(), live_l[start].copy()
         for _ in range(walks):
-            prop = cu + scale * rng.standard_normal((k, ndim)) @ chol.T
+            prop = cu + scale * rng.standard_normal((kw, ndim)) @ chol.T
             ok = np.all((prop > 0.0) & (prop < 1.0), axis=1)
             if screen is not None and ok.any():
                 idx = np.nonzero(ok)[0]
                 keep = np.asarray(screen(prop[idx], lstar), dtype=bool)
                 n_screened += int((~keep).sum())
                 ok[idx[~keep]] = False
-            acc = np.zeros(k, dtype=bool)
+            acc = np.zeros(kw, dtype=bool)
             if ok.any():
                 idx = np.nonzero(ok)[0]
                 pl = np.asarray(loglike(prop[idx]), dtype=np.float64)
@@ -130,9 +157,12 @@ def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks
                 cu[idx[good]] = prop[idx[good]]
                 cl[idx[good]] = pl[good]
             frac = acc.mean()
-            n_prop += k
+            n_prop += kw
             n_acc += int(acc.sum())
-            scale = min(max(scale * math.exp(frac - 0.4), 1e-4), 10.0)
+            target = (screened_accept_target if (screen is not None and
+                                                 screened_accept_target is not None)
+                      else accept_target)
+            scale = min(max(scale * math.exp(frac - target), 1e-4), 10.0)
         live_u[gone] = cu
         live_l[gone] = cl
         if callback:

@@ -64,3 +64,33 @@ def test_adam_first_step_moves_by_lr():
     m, v = np.zeros(4), np.zeros(4)
     M.adam_step(th, g, m, v, 1, 0.01)
     assert np.allclose(th, -0.01 * np.sign(g), rtol=1e-4)
+
+
+@pytest.mark.parametrize("seq", ["constant", "alternating", "random"])
+def test_adam_matches_explicit_moment_sums_over_many_steps(seq):
+    # Adam's moments after t steps are exponentially weighted sums of the
+    # gradients, m_t = (1-b1) sum_i b1^(t-i) g_i and v_t = (1-b2) sum_i
+    # b2^(t-i) g_i^2 (Kingma & Ba 2015, Sec. 3); the update uses them with
+    # the bias corrections 1 - b^t.  Written out as sums here (not as the
+    # reference's recurrence), over 12 steps, so a wrong decay, a swapped
+    # b / 1-b or a missing correction at t > 1 shows.  A constant gradient
+    # moves every step by lr sign(g) (m_t / (1-b1^t) = g, v_t / (1-b2^t) = g^2).
+    b1, b2, eps, lr, T = 0.9, 0.999, 1e-8, 0.01, 12
+    rng = np.random.default_rng(3)
+    if seq == "constant":
+        gs = [np.array([2.0, -0.5, 3e-3])] * T
+    elif seq == "alternating":
+        gs = [np.array([1.0, -2.0, 0.5]) * (-1) ** t for t in range(T)]
+    else:
+        gs = [rng.standard_normal(3) for _ in range(T)]
+    th, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    expect = np.zeros(3)
+    for t in range(1, T + 1):
+        M.adam_step(th, gs[t - 1], m, v, t, lr)
+        ms = (1 - b1) * sum(b1 ** (t - i) * gs[i - 1] for i in range(1, t + 1))
+        vs = (1 - b2) * sum(b2 ** (t - i) * gs[i - 1] ** 2 for i in range(1, t + 1))
+        expect -= lr * (ms / (1 - b1 ** t)) / (np.sqrt(vs / (1 - b2 ** t)) + eps)
+        assert np.allclose(m, ms, rtol=1e-13, atol=0) and np.allclose(v, vs, rtol=1e-13, atol=0)
+        assert np.allclose(th, expect, rtol=1e-12, atol=1e-15), (seq, t)
+    if seq == "constant":
+        assert np.allclose(th, -T * lr * np.sign(gs[0]), rtol=1e-4)
