@@ -534,18 +534,22 @@ def run_rules(args):
 
 def run_surrogate(args):
     """c5: wall time to the evidence estimate with the surrogate versus the
-    plain batched run (same seed).  Two surrogate modes: retrained online
-    during the run on its own exact evaluations (whitened inputs), and
+    plain batched run (same seed).  Runs: plain; online (the network
+    retrained during the run on its own recent exact evaluations screens the
+    walk proposals -- delayed acceptance -- and, once its held-out scatter is
+    small, the 65,536-candidate batches of the bounding-ellipsoid draws, its
+    cut calibrated so every live point passes); an audit of the online
+    screen (every proposal evaluated exactly anyway: what it would save and
+    how many points inside the contour it would wrongly drop); and a network
     trained once on the (parameters, logL) pairs of an earlier run (at most
-    2M).  In both the network is the first stage of delayed-acceptance walk
-    steps: proposals it rejects skip the exact evaluation; the exact
-    likelihood decides every accepted point."""
+    2M).  The exact likelihood decides every accepted point."""
     import torch
 
     import workloads as W
     from paper_1505_07674_gb300 import build as build_lib
     from paper_1505_07674_gb300 import lensed as LZ
-    from paper_1505_07674_gb300.posterior import GpuLikelihood, OnlineSurrogate, SurrogateScreen
+    from paper_1505_07674_gb300.posterior import (EllipsoidSampler, GpuLikelihood,
+                                                  OnlineSurrogate, SurrogateScreen)
     from paper_1505_07674_gb300.sampler import nested_sampling
 
     torch.cuda.set_device(0)
@@ -563,14 +567,24 @@ def run_surrogate(args):
     like = GpuLikelihood(m, spec)
     res = nested_sampling(like, like.ndim, args.live, seed=12, dlogz=0.1, max_evals=8_000_000)
     runs["plain"] = summary(res, like)
-    rec = GpuLikelihood(m, spec, record=True)
-    online = OnlineSurrogate(rec, rec.ndim)
-    res = nested_sampling(rec, rec.ndim, args.live, seed=12, dlogz=0.1, prescreen=online,
-                          on_round=online.on_round, max_evals=8_000_000)
-    runs["online_surrogate"] = summary(res, rec, {
-        "train_s": online.train_s, "screen_s": online.screen_s, "fits": len(online.fits),
-        "active_fits": int(sum(f[3] for f in online.fits)),
-        "last_rms_y": online.fits[-1][2] if online.fits else None})
+    for audit in (False, True):
+        rec = GpuLikelihood(m, spec, record=True)
+        online = OnlineSurrogate(rec, rec.ndim, forward_batch=65536)
+        ell = None if audit else EllipsoidSampler(rec, rec.ndim, screen=online, seed=12)
+        res = nested_sampling(rec, rec.ndim, args.live, seed=12, dlogz=0.1, prescreen=online,
+                              on_round=online.on_round, bounded=ell, max_evals=8_000_000,
+                              audit_prescreen=audit)
+        extra = {"train_s": online.train_s, "screen_s": online.screen_s,
+                 "fits": len(online.fits), "active_fits": int(sum(f[3] for f in online.fits)),
+                 "last_rms_y": online.fits[-1][2] if online.fits else None}
+        if audit:
+            extra.update(would_save=res["n_prescreened"], wrongly_screened=res["n_screen_false"])
+            runs["online_audit"] = summary(res, rec, extra)
+        else:
+            extra.update(ellipsoid_rounds=ell.rounds_used, ellipsoid_accepted=ell.n_accept,
+                         ellipsoid_exact=ell.n_exact, candidates=ell.n_candidates,
+                         ellipsoid_draw_s=ell.draw_s, audited=ell.n_audit, missed=ell.missed)
+            runs["online_surrogate"] = summary(res, rec, extra)
     # global surrogate from an earlier run's evaluations (seed 11)
     gen = GpuLikelihood(m, spec, record=True)
     t0 = time.perf_counter()

@@ -163,8 +163,8 @@ class OnlineSurrogate:
     first fit and whenever the held-out scatter exceeds `max_rms`."""
 
     def __init__(self, recorder: GpuLikelihood, ndim, hidden=256, retrain_every=12,
-                 window=150_000, min_pairs=20_000, steps=120, batch=8192, lr=1e-3,
-                 margin_sigmas=3.0, max_rms=0.3, seed=0, forward_batch=None):
+                 window=150_000, min_pairs=20_000, steps=400, batch=8192, lr=1e-3,
+                 margin_sigmas=5.0, max_rms=0.3, seed=0, forward_batch=None):
         self.rec = recorder
         self.ndim = ndim
         # forward calls run in slices of the network's largest batch

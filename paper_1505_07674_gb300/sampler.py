@@ -55,7 +55,8 @@ class Result(dict):
 
 def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks=20,
                     prescreen=None, max_evals=None, callback=None, on_round=None,
-                    bounded=None, accept_target=0.4, screened_accept_target=None):
+                    bounded=None, accept_target=0.4, screened_accept_target=None,
+                    audit_prescreen=False):
     """Run nested sampling.
 
     loglike(U) -> logL for a float64 array U [B, ndim] in the unit cube (one
@@ -70,8 +71,12 @@ def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks
     The walks' step scale adapts towards an acceptance of accept_target, or
     of screened_accept_target in rounds where a pre-screen is active: a
     proposal the screen rejects costs no exact evaluation, so larger steps
-    (more rejections, farther moves) are cheap there.  Stops when the live
-    points can add at most dlogz to log Z (or after max_evals
+    (more rejections, farther moves) are cheap there.  With audit_prescreen
+    the screen's verdicts are only recorded: every proposal is still
+    evaluated exactly and decided by the exact value (the plain run), and
+    n_prescreened / n_screen_false count the proposals the screen would
+    have dropped and those of them that lie inside the contour.  Stops when
+    the live points can add at most dlogz to log Z (or after max_evals
     evaluations)."""
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
@@ -80,6 +85,7 @@ def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks
     live_u = rng.random((N, ndim))
     live_l = np.asarray(loglike(live_u), dtype=np.float64)
     n_evals, n_screened, n_prop, n_acc = N, 0, 0, 0
+    n_false = 0
     dead_u, dead_l, dead_logw = [], [], []
     logz, info, logx = -np.inf, 0.0, 0.0
     scale = 1.0
@@ -142,17 +148,24 @@ def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks
         for _ in range(walks):
             prop = cu + scale * rng.standard_normal((kw, ndim)) @ chol.T
             ok = np.all((prop > 0.0) & (prop < 1.0), axis=1)
+            dropped = None
             if screen is not None and ok.any():
                 idx = np.nonzero(ok)[0]
                 keep = np.asarray(screen(prop[idx], lstar), dtype=bool)
                 n_screened += int((~keep).sum())
-                ok[idx[~keep]] = False
+                if audit_prescreen:
+                    dropped = np.zeros(kw, dtype=bool)
+                    dropped[idx[~keep]] = True
+                else:
+                    ok[idx[~keep]] = False
             acc = np.zeros(kw, dtype=bool)
             if ok.any():
                 idx = np.nonzero(ok)[0]
                 pl = np.asarray(loglike(prop[idx]), dtype=np.float64)
                 n_evals += len(idx)
                 good = pl > lstar
+                if dropped is not None:
+                    n_false += int((good & dropped[idx]).sum())
                 acc[idx[good]] = True
                 cu[idx[good]] = prop[idx[good]]
                 cl[idx[good]] = pl[good]
@@ -177,4 +190,5 @@ def nested_sampling(loglike, ndim, n_live, seed=0, dlogz=0.1, k_frac=0.25, walks
     return Result(logz=float(logz), logz_err=float(math.sqrt(max(info, 0.0) / N)),
                   information=float(info), n_evals=int(n_evals), n_iter=it, samples=samples,
                   logl=logl, logwt=logw + logl - logz, wall_s=time.perf_counter() - t0,
-                  n_prescreened=n_screened, accept=n_acc / max(n_prop, 1))
+                  n_prescreened=n_screened, n_screen_false=n_false,
+                  accept=n_acc / max(n_prop, 1))
