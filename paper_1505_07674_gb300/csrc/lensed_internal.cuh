@@ -69,6 +69,11 @@ struct SysDev {
     long long pre_off;      // into the precomputed luminosity table, -1 if none
     int psf_rank;           // > 0: the PSF is applied as a sum of psf_rank separable terms
     int psf_sep_off;        // into the float PSF table: per term, column then row factor
+    // the pixel weights are stored relative to this per-system scale (their
+    // largest value), which multiplies the chi^2 in FP64 at the end: a
+    // uniform weight is then exactly 1 in float, and the float rounding of
+    // the weights cannot bias the whole log-likelihood coherently
+    double wscale;
 };
 
 // Trace-kernel block table entry: system and the range [start, end) of its

@@ -172,7 +172,9 @@ __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__res
         // 8 s^2, 9 s, 10 q^2 s, 11 e, 12 e_lo, 13 pref, 14 pref_lo,
         // 15 series flag, 16 e^2, 17 FP64 flag (MIXED, e < 0.05),
         // 18 (2 s / q)^2: pixels whose square comes inside this radius of
-        // the lens centre take the FP64 branch in MIXED
+        // the lens centre take the FP64 branch in MIXED;
+        // 19 x0_lo, 20 y0_lo, 21 s^2_lo, 22 s_lo, 23 q^2 s_lo (the float-float
+        // re-trace reads every constant as a pair)
         const double b = v[2], q = v[3], sc = v[5];
         ok = ok && q > 0.0 && q <= 1.0 && b >= 0.0 && sc >= 0.0;
         double sn, cs;
@@ -197,16 +199,28 @@ __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__res
         lo[6] = 7;
         lo[11] = 12;
         lo[13] = 14;
+        lo[0] = 19;
+        lo[1] = 20;
+        lo[8] = 21;
+        lo[9] = 22;
+        lo[10] = 23;
     } else if (type == LENSED_SHEAR) {
-        // 0 x0, 1 y0, 2 gamma_1, 3 gamma_2
+        // 0 x0, 1 y0, 2 gamma_1, 3 gamma_2; 4-7 their residuals
         double sn, cs;
         sincospi(v[3] / 90.0, &sn, &cs);  // 2 phi
         o[2] = v[2] * cs;
         o[3] = v[2] * sn;
+        lo[0] = 4;
+        lo[1] = 5;
+        lo[2] = 6;
+        lo[3] = 7;
     } else if (type == LENSED_POINTMASS) {
-        // 0 x0, 1 y0, 2 theta_E^2
+        // 0 x0, 1 y0, 2 theta_E^2; 3-5 their residuals
         ok = ok && v[2] >= 0.0;
         o[2] = v[2] * v[2];
+        lo[0] = 3;
+        lo[1] = 4;
+        lo[2] = 5;
     } else if (type == LENSED_SKY) {
         // flat sky (Sec. 5): 13 A = S h^2, 14 A_lo, 15 kind; no position
         o[0] = 0.0;
@@ -219,7 +233,7 @@ __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__res
         // Gaussian (x y sigma mag q pa).
         // 0 x0, 1 y0, 2 cos, 3 sin, 4 cos_lo, 5 sin_lo, 6 q/r^2, 7 1/(q r^2),
         // 8 q/r^2 lo, 9 1/(q r^2) lo, 10 p2, 11 B, 12 B_lo, 13 A, 14 A_lo,
-        // 15 kind.  rho^2 = (q u^2 + v^2/q)/r^2; Sersic t = B rho^(2 p2) with
+        // 15 kind, 16 x0_lo, 17 y0_lo.  rho^2 = (q u^2 + v^2/q)/r^2; Sersic t = B rho^(2 p2) with
         // B = b_n log2(e), p2 = 1/(2n); Gaussian (r = sqrt(2) sigma) t =
         // B rho^2 with B = log2(e); I = A 2^-t with A = I_0 h^2.
         const double r = v[2];
@@ -238,6 +252,8 @@ __global__ void k_prologue_comp(const SysDev *__restrict__ sys, const int *__res
         lo[7] = 9;
         lo[11] = 12;
         lo[13] = 14;
+        lo[0] = 16;
+        lo[1] = 17;
         if (ok && type == LENSED_GAUSS) {
             const double r2 = 2.0 * r * r;
             o[6] = q / r2;
@@ -406,6 +422,62 @@ __device__ __forceinline__ float light_any_f32(const LightF &k, float x, float y
     return k.kind == (float)kKindFlat ? k.A : light_f32(k, x, y);
 }
 
+// The parts of a rotation into a component's frame that depend on the row
+// coordinate alone, dy = y - y0 (shared by the G rays of a node row):
+// du = dy sin(PA), dv = dy cos(PA), each compensated like the per-ray terms.
+struct RowTerms {
+    float du, dv;
+};
+__device__ __forceinline__ RowTerms row_terms(float y, float y0, float cs, float sn, float csl,
+                                              float snl)
+{
+    const float dy = y - y0;
+    return {fmaf(dy, sn, dy * snl), fmaf(dy, cs, dy * csl)};
+}
+
+// sie_f32 for a ray of the row whose terms are R (same arithmetic, the row's
+// products computed once)
+__device__ __forceinline__ void sie_f32_row(const SieF &k, const RowTerms &R, float x, float &ax,
+                                            float &ay)
+{
+    const float dx = x - k.x0;
+    const float u = fmaf(dx, k.cs, fmaf(dx, k.csl, R.du));
+    const float v = fmaf(-dx, k.sn, fmaf(-dx, k.snl, R.dv));
+    const float w = fmaf(u, u, k.s2);
+    const float psi2 = fmaf(k.q2, w, fmaf(k.q2l, w, v * v));
+    const float psi = psi2 > 0.f ? psi2 * rsqrtf(psi2) : 0.f;
+    const float du = psi + k.s, dv = psi + k.q2s;
+    const float zu = du > 0.f ? __fdividef(u, du) : 0.f;
+    const float zv = du > 0.f ? __fdividef(v, dv) : 0.f;
+    float A1, A2;
+    if (k.series != 0.f) {
+        const float zu2 = zu * zu, zv2 = zv * zv;
+        A1 = zu * (1.f - k.e2 * zu2 * (1.f / 3.f) + k.e2 * k.e2 * zu2 * zu2 * 0.2f);
+        A2 = zv * (1.f + k.e2 * zv2 * (1.f / 3.f) + k.e2 * k.e2 * zv2 * zv2 * 0.2f);
+    } else {
+        A1 = atanf(fmaf(k.e, zu, k.el * zu));
+        A2 = atanhf(fmaf(k.e, zv, k.el * zv));
+    }
+    const float au = fmaf(k.pref, A1, k.prefl * A1);
+    const float av = fmaf(k.pref, A2, k.prefl * A2);
+    ax += fmaf(au, k.cs, fmaf(-av, k.sn, fmaf(au, k.csl, -av * k.snl)));
+    ay += fmaf(au, k.sn, fmaf(av, k.cs, fmaf(au, k.snl, av * k.csl)));
+}
+
+// light_f32 for a ray of the row whose terms are R
+__device__ __forceinline__ float light_f32_row(const LightF &k, const RowTerms &R, float x)
+{
+    const float dx = x - k.x0;
+    const float u = fmaf(dx, k.cs, fmaf(dx, k.csl, R.du));
+    const float v = fmaf(-dx, k.sn, fmaf(-dx, k.snl, R.dv));
+    const float uu = u * u, vv = v * v;
+    const float rho2 = fmaf(k.qr, uu, fmaf(k.iqr, vv, fmaf(k.qrl, uu, k.iqrl * vv)));
+    const float f = (k.kind == (float)kKindGauss) ? rho2 : ex2f(k.p2 * lg2f(rho2));
+    const float t = fmaf(k.B, f, k.Bl * f);
+    const float g = ex2f(-t);
+    return fmaf(k.A, g, k.Al * g);
+}
+
 // FP64 SIE of one ray in a MIXED evaluation.  Out of line, so that none of
 // its double-precision arithmetic is scheduled on the FP32 path; the ray
 // position is rebuilt in FP64 from the pixel index and the FP64 node offsets.
@@ -494,8 +566,11 @@ __global__ void k_prologue_valid(const SysDev *__restrict__ sys, int s0, int nS,
             if (!isfinite(yx) || !isfinite(yy)) ok = 0;
             cc[0] = yx;
             cc[1] = yy;
-            cf[base + (size_t)c * kNC + 0] = (float)yx;
-            cf[base + (size_t)c * kNC + 1] = (float)yy;
+            float *fc = cf + base + (size_t)c * kNC;
+            fc[0] = (float)yx;
+            fc[1] = (float)yy;
+            fc[16] = (float)(yx - (double)fc[0]);
+            fc[17] = (float)(yy - (double)fc[1]);
         }
     }
     valid[(size_t)s * P + p] = ok;
@@ -526,7 +601,6 @@ void launch_prologue(const SysDev *sys, const int *comp_sys, int s0, int nS, int
 struct TraceSmem {
     float cf[LENSED_MAX_COMPONENTS * kNC];
     double cd[LENSED_MAX_COMPONENTS * kNC];
-    float ch[LENSED_MAX_COMPONENTS * kNC], cl[LENSED_MAX_COMPONENTS * kNC];  // cd as float pairs
     float uh[LENSED_MAX_RULE_ORDER], ul[LENSED_MAX_RULE_ORDER];            // ud as float pairs
     int type[LENSED_MAX_COMPONENTS], plane[LENSED_MAX_COMPONENTS];
     float u[LENSED_MAX_RULE_ORDER];
@@ -543,12 +617,7 @@ __device__ __forceinline__ void stage_point(TraceSmem &sm, const SysDev &S, cons
     const int ncomp = S.ncomp, nn = S.nn;
     for (int k = threadIdx.x; k < ncomp * kNC; k += blockDim.x) {
         sm.cf[k] = cf[cbase + k];
-        if (need_f64) {
-            const double v = cd[cbase + k];
-            sm.cd[k] = v;
-            sm.ch[k] = (float)v;
-            sm.cl[k] = (float)(v - (double)(float)v);
-        }
+        if (need_f64) sm.cd[k] = cd[cbase + k];
     }
     for (int k = threadIdx.x; k < ncomp; k += blockDim.x) {
         sm.type[k] = comp_type[S.comp_off + k];
@@ -611,26 +680,44 @@ __device__ __forceinline__ ff ff_mulf(ff x, float f)
     return ff_quick(p, fmaf(x.lo, f, e));
 }
 __device__ __forceinline__ ff ff_addf(ff x, float f) { return ff_add(x, ff{f, 0.f}); }
-// x / y for y != 0: three quotient digits, each from the exact remainder
+// MUFU approximate reciprocal and reciprocal square root (rcp.approx /
+// rsqrt.approx, ~22 correct bits): the float-float operations below start
+// from them and recover the remaining digits from exact remainders.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// x / y for y != 0: two quotient digits, the second from the exact
+// remainder x - y q1 (relative error ~2^-44, far below what the re-trace
+// needs: positions to ~1e-10 arcsec)
 __device__ __forceinline__ ff ff_div(ff x, ff y)
 {
-    const float r = 1.f / y.hi;
+    const float r = rcp_approx(y.hi);
     const float q1 = x.hi * r;
-    ff rem = ff_sub(x, ff_mulf(y, q1));
+    const ff rem = ff_sub(x, ff_mulf(y, q1));
     const float q2 = rem.hi * r;
-    rem = ff_sub(rem, ff_mulf(y, q2));
-    const float q3 = rem.hi * r;
-    return ff_addf(ff_quick(q1, q2), q3);
+    return ff_quick(q1, q2);
 }
-// sqrt(x) for x >= 0: float root, then one correction from the exact residual
+// sqrt(x) for x >= 0: approximate root, then one Newton correction from the
+// exact residual x - s^2 (quadratic: ~2^-44)
 __device__ __forceinline__ ff ff_sqrt(ff x)
 {
     if (!(x.hi > 0.f)) return {0.f, 0.f};
-    const float s = sqrtf(x.hi);
+    const float rs = rsqrt_approx(x.hi);
+    const float s = x.hi * rs;
     const float p = s * s;
     const ff sq{p, fmaf(s, s, -p)};
     const ff d = ff_sub(x, sq);
-    return ff_quick(s, d.hi / (2.f * s));
+    return ff_quick(s, d.hi * (0.5f * rs));
 }
 
 // tan(k/16), k = 0..26, and tanh(k/16), k = 0..127, as float pairs (computed
@@ -639,38 +726,47 @@ __constant__ float kTan16[27][2];
 __constant__ float kTanh16[128][2];
 
 // atan(t) = k/16 + atan(w), w = (t - tan(k/16)) / (1 + t tan(k/16)), k the
-// nearest multiple of 1/16 to atan(t), so |w| <= tan(1/32) and the series
-// w - w^3/3 + w^5/5 - w^7/7 leaves < 1e-13; its tail after w is applied in
-// float.  Odd in t.
+// multiple of 1/16 nearest to an estimate of atan(t) (t / (1 + 0.28 t^2),
+// or pi/2 minus that of 1/t beyond 1; error < 0.005), so |w| <= tan(1/32 +
+// 0.005) and the series w - w^3/3 + w^5/5 - w^7/7 + w^9/9 leaves < 1e-15;
+// its tail after w is applied in float.  Odd in t.
 __device__ __forceinline__ ff ff_atan(ff t)
 {
     const bool neg = t.hi < 0.f;
     if (neg) t = ff_neg(t);
-    const int k = min(max(__float2int_rn(16.f * atanf(t.hi)), 0), 26);
+    const float a = t.hi;
+    const float est = a <= 1.f ? a * rcp_approx(fmaf(0.28f, a * a, 1.f))
+                               : 1.5707964f - a * rcp_approx(fmaf(a, a, 0.28f));
+    const int k = min(max(__float2int_rn(16.f * est), 0), 26);
     const ff c{kTan16[k][0], kTan16[k][1]};
     const ff w = ff_div(ff_sub(t, c), ff_addf(ff_mul(t, c), 1.f));
     const float s = w.hi * w.hi;
-    const float tail = w.hi * s * fmaf(s, fmaf(s, -1.f / 7.f, 0.2f), -1.f / 3.f);
+    const float tail = w.hi * s * fmaf(s, fmaf(s, fmaf(s, 1.f / 9.f, -1.f / 7.f), 0.2f), -1.f / 3.f);
     ff r = ff_addf(ff_add(ff{k * 0.0625f, 0.f}, w), tail);
     return neg ? ff_neg(r) : r;
 }
 
 // atanh(z), |z| < 1: the same reduction with tanh(k/16) and
-// w = (z - tanh(k/16)) / (1 - z tanh(k/16)); series w + w^3/3 + w^5/5 + w^7/7.
+// w = (z - tanh(k/16)) / (1 - z tanh(k/16)), k from the estimate
+// (ln 2 / 2)(lg2(1 + z) - lg2(1 - z)); series w + w^3/3 + ... + w^9/9.
 __device__ __forceinline__ ff ff_atanh(ff z)
 {
     const bool neg = z.hi < 0.f;
     if (neg) z = ff_neg(z);
-    const int k = min(max(__float2int_rn(16.f * atanhf(fminf(z.hi, 0.99999994f))), 0), 127);
+    const float a = fminf(z.hi, 0.99999994f);
+    const float est = 0.34657359f * (lg2f(1.f + a) - lg2f(1.f - a));
+    const int k = min(max(__float2int_rn(16.f * est), 0), 127);
     const ff c{kTanh16[k][0], kTanh16[k][1]};
     const ff w = ff_div(ff_sub(z, c), ff_add(ff{1.f, 0.f}, ff_neg(ff_mul(z, c))));
     const float s = w.hi * w.hi;
-    const float tail = w.hi * s * fmaf(s, fmaf(s, 1.f / 7.f, 0.2f), 1.f / 3.f);
+    const float tail = w.hi * s * fmaf(s, fmaf(s, fmaf(s, 1.f / 9.f, 1.f / 7.f), 0.2f), 1.f / 3.f);
     ff r = ff_addf(ff_add(ff{k * 0.0625f, 0.f}, w), tail);
     return neg ? ff_neg(r) : r;
 }
 
-__device__ __forceinline__ ff ff_const(const TraceSmem &sm, int idx) { return {sm.ch[idx], sm.cl[idx]}; }
+// A packed constant as a float pair: its FP32 value and the residual the
+// prologue stored in slot `lo` of the same component.
+__device__ __forceinline__ ff ff_pair(const float *c, int hi, int lo) { return {c[hi], c[lo]}; }
 
 // FP32 light profile at a given offset (dx, dy) from its centre.
 __device__ __forceinline__ float light_f32_at(const LightF &k, float dx, float dy)
@@ -686,7 +782,9 @@ __device__ __forceinline__ float light_f32_at(const LightF &k, float dx, float d
 }
 
 // Source-plane brightness of ray (a, b) of pixel (jc, ic) with the lens
-// equation in float-float (all lens components), the light in FP32.
+// equation in float-float (all lens components), the light in FP32.  Every
+// constant comes as a float pair from the component's packed FP32 block
+// (value and residual slots, see k_prologue_comp).
 __device__ __noinline__ float source_brightness_ff(const TraceSmem &sm, int ncomp, float jc,
                                                    float ic, float h, float h_lo, int a, int b)
 {
@@ -698,42 +796,45 @@ __device__ __noinline__ float source_brightness_ff(const TraceSmem &sm, int ncom
     ff ax{0.f, 0.f}, ay{0.f, 0.f};
     for (int c = 0; c < ncomp; ++c) {
         if (sm.plane[c] != LENSED_PLANE_LENS) continue;
-        const int o = c * kNC, t = sm.type[c];
-        const ff dx = ff_sub(x, ff_const(sm, o + 0)), dy = ff_sub(y, ff_const(sm, o + 1));
+        const float *k = sm.cf + c * kNC;
+        const int t = sm.type[c];
         if (t == LENSED_SIE) {
-            const ff cs = ff_const(sm, o + 2), sn = ff_const(sm, o + 3);
+            const ff dx = ff_sub(x, ff_pair(k, 0, 19)), dy = ff_sub(y, ff_pair(k, 1, 20));
+            const ff cs = ff_pair(k, 2, 4), sn = ff_pair(k, 3, 5);
             const ff u = ff_add(ff_mul(dx, cs), ff_mul(dy, sn));
             const ff v = ff_sub(ff_mul(dy, cs), ff_mul(dx, sn));
-            const ff psi = ff_sqrt(ff_add(ff_mul(ff_const(sm, o + 6),
-                                                 ff_add(ff_const(sm, o + 8), ff_mul(u, u))),
+            const ff psi = ff_sqrt(ff_add(ff_mul(ff_pair(k, 6, 7),
+                                                 ff_add(ff_pair(k, 8, 21), ff_mul(u, u))),
                                           ff_mul(v, v)));
-            const ff du = ff_add(psi, ff_const(sm, o + 9));
-            const ff dv = ff_add(psi, ff_const(sm, o + 10));
+            const ff du = ff_add(psi, ff_pair(k, 9, 22));
+            const ff dv = ff_add(psi, ff_pair(k, 10, 23));
             if (!(du.hi > 0.f)) continue;  // exact centre of a coreless SIE
             ff A1, A2;
-            if (sm.cd[o + 15] != 0.0) {
+            if (k[15] != 0.f) {
                 const ff zu = ff_div(u, du), zv = ff_div(v, dv);
-                const float e2 = sm.ch[o + 16];
+                const float e2 = k[16];
                 const float su = e2 * zu.hi * zu.hi, sv = e2 * zv.hi * zv.hi;
                 A1 = ff_addf(zu, zu.hi * su * fmaf(su, 0.2f, -1.f / 3.f));
                 A2 = ff_addf(zv, zv.hi * sv * fmaf(sv, 0.2f, 1.f / 3.f));
             } else {
-                const ff e = ff_const(sm, o + 11);
+                const ff e = ff_pair(k, 11, 12);
                 A1 = ff_atan(ff_div(ff_mul(e, u), du));
                 A2 = ff_atanh(ff_div(ff_mul(e, v), dv));
             }
-            const ff pref = ff_const(sm, o + 13);
+            const ff pref = ff_pair(k, 13, 14);
             const ff au = ff_mul(pref, A1), av = ff_mul(pref, A2);
             ax = ff_add(ax, ff_sub(ff_mul(au, cs), ff_mul(av, sn)));
             ay = ff_add(ay, ff_add(ff_mul(au, sn), ff_mul(av, cs)));
         } else if (t == LENSED_SHEAR) {
-            const ff g1 = ff_const(sm, o + 2), g2 = ff_const(sm, o + 3);
+            const ff dx = ff_sub(x, ff_pair(k, 0, 4)), dy = ff_sub(y, ff_pair(k, 1, 5));
+            const ff g1 = ff_pair(k, 2, 6), g2 = ff_pair(k, 3, 7);
             ax = ff_add(ax, ff_add(ff_mul(g1, dx), ff_mul(g2, dy)));
             ay = ff_add(ay, ff_sub(ff_mul(g2, dx), ff_mul(g1, dy)));
         } else {
+            const ff dx = ff_sub(x, ff_pair(k, 0, 3)), dy = ff_sub(y, ff_pair(k, 1, 4));
             const ff r2 = ff_add(ff_mul(dx, dx), ff_mul(dy, dy));
             if (!(r2.hi > 0.f)) continue;
-            const ff f = ff_div(ff_const(sm, o + 2), r2);
+            const ff f = ff_div(ff_pair(k, 2, 5), r2);
             ax = ff_add(ax, ff_mul(f, dx));
             ay = ff_add(ay, ff_mul(f, dy));
         }
@@ -742,13 +843,13 @@ __device__ __noinline__ float source_brightness_ff(const TraceSmem &sm, int ncom
     float I = 0.f;
     for (int c = 0; c < ncomp; ++c) {
         if (sm.plane[c] != LENSED_PLANE_SOURCE) continue;
-        const int o = c * kNC;
-        const LightF L = load_light(sm.cf + o);
+        const float *k = sm.cf + c * kNC;
+        const LightF L = load_light(k);
         if (L.kind == (float)kKindFlat) {
             I += L.A;
             continue;
         }
-        const ff ox = ff_sub(sx, ff_const(sm, o + 0)), oy = ff_sub(sy, ff_const(sm, o + 1));
+        const ff ox = ff_sub(sx, ff_pair(k, 0, 16)), oy = ff_sub(sy, ff_pair(k, 1, 17));
         I += light_f32_at(L, ox.hi + ox.lo, oy.hi + oy.lo);
     }
     return I;
@@ -801,8 +902,7 @@ __global__ void __launch_bounds__(256)
     __shared__ unsigned short q_t[kQueue ? kQCap : 1];
     __shared__ unsigned char q_r[kQueue ? kQCap : 1];
     __shared__ float q_v[kQueue ? kQCap : 1];
-    stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, MODE == LENSED_PREC_MIXED_FF, false,
-                nodes);
+    stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, false, false, nodes);
     if (kQueue && threadIdx.x == 0) q_n = 0;
     __syncthreads();
 
@@ -843,15 +943,17 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
                         for (int k = 0; k < G; ++k) I[k] += L.A;
                     } else {
+                        const RowTerms R = row_terms(y, L.y0, L.cs, L.sn, L.csl, L.snl);
 #pragma unroll
-                        for (int k = 0; k < G; ++k) I[k] += light_f32(L, xk[k], y);
+                        for (int k = 0; k < G; ++k) I[k] += light_f32_row(L, R, xk[k]);
                     }
                 } else if (pl == LENSED_PLANE_LENS) {
                     const int t = sm.type[c];
                     if (t == LENSED_SIE) {
                         const SieF K = load_sie(cc);
+                        const RowTerms R = row_terms(y, K.y0, K.cs, K.sn, K.csl, K.snl);
 #pragma unroll
-                        for (int k = 0; k < G; ++k) sie_f32(K, xk[k], y, ax[k], ay[k]);
+                        for (int k = 0; k < G; ++k) sie_f32_row(K, R, xk[k], ax[k], ay[k]);
                     } else if (t == LENSED_SHEAR) {
                         const float x0 = cc[0], y0 = cc[1], g1 = cc[2], g2 = cc[3];
 #pragma unroll
@@ -1014,7 +1116,7 @@ __global__ void __launch_bounds__(kFfThreads)
         const FfHeader H = fq.hdr[h];
         const SysDev &S = sys[H.sys];
         const size_t cbase = ((size_t)H.p * C_total + S.comp_off) * kNC;
-        stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, true, false, nodes);
+        stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, false, false, nodes);
         const int n = min(H.n, kQCap);
         for (int e = threadIdx.x; e < n; e += blockDim.x) q_e[e] = fq.ent[H.base + e];
         __syncthreads();
@@ -1805,7 +1907,7 @@ __global__ void k_finalize(const SysDev *__restrict__ sys, const unsigned char *
         double t = 0.0;
         const double *row = partial + (size_t)p * T_total + S.tile_off;
         for (int k = 0; k < S.n_tiles; ++k) t += row[k];
-        v = -0.5 * t;
+        v = -0.5 * (S.wscale * t);  // the partials use the relative weights
     }
     out[(size_t)s * P + p] = v;
 }

@@ -548,6 +548,15 @@ struct lensed_model {
         return {ffq_cnt.p, ffq_hdr.p, ffq_ent.p, (long long)ffq_hdr.n, (long long)ffq_ent.n};
     }
     size_t elem() const { return precision == LENSED_PREC_FP64 ? sizeof(double) : sizeof(float); }
+    // FP32 modes with fixed lights: the chi^2 path traces without them and
+    // compares with data from which their convolved image was removed
+    bool fold_fixed = false;
+    NodeTables nodes_chi() const
+    {
+        NodeTables n = nodes();
+        if (fold_fixed) n.pre_f = nullptr;
+        return n;
+    }
     NodeTables nodes() const
     {
         return {node_u.p, node_w.p, node_ud.p, node_wd.p, pre_f.p, pre_d.p,
@@ -686,11 +695,11 @@ void enqueue_batch(lensed_model *m, const double *params, int P, double *out, La
         for (const TraceGroup &g : m->trace_groups)
             launch_trace(m->precision, cfg, g.nn, m->sys.p, m->comp_type.p, m->comp_plane.p,
                          m->cf.p, m->cd.p, m->valid.p, P, m->C_total, m->trace_blocks.p + g.off,
-                         g.count, m->need.p, m->nodes(), p0, nP, m->Lbuf.p, m->total_pix, st,
+                         g.count, m->need.p, m->nodes_chi(), p0, nP, m->Lbuf.p, m->total_pix, st,
                          m->ffq());
         if (is_mixed(m->precision))
             launch_fix64(cfg, m->sys.p, 0, m->n_sys, m->comp_type.p, m->comp_plane.p, m->cf.p,
-                         m->cd.p, m->valid.p, P, m->C_total, m->need.p, m->nodes(), p0, nP,
+                         m->cd.p, m->valid.p, P, m->C_total, m->need.p, m->nodes_chi(), p0, nP,
                          m->Lbuf.p, m->total_pix, st);
         if (tm) tm->end();
         if (tm) tm->begin(2);
@@ -805,7 +814,30 @@ static int psf_low_rank(const double *F, int m, int n, std::vector<double> &c,
 // all fixed (device plane kPlanePrecomputed): every evaluation starts each
 // pixel's sum from them instead of tracing those components again.  For a
 // Gauss-Kronrod system the embedded Gauss rule gets a table of its own.
-static int precompute_fixed_light(lensed_model *m, const std::vector<int> &cplane_pre)
+// Eq. 15 on the host in FP64, with the kernels' indexing: L*_ij =
+// sum_kl Fs[k][l] L[clamp(i + k - p)][clamp(j + l - q)], Fs the stored
+// (flipped, unit-sum) PSF of the system.
+static void convolve_host(const SysDev &S, const double *L, const double *Fs, double *out)
+{
+    const int p = S.psf_p, q = S.psf_q, W = 2 * q + 1;
+    for (int i = 0; i < S.ny; ++i)
+        for (int j = 0; j < S.nx; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k <= 2 * p; ++k) {
+                const int gi = std::min(std::max(i + k - p, 0), S.ny - 1);
+                for (int l = 0; l < W; ++l) {
+                    const int gj = std::min(std::max(j + l - q, 0), S.nx - 1);
+                    acc += Fs[k * W + l] * L[(size_t)gi * S.nx + gj];
+                }
+            }
+            out[(size_t)i * S.nx + j] = acc;
+        }
+}
+
+static int precompute_fixed_light(lensed_model *m, const std::vector<int> &cplane_pre,
+                                  const std::vector<double> &data_d,
+                                  const std::vector<double> &psf_d,
+                                  const std::vector<size_t> &psfd_off)
 {
     bool any = false;
     for (auto &S : m->sys_h) any |= S.pre_off >= 0;
@@ -840,6 +872,33 @@ static int precompute_fixed_light(lensed_model *m, const std::vector<int> &cplan
     CUDA_OK(cudaMemcpy(hd.data(), m->pre_d.p, sizeof(double) * 2 * T, cudaMemcpyDeviceToHost));
     std::vector<float> hf(hd.begin(), hd.end());
     if ((rc = m->pre_f.upload(hf))) return rc;
+    if (m->precision != LENSED_PREC_FP64) {
+        // FP32 modes: the chi^2 path leaves the fixed lights out of the float
+        // arithmetic.  Eq. 15 is linear, so L* = F * L_fixed + F * L_rest;
+        // the first term is the same for every point and is taken off the
+        // data here in FP64, the kernels convolve only the rest in float.
+        // (Renders still start from the fixed lights and convolve the sum.)
+        std::vector<float> dres(T);
+        std::vector<double> conv;
+        for (int s = 0; s < m->n_sys; ++s) {
+            const SysDev &S = m->sys_h[s];
+            const double *d = data_d.data() + S.pix_off;
+            float *o = dres.data() + S.pix_off;
+            if (S.pre_off < 0) {
+                for (int k = 0; k < S.npix; ++k) o[k] = (float)d[k];
+                continue;
+            }
+            const double *Lf = hd.data() + S.pix_off;
+            conv.assign(S.npix, 0.0);
+            if (S.psf_p > 0 || S.psf_q > 0)
+                convolve_host(S, Lf, psf_d.data() + psfd_off[s], conv.data());
+            else
+                std::copy(Lf, Lf + S.npix, conv.begin());
+            for (int k = 0; k < S.npix; ++k) o[k] = (float)(d[k] - conv[k]);
+        }
+        if ((rc = m->data.upload(dres))) return rc;
+        m->fold_fixed = true;
+    }
     // point the systems (and their Gauss shadows) at their tables
     for (int s = 0; s < m->n_sys; ++s) {
         if (m->sys_h[s].pre_off < 0) continue;
@@ -925,6 +984,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
     std::vector<double> cval;
     std::vector<float> data, weight, psf_f, node_u, node_w;
     std::vector<double> data_d, weight_d, psf_d, node_ud, node_wd;
+    std::vector<size_t> psfd_off(n_systems);
     std::vector<int> need;
     std::vector<std::vector<PsfBlock>> chi_tiles(n_systems);
     std::vector<int> need_count(n_systems), nn_v(n_systems), pp(n_systems), qq(n_systems),
@@ -970,13 +1030,18 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
             data.push_back((float)dv);
             data_d.push_back(dv);
         }
+        double wmax = 0.0;
+        for (int k = 0; k < npix; ++k) wmax = std::max(wmax, w[k]);
+        S.wscale = wmax > 0.0 ? wmax : 1.0;
         for (int k = 0; k < npix; ++k) {
-            weight.push_back((float)w[k]);
-            weight_d.push_back(w[k]);
+            const double rel = w[k] / S.wscale;
+            weight.push_back((float)rel);
+            weight_d.push_back(rel);
         }
         // PSF (Sec. 3.1): normalised to unit sum, stored flipped (F_{-k,-l})
         int P = 0, Q = 0;
         S.psf_off = (int)psf_f.size();
+        psfd_off[s] = psf_d.size();  // the FP64 table holds no separable factors
         if (d.psf) {
             P = d.psf_ny / 2;
             Q = d.psf_nx / 2;
@@ -1263,7 +1328,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         g_last_error = msg;
         return rc;
     }
-    if ((rc = precompute_fixed_light(m, cplane_pre))) {
+    if ((rc = precompute_fixed_light(m, cplane_pre, data_d, psf_d, psfd_off))) {
         std::string msg = g_last_error;
         delete m;
         g_last_error = msg;
@@ -1517,10 +1582,10 @@ extern "C" int lensed_loglike_plain(lensed_model *m, const double *params, int P
                          m->comp_plane.p, m->cf.p,
                          m->cd.p, m->valid.p, P, m->C_total,
                          m->trace_blocks.p + m->trace_sys_off[s], m->trace_sys_cnt[s], m->need.p,
-                         m->nodes(), p, 1, m->Lbuf.p, m->total_pix, st);
+                         m->nodes_chi(), p, 1, m->Lbuf.p, m->total_pix, st);
             if (is_mixed(m->precision))
                 launch_fix64(cfg, m->sys.p, s, 1, m->comp_type.p, m->comp_plane.p, m->cf.p,
-                             m->cd.p, m->valid.p, P, m->C_total, m->need.p, m->nodes(), p, 1,
+                             m->cd.p, m->valid.p, P, m->C_total, m->need.p, m->nodes_chi(), p, 1,
                              m->Lbuf.p, m->total_pix, st);
             if (m->psf_sys_cnt[s] > 0)
                 launch_psf(m->precision, m->psf_q[s], cfg.psf_sep ? m->psf_sep[s] : 0, m->psf_p[s],
@@ -1757,10 +1822,10 @@ extern "C" int lensed_loglike_batch_noalloc(lensed_model *m, const double *param
         for (const TraceGroup &g : m->trace_groups)
             launch_trace(m->precision, cfg, g.nn, m->sys.p, m->comp_type.p, m->comp_plane.p, cf,
                          cd, valid, P, m->C_total, m->trace_blocks.p + g.off, g.count, m->need.p,
-                         m->nodes(), p0, nP, Lbuf, m->total_pix, st);
+                         m->nodes_chi(), p0, nP, Lbuf, m->total_pix, st);
         if (is_mixed(m->precision))
             launch_fix64(cfg, m->sys.p, 0, m->n_sys, m->comp_type.p, m->comp_plane.p, cf, cd,
-                         valid, P, m->C_total, m->need.p, m->nodes(), p0, nP, Lbuf,
+                         valid, P, m->C_total, m->need.p, m->nodes_chi(), p0, nP, Lbuf,
                          m->total_pix, st);
         for (const PsfGroup &g : m->psf_groups)
             launch_psf(m->precision, g.q, cfg.psf_sep ? g.sep : 0, g.p_max, m->sys.p, m->psf_f.p, m->psf_d.p, m->data.p,
