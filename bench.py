@@ -595,7 +595,7 @@ def run_surrogate(args):
     screen = SurrogateScreen(gen.ndim, 256, 8192).fit(U, L, epochs=20, margin_sigmas=4.0)
     like = GpuLikelihood(m, spec)
     res = nested_sampling(like, like.ndim, args.live, seed=12, dlogz=0.1, prescreen=screen,
-                          max_evals=8_000_000)
+                          on_round=screen.on_round, max_evals=8_000_000)
     runs["global_surrogate"] = summary(res, like, {
         "pairs": int(screen.n_train), "generation_s": gen_s, "train_s": screen.train_s,
         "holdout_rms_y": screen.val_rms, "margin_y": screen.margin})

@@ -107,19 +107,27 @@ enum {
 enum { LENSED_RULE_POINT = 0, LENSED_RULE_SUB = 1, LENSED_RULE_GL = 2, LENSED_RULE_GK = 3 };
 #define LENSED_MAX_KRONROD_ORDER 7
 
-/* Arithmetic of the evaluation:
- *   LENSED_PREC_FP32   rays, brightness and PSF in FP32; chi^2 summed in FP64
+/* Arithmetic of the evaluation, and its accuracy against an FP64 evaluation
+ * of the same discretised model (the target being |dlogL| <= 1e-3 where
+ * chi^2 / N <= 10, and <= 1e-6 |logL| elsewhere):
+ *   LENSED_PREC_FP32   rays, brightness and PSF in FP32; chi^2 summed in FP64.
+ *                      Misses the target: the float grid of traced positions
+ *                      leaves up to ~1e-2 absolute (a few 1e-6 relative) on
+ *                      steep, compact sources.
  *   LENSED_PREC_MIXED  as FP32, but the SIE deflection is evaluated in FP64
  *                      for axis ratios close to 1 (e = sqrt(1-q^2) < 0.05)
- *                      and for rays within 2 s / q of the SIE centre
- *   LENSED_PREC_FP64   everything in FP64 (validation mode)
+ *                      and for rays within 2 s / q of the SIE centre.  Misses
+ *                      the target like FP32.
+ *   LENSED_PREC_FP64   everything in FP64 (validation mode).  Meets it.
  *   LENSED_PREC_MIXED_FF  as MIXED, and every ray whose FP32 source-plane
  *                      position falls within one effective radius of a
  *                      Sersic-type source (R < r) is re-traced with the lens
- *                      equation in float-float arithmetic (~48 bits): the
- *                      float grid of traced positions otherwise limits the
- *                      log-likelihood to ~1e-2 absolute on steep, compact
- *                      sources; this mode reaches ~1e-3 at 1.5-3x the cost.
+ *                      equation in float-float arithmetic (~44 bits).  Meets
+ *                      the target on the 64x64 and 200x200 workloads and near
+ *                      the posterior of large images; far from the posterior
+ *                      on large, high signal-to-noise images (chi^2 / N of a
+ *                      few, |logL| >= 1e4) FP32 storage of the images leaves
+ *                      a few 1e-6 relative.  1.4-3x the cost of MIXED.
  *                      Its batched calls also keep a queue for the second
  *                      pass of the re-traces (a 24-byte header per trace
  *                      block and point, and 4 bytes per re-traced ray, at

@@ -31,7 +31,7 @@ def _stream_handle(stream):
 
 
 class Model:
-    def __init__(self, specs, observations, precision="mixed", extra_weights=None):
+    def __init__(self, specs, observations, precision="mixed_ff", extra_weights=None):
         if isinstance(specs, dict):
             specs = [specs]
             observations = [observations]

@@ -136,10 +136,17 @@ class SurrogateScreen:
         out = self.net.forward(self._x(U)).cpu().numpy().astype(np.float64)
         return out * self.y_std + self.y_mean
 
+    def on_round(self, live_u, live_l, threshold):
+        """Calibration (pass as the sampler's on_round): the cut is raised to
+        the highest prediction among the current live points, which all lie
+        inside the contour (see OnlineSurrogate._calibrate)."""
+        self.live_y_max = float(self.predict_y(live_u).max())
+
     def __call__(self, U, threshold):
         t0 = time.perf_counter()
         y_thr = math.log1p(max(self.L_ref - threshold, 0.0))
-        keep = self.predict_y(U) < y_thr + self.margin
+        cut = max(y_thr, getattr(self, "live_y_max", y_thr)) + self.margin
+        keep = self.predict_y(U) < cut
         self.n_screen += len(U)
         self.screen_s += time.perf_counter() - t0
         return keep

@@ -39,7 +39,7 @@ def gk_case(n):
 
 
 @pytest.mark.parametrize("n", [3, 5, 7])
-@pytest.mark.parametrize("precision", ["fp32", "mixed", "fp64"])
+@pytest.mark.parametrize("precision", ["fp32", "mixed", "mixed_ff", "fp64"])
 def test_kronrod_render_and_error_map(n, precision):
     spec, obs, osys = gk_case(n)
     m = lensed().Model(spec, obs, precision=precision)
@@ -59,8 +59,10 @@ def test_kronrod_render_and_error_map(n, precision):
         assert np.all(e_gpu >= 0)
 
 
-@pytest.mark.parametrize("n", [3, 7])
-@pytest.mark.parametrize("precision", ["fp32", "mixed", "fp64"])
+# g3k7 has 7 nodes per row (MIXED_FF's queued re-trace), g5k11 and g7k15 have
+# 11 and 15 (its in-place re-trace)
+@pytest.mark.parametrize("n", [3, 5, 7])
+@pytest.mark.parametrize("precision", ["fp32", "mixed", "mixed_ff", "fp64"])
 def test_kronrod_loglike(n, precision):
     spec, obs, osys = gk_case(n)
     m = lensed().Model(spec, obs, precision=precision)
