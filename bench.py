@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="mixed_ff", choices=["fp32", "mixed", "mixed_ff", "fp64"],
                     help="mixed_ff (default): FP32 rays, FP64 SIE near the core and for q -> 1, "
-                         "float-float lens equation within one effective radius of a source "
+                         "float-float lens equation within half an effective radius of a source "
                          "centre; the mode that holds |dlogL| near 1e-3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=POINTS,

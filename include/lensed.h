@@ -120,8 +120,8 @@ enum { LENSED_RULE_POINT = 0, LENSED_RULE_SUB = 1, LENSED_RULE_GL = 2, LENSED_RU
  *                      the target like FP32.
  *   LENSED_PREC_FP64   everything in FP64 (validation mode).  Meets it.
  *   LENSED_PREC_MIXED_FF  as MIXED, and every ray whose FP32 source-plane
- *                      position falls within one effective radius of a
- *                      Sersic-type source (R < r) is re-traced with the lens
+ *                      position falls within half an effective radius of a
+ *                      Sersic-type source (R < r/2) is re-traced with the lens
  *                      equation in float-float arithmetic (~44 bits).  Meets
  *                      the target on the 64x64 and 200x200 workloads and near
  *                      the posterior of large images; far from the posterior

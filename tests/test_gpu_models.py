@@ -191,5 +191,7 @@ def test_low_rank_and_full_psfs(name, precision):
         for xi in pts[:2]:
             assert_image_close(m.render(0, xi).cpu().numpy(), osys.render(xi), what=(name, idx))
         g = m.loglike_batch(pts).cpu().numpy()[0]
-        assert_loglike_close(g, ref, int((np.asarray(spec["mask"]) == 0).sum()), precision)
+        # the truth is the posterior region; the rest are prior points
+        _loglike_close_by_region(g, ref, 1, int((np.asarray(spec["mask"]) == 0).sum()),
+                                 precision)
         assert np.array_equal(g, m.loglike_plain(pts).cpu().numpy()[0])
