@@ -1457,6 +1457,22 @@ static __host__ __device__ __forceinline__ int psf_row_stride(int q)
 // each row starts 16-byte aligned.
 static __host__ __device__ __forceinline__ int psf_tap_stride(int q) { return (2 * q + 1 + 3) & ~3; }
 
+// Stage rows x cols of an image into shared memory (row stride `stride`),
+// from image row i0 and column j0 on, indices clamped to the image (Eq. 15's
+// edge padding): one warp per row, consecutive lanes on consecutive columns
+// (coalesced), no integer division.
+template <typename T>
+__device__ __forceinline__ void stage_tile(T *s, int stride, const T *__restrict__ L, int nx,
+                                           int ny, int i0, int j0, int rows, int cols)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < rows; r += (int)(blockDim.x >> 5)) {
+        const T *src = L + (size_t)min(max(i0 + r, 0), ny - 1) * nx;
+        T *dst = s + r * stride;
+        for (int c = lane; c < cols; c += 32) dst[c] = src[min(max(j0 + c, 0), nx - 1)];
+    }
+}
+
 template <typename T, int Q>
 __global__ void __launch_bounds__(kPsfThreads)
     k_psf(const SysDev *__restrict__ sys, const T *__restrict__ psf,
@@ -1497,13 +1513,7 @@ __global__ void __launch_bounds__(kPsfThreads)
         s_F[k] = c < W ? psf[S.psf_off + r * W + c] : T(0);
     }
     const T *L = Lbuf + (size_t)(p - p0) * L_stride + S.pix_off;
-    const int cols = kTileW + 2 * Q;
-    for (int k = threadIdx.x; k < rows * cols; k += blockDim.x) {
-        const int r = k / cols, c = k - (k / cols) * cols;
-        const int gi = min(max(pb.i0 - Ph + r, 0), ny - 1);
-        const int gj = min(max(pb.j0 - Q + c, 0), nx - 1);
-        s_L[r * stride + c] = L[(size_t)gi * nx + gj];
-    }
+    stage_tile(s_L, stride, L, nx, ny, pb.i0 - Ph, pb.j0 - Q, rows, kTileW + 2 * Q);
     __syncthreads();
 
     // each warp owns a 16 x 16 block of outputs (the tile is 2 x 4 warps);
@@ -1632,20 +1642,42 @@ __global__ void __launch_bounds__(kPsfThreads)
         s_r[k] = l < W ? fac[t * nf + 2 * Ph + 1 + l] : 0.f;
     }
     const float *L = Lbuf + (size_t)(p - p0) * L_stride + S.pix_off;
-    const int cols = kTileW + 2 * Q;
-    for (int k = threadIdx.x; k < rows * cols; k += blockDim.x) {
-        const int r = k / cols, c = k - (k / cols) * cols;
-        const int gi = min(max(pb.i0 - Ph + r, 0), ny - 1);
-        const int gj = min(max(pb.j0 - Q + c, 0), nx - 1);
-        s_L[r * stride + c] = L[(size_t)gi * nx + gj];
+    stage_tile(s_L, stride, L, nx, ny, pb.i0 - Ph, pb.j0 - Q, rows, kTileW + 2 * Q);
+    // chi^2 mode: output rows of the tile with a weighted pixel; the row pass
+    // is needed only within p rows of one
+    __shared__ unsigned char s_live[kTileH + 2 * LENSED_MAX_PSF_HALF];
+    if (partial) {
+        __shared__ unsigned char s_orow[kTileH];
+        const int warp0 = threadIdx.x >> 5, lane0 = threadIdx.x & 31;
+        for (int r = warp0; r < kTileH; r += kPsfThreads / 32) {
+            const int i = pb.i0 + r;
+            bool any = false;
+            if (i < ny)
+                for (int c = lane0; c < kTileW; c += 32) {
+                    const int j = pb.j0 + c;
+                    any = any || (j < nx && weight[S.pix_off + (size_t)i * nx + j] > 0.f);
+                }
+            any = __any_sync(0xffffffffu, any);
+            if (lane0 == 0) s_orow[r] = any ? 1 : 0;
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+            bool need = false;
+            for (int o = max(0, r - 2 * Ph); o <= min(kTileH - 1, r); ++o) need = need || s_orow[o];
+            s_live[r] = need ? 1 : 0;
+        }
     }
     __syncthreads();
 
-    // pass 1: rows, kOutPerThread outputs per item
+    // pass 1: rows, kOutPerThread outputs per item (the kSeg segments of a row
+    // on kSeg consecutive threads)
     constexpr int kSeg = kTileW / kOutPerThread;
-    for (int it = threadIdx.x; it < R * rows * kSeg; it += blockDim.x) {
-        const int t = it / (rows * kSeg), rem = it - t * (rows * kSeg);
-        const int r = rem / kSeg, j0 = (rem - r * kSeg) * kOutPerThread;
+    static_assert(kPsfThreads % kSeg == 0, "row-pass mapping");
+    const int seg = threadIdx.x & (kSeg - 1), rgrp = threadIdx.x / kSeg;
+    for (int t = 0; t < R; ++t)
+    for (int r = rgrp; r < rows; r += kPsfThreads / kSeg) {
+        if (partial && !s_live[r]) continue;
+        const int j0 = seg * kOutPerThread;
         const float *srow = s_L + r * stride + j0;
         float lv[kOutPerThread + 2 * Q];
 #pragma unroll
