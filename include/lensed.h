@@ -320,6 +320,17 @@ int lensed_tuned_config(const lensed_model *m, char *buf, int buflen);
  * Synchronous; allocates a small scratch buffer. */
 int lensed_measure_alu_peaks(double *fma_tflops, double *mufu_tops, void *stream);
 
+/* Accuracy probe of the FP32 SIE's inverse tangents (Sec. 2.1, Eqs. 2-3:
+ * the deflection's atan(e x' / (psi + s)) and atanh(e y' / (psi + q^2 s))).
+ * For i < count, with DEVICE arrays n[count], d[count] (d >= 0; |n| < d for
+ * atanh) it writes to the DEVICE array out[4 * count]: out[i] = the kernel's
+ * atan(n/d), out[count + i] = its atanh(n/d), out[2 count + i] = CUDA's
+ * atanf of the rounded FP32 quotient, out[3 count + i] = atanhf of it.
+ * Asynchronous on `stream`; LENSED_E_ARG for a negative count or a NULL
+ * pointer with count > 0. */
+int lensed_eval_sie_trig(const float *n, const float *d, long long count, float *out,
+                         void *stream);
+
 /* Use configuration `index` (0 .. n-1 as lensed_tuned_config numbers them,
  * -1 = default) instead of the autotuner's choice; returns the number of
  * configurations n (6, and 12 for LENSED_PREC_MIXED_FF, whose configurations

@@ -195,6 +195,8 @@ void launch_copy_image(int precision, const void *Lbuf, long long off, int npix,
 
 // Throughput probes (FMA or MUFU ex2 chains) for the measured ALU peaks.
 void launch_probe(int mufu, int blocks, int threads, int iters, float *sink, cudaStream_t st);
+void launch_trig_probe(const float *n, const float *d, long long count, float *out,
+                       cudaStream_t st);
 
 // |L_K - L_G| of one system's pixels (the Gauss-Kronrod error estimate),
 // NaN if the point is invalid.

@@ -34,6 +34,7 @@
 #include <utility>
 
 #include "lensed_internal.cuh"
+#include "lensed_sie_trig.cuh"
 
 namespace lensed {
 
@@ -375,7 +376,8 @@ __device__ __forceinline__ LightF load_light(const float *c)
 // that carries a residual partner is a float-pair multiply-add, so the
 // float rounding of the constants does not bias the deflection field.
 // Quotients and the square root use the fast forms (a few ulp, random in
-// sign from ray to ray).
+// sign from ray to ray); atan and atanh are the minimax forms of
+// lensed_sie_trig.cuh, fed the numerator and denominator of their argument.
 __device__ __forceinline__ void sie_f32(const SieF &k, float x, float y, float &ax, float &ay)
 {
     const float dx = x - k.x0, dy = y - k.y0;
@@ -385,16 +387,16 @@ __device__ __forceinline__ void sie_f32(const SieF &k, float x, float y, float &
     const float psi2 = fmaf(k.q2, w, fmaf(k.q2l, w, v * v));
     const float psi = psi2 > 0.f ? psi2 * rsqrtf(psi2) : 0.f;
     const float du = psi + k.s, dv = psi + k.q2s;
-    const float zu = du > 0.f ? __fdividef(u, du) : 0.f;
-    const float zv = du > 0.f ? __fdividef(v, dv) : 0.f;
     float A1, A2;
     if (k.series != 0.f) {
+        const float zu = du > 0.f ? __fdividef(u, du) : 0.f;
+        const float zv = du > 0.f ? __fdividef(v, dv) : 0.f;
         const float zu2 = zu * zu, zv2 = zv * zv;
         A1 = zu * (1.f - k.e2 * zu2 * (1.f / 3.f) + k.e2 * k.e2 * zu2 * zu2 * 0.2f);
         A2 = zv * (1.f + k.e2 * zv2 * (1.f / 3.f) + k.e2 * k.e2 * zv2 * zv2 * 0.2f);
     } else {
-        A1 = atanf(fmaf(k.e, zu, k.el * zu));
-        A2 = atanhf(fmaf(k.e, zv, k.el * zv));
+        A1 = atan_ratio(fmaf(k.e, u, k.el * u), du);
+        A2 = atanh_ratio(fmaf(k.e, v, k.el * v), dv);
     }
     const float au = fmaf(k.pref, A1, k.prefl * A1);
     const float av = fmaf(k.pref, A2, k.prefl * A2);
@@ -447,16 +449,16 @@ __device__ __forceinline__ void sie_f32_row(const SieF &k, const RowTerms &R, fl
     const float psi2 = fmaf(k.q2, w, fmaf(k.q2l, w, v * v));
     const float psi = psi2 > 0.f ? psi2 * rsqrtf(psi2) : 0.f;
     const float du = psi + k.s, dv = psi + k.q2s;
-    const float zu = du > 0.f ? __fdividef(u, du) : 0.f;
-    const float zv = du > 0.f ? __fdividef(v, dv) : 0.f;
     float A1, A2;
     if (k.series != 0.f) {
+        const float zu = du > 0.f ? __fdividef(u, du) : 0.f;
+        const float zv = du > 0.f ? __fdividef(v, dv) : 0.f;
         const float zu2 = zu * zu, zv2 = zv * zv;
         A1 = zu * (1.f - k.e2 * zu2 * (1.f / 3.f) + k.e2 * k.e2 * zu2 * zu2 * 0.2f);
         A2 = zv * (1.f + k.e2 * zv2 * (1.f / 3.f) + k.e2 * k.e2 * zv2 * zv2 * 0.2f);
     } else {
-        A1 = atanf(fmaf(k.e, zu, k.el * zu));
-        A2 = atanhf(fmaf(k.e, zv, k.el * zv));
+        A1 = atan_ratio(fmaf(k.e, u, k.el * u), du);
+        A2 = atanh_ratio(fmaf(k.e, v, k.el * v), dv);
     }
     const float au = fmaf(k.pref, A1, k.prefl * A1);
     const float av = fmaf(k.pref, A2, k.prefl * A2);

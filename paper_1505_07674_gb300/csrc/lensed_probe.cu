@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "lensed_internal.cuh"
+#include "lensed_sie_trig.cuh"
 
 namespace lensed {
 
@@ -42,6 +43,31 @@ __global__ void k_probe_mufu(int iters, float seed, float *__restrict__ sink)
 #pragma unroll
     for (int k = 0; k < 8; ++k) t += a[k];
     if (t == 12345.f) sink[blockIdx.x] = t;
+}
+
+// The FP32 SIE's atan and atanh of n[i] / d[i] (lensed_sie_trig.cuh) beside
+// CUDA's atanf / atanhf of the rounded quotient, for accuracy tests.
+__global__ void k_probe_trig(const float *__restrict__ n, const float *__restrict__ d,
+                             long long count, float *__restrict__ out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float a = n[i], b = d[i];
+        const float z = b > 0.f ? a / b : 0.f;
+        out[i] = atan_ratio(a, b);
+        out[count + i] = atanh_ratio(a, b);
+        out[2 * count + i] = atanf(z);
+        out[3 * count + i] = atanhf(z);
+    }
+}
+
+void launch_trig_probe(const float *n, const float *d, long long count, float *out,
+                       cudaStream_t st)
+{
+    if (count <= 0) return;
+    const long long want = (count + 255) / 256;
+    const unsigned grid = (unsigned)(want < 4096 ? want : 4096);
+    k_probe_trig<<<grid, 256, 0, st>>>(n, d, count, out);
 }
 
 void launch_probe(int mufu, int blocks, int threads, int iters, float *sink, cudaStream_t st)

@@ -1449,6 +1449,16 @@ extern "C" int lensed_measure_alu_peaks(double *fma_tflops, double *mufu_tops, v
     return LENSED_OK;
 }
 
+extern "C" int lensed_eval_sie_trig(const float *n, const float *d, long long count, float *out,
+                                    void *stream)
+{
+    if (count < 0) return fail(LENSED_E_ARG, "negative count");
+    if (count > 0 && (!n || !d || !out)) return fail(LENSED_E_ARG, "NULL pointer");
+    launch_trig_probe(n, d, count, out, (cudaStream_t)stream);
+    CUDA_OK(cudaGetLastError());
+    return LENSED_OK;
+}
+
 extern "C" int lensed_rule_nodes(int rule, int order, double *t, double *w, double *w_gauss)
 {
     if (!t || !w) return fail(LENSED_E_ARG, "t/w is NULL");
