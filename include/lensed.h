@@ -439,8 +439,14 @@ int lensed_mlp_screen_ellipsoid(lensed_mlp *m, int d, int n, unsigned long long 
  *     already issued, frees its tensor memory, writes no output and records
  *     the expiry, which the next lensed_mlp_get_params reports as
  *     LENSED_E_TIMEOUT; lensed_mlp_set_params clears it.  Values above the
- *     default are clamped to it. */
+ *     default are clamped to it.
+ *   lensed_debug_ff_queue_cap(m, cap): MIXED_FF launches whose float-float
+ *     re-traces go to a second kernel see a queue of at most `cap` entries
+ *     (cap < 0: the allocated size).  A warp whose rays do not fit marks its
+ *     slots empty and re-traces them itself, so the results are unchanged;
+ *     the hook exercises that path.  Synchronises the device. */
 long long lensed_debug_fail_alloc(long long after);
+int lensed_debug_ff_queue_cap(lensed_model *m, long long cap);
 int lensed_mlp_debug_spin_limit(lensed_mlp *m, int polls);
 
 /* Thread-local message of the last failing call ("" if none). */

@@ -34,7 +34,7 @@ EXPORTS = ("lensed_create_model", "lensed_destroy", "lensed_model_info_get", "le
            "lensed_mlp_create", "lensed_mlp_destroy", "lensed_mlp_param_count",
            "lensed_mlp_set_params", "lensed_mlp_get_params", "lensed_mlp_forward",
            "lensed_mlp_gradient", "lensed_mlp_train_step", "lensed_mlp_last_error",
-           "lensed_debug_fail_alloc", "lensed_mlp_debug_spin_limit",
+           "lensed_debug_fail_alloc", "lensed_debug_ff_queue_cap", "lensed_mlp_debug_spin_limit",
            "lensed_mlp_screen_ellipsoid")
 
 
@@ -111,6 +111,7 @@ def lib():
                                                   vp, vp, vp, vp]
         L.lensed_debug_fail_alloc.argtypes = [C.c_longlong]
         L.lensed_debug_fail_alloc.restype = C.c_longlong
+        L.lensed_debug_ff_queue_cap.argtypes = [vp, C.c_longlong]
         L.lensed_mlp_debug_spin_limit.argtypes = [vp, C.c_int]
         L.lensed_mlp_last_error.restype = C.c_char_p
         L.lensed_mlp_last_error.argtypes = []

@@ -109,24 +109,25 @@ struct LaunchCfg {
     int ff_split;       // 1 (MIXED_FF): float-float re-traces in a second kernel
 };
 
-// A trace block's deferred float-float rays handed to the second pass: the
-// block's system, point, first need-list item, number of entries and offset
-// of its entries in FfQueue::ent.
-struct FfHeader {
-    int sys, p, start, n;
-    long long base;
+// One deferred float-float ray of a trace launch: lin = the pixel's index in
+// the launch's image scratch ((point - p0) * stride + pixel offset of the
+// system + pixel), sr = system << 8 | ray index in the rule grid (row-major,
+// b * nn + a).  A pixel's entries are consecutive and in ray order.
+// lin == kFfNone marks a slot left empty.
+struct FfEntry {
+    unsigned lin, sr;
 };
+constexpr unsigned kFfNone = 0xffffffffu;
 
-// MIXED_FF second-pass queue of one trace launch.  cnt[0]: headers written,
-// cnt[1]: entries reserved, cnt[2]: headers taken by the second pass (all
-// three zeroed before the launch).  Entry: pixel slot in the block
-// (bits 0-15) | ray index in the rule grid (bits 16-23).  cnt == nullptr:
+// MIXED_FF second-pass queue of one trace launch: *cnt = entries reserved
+// (zeroed before the launch), ent[ecap] the entries, val[ecap] their
+// source-plane brightness (written by the second pass).  cnt == nullptr:
 // every block re-traces its own rays (no second pass).
 struct FfQueue {
     unsigned long long *cnt;
-    FfHeader *hdr;
-    unsigned *ent;
-    long long hcap, ecap;
+    FfEntry *ent;
+    float *val;
+    long long ecap;
 };
 
 // True when the test hook lensed_debug_fail_alloc says the next device

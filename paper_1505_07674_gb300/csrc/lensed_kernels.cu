@@ -783,23 +783,37 @@ __device__ __forceinline__ float light_f32_at(const LightF &k, float dx, float d
     return fmaf(k.A, g, k.Al * g);
 }
 
-// Source-plane brightness of ray (a, b) of pixel (jc, ic) with the lens
-// equation in float-float (all lens components), the light in FP32.  Every
-// constant comes as a float pair from the component's packed FP32 block
-// (value and residual slots, see k_prologue_comp).
-__device__ __noinline__ float source_brightness_ff(const TraceSmem &sm, int ncomp, float jc,
-                                                   float ic, float h, float h_lo, int a, int b)
+// Where the float-float re-trace reads a point's constants: the packed FP32
+// blocks of its components, their types and planes (shared memory in the
+// trace block, global memory in the second pass).
+struct FfConsts {
+    const float *cf;
+    const int *type, *plane;
+};
+
+// A node offset (FP64) as a float pair.
+__device__ __forceinline__ ff node_pair(double v)
+{
+    const float hi = (float)v;
+    return {hi, (float)(v - (double)hi)};
+}
+
+// Source-plane brightness of a ray of pixel (jc, ic) with node offsets ua
+// (along x) and vb (along y) as float pairs, with the lens equation in
+// float-float (all lens components) and the light in FP32.  Every constant
+// comes as a float pair from the component's packed FP32 block (value and
+// residual slots, see k_prologue_comp).
+__device__ __noinline__ float source_brightness_ff_at(FfConsts K, int ncomp, float jc, float ic,
+                                                      float h, float h_lo, ff ua, ff vb)
 {
     // ray position: (j - cx) h + t_a h, with h and the node offset as float pairs
-    ff x = ff_add(ff_add(ff{jc * h, fmaf(jc, h, -(jc * h))}, ff{jc * h_lo, 0.f}),
-                  ff{sm.uh[a], sm.ul[a]});
-    ff y = ff_add(ff_add(ff{ic * h, fmaf(ic, h, -(ic * h))}, ff{ic * h_lo, 0.f}),
-                  ff{sm.uh[b], sm.ul[b]});
+    ff x = ff_add(ff_add(ff{jc * h, fmaf(jc, h, -(jc * h))}, ff{jc * h_lo, 0.f}), ua);
+    ff y = ff_add(ff_add(ff{ic * h, fmaf(ic, h, -(ic * h))}, ff{ic * h_lo, 0.f}), vb);
     ff ax{0.f, 0.f}, ay{0.f, 0.f};
     for (int c = 0; c < ncomp; ++c) {
-        if (sm.plane[c] != LENSED_PLANE_LENS) continue;
-        const float *k = sm.cf + c * kNC;
-        const int t = sm.type[c];
+        if (K.plane[c] != LENSED_PLANE_LENS) continue;
+        const float *k = K.cf + c * kNC;
+        const int t = K.type[c];
         if (t == LENSED_SIE) {
             const ff dx = ff_sub(x, ff_pair(k, 0, 19)), dy = ff_sub(y, ff_pair(k, 1, 20));
             const ff cs = ff_pair(k, 2, 4), sn = ff_pair(k, 3, 5);
@@ -844,8 +858,8 @@ __device__ __noinline__ float source_brightness_ff(const TraceSmem &sm, int ncom
     const ff sx = ff_sub(x, ax), sy = ff_sub(y, ay);
     float I = 0.f;
     for (int c = 0; c < ncomp; ++c) {
-        if (sm.plane[c] != LENSED_PLANE_SOURCE) continue;
-        const float *k = sm.cf + c * kNC;
+        if (K.plane[c] != LENSED_PLANE_SOURCE) continue;
+        const float *k = K.cf + c * kNC;
         const LightF L = load_light(k);
         if (L.kind == (float)kKindFlat) {
             I += L.A;
@@ -855,6 +869,14 @@ __device__ __noinline__ float source_brightness_ff(const TraceSmem &sm, int ncom
         I += light_f32_at(L, ox.hi + ox.lo, oy.hi + oy.lo);
     }
     return I;
+}
+
+// The same for ray (a, b) of the rule, with the point staged in shared memory.
+__device__ __forceinline__ float source_brightness_ff(const TraceSmem &sm, int ncomp, float jc,
+                                                      float ic, float h, float h_lo, int a, int b)
+{
+    return source_brightness_ff_at(FfConsts{sm.cf, sm.type, sm.plane}, ncomp, jc, ic, h, h_lo,
+                                   ff{sm.uh[a], sm.ul[a]}, ff{sm.uh[b], sm.ul[b]});
 }
 
 // FP32 light of a source, also reporting (R / r)^2 of the ray.
@@ -885,7 +907,9 @@ constexpr int kQCap = 2048;       // deferred float-float rays per trace block
 // component, so each component's constants are read into registers once per
 // G rays and the G independent rays give the scheduler instruction-level
 // parallelism.  EXACT: the rule has exactly G nodes per row (no guards).
-template <int MODE, int G, bool EXACT>
+// GQ (MIXED_FF, EXACT): the float-float re-traces go to the launch's global
+// queue, appended warp by warp, for k_retrace_ff and k_apply_ff.
+template <int MODE, int G, bool EXACT, bool GQ>
 __global__ void __launch_bounds__(256)
     k_trace_rows(const SysDev *__restrict__ sys, const int *__restrict__ comp_type,
                  const int *__restrict__ comp_plane, const float *__restrict__ cf,
@@ -900,13 +924,14 @@ __global__ void __launch_bounds__(256)
     if (!valid[(size_t)tb.sys * P + p]) return;
     const SysDev &S = sys[tb.sys];
     const size_t cbase = ((size_t)p * C_total + S.comp_off) * kNC;
-    // MIXED_FF with at most 8 nodes per row defers its float-float re-traces to a
-    // block-wide queue (64-bit ray mask per pixel), processed by all lanes
-    // after the main loop, or handed to the second pass (k_retrace_ff) when
-    // the launch has a queue in global memory; the others re-trace in place
-    constexpr bool kQueue = (MODE == LENSED_PREC_MIXED_FF) && EXACT;
-    __shared__ int q_n, q_ok;
-    __shared__ long long q_base;
+    // MIXED_FF with at most 8 nodes per row defers its float-float re-traces
+    // (64-bit ray mask per pixel): to a block-wide queue processed by all
+    // lanes after the main loop, or (GQ) to the launch's global queue; the
+    // others re-trace in place
+    constexpr bool kFfDefer = (MODE == LENSED_PREC_MIXED_FF) && EXACT;
+    constexpr bool kQueue = kFfDefer && !GQ;
+    constexpr bool kWarpQ = kFfDefer && GQ;
+    __shared__ int q_n;
     __shared__ unsigned short q_t[kQueue ? kQCap : 1];
     __shared__ unsigned char q_r[kQueue ? kQCap : 1];
     __shared__ float q_v[kQueue ? kQCap : 1];
@@ -916,7 +941,8 @@ __global__ void __launch_bounds__(256)
 
     const int idx = tb.start + threadIdx.x;
     const bool active = idx < tb.end;
-    if (!kQueue && !active) return;
+    // (a warp appending to the global queue needs all its lanes)
+    if (!kQueue && !kWarpQ && !active) return;
     const int ncomp = S.ncomp;
     const int nn = EXACT ? G : S.nn;
     const int nx = S.nx;
@@ -1008,24 +1034,68 @@ __global__ void __launch_bounds__(256)
                     for (int k = 0; k < G; ++k) I[k] += light_f32(L, xk[k] - ax[k], y - ay[k]);
                 }
             }
-            if (MODE == LENSED_PREC_MIXED_FF) {
+            if (kFfDefer) {
+                // the source part comes from the queue; keep the rest (the
+                // row's flags gathered first, one shift into the mask per row)
+                unsigned row = 0u;
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    row |= near[k] ? 1u << k : 0u;
+                    I[k] = near[k] ? Ifg[k] : I[k];
+                }
+                mask |= (unsigned long long)row << (b * nn);
+            } else if (MODE == LENSED_PREC_MIXED_FF) {
 #pragma unroll
                 for (int k = 0; k < G; ++k) {
                     if (!near[k] || !(EXACT || a0 + k < nn)) continue;
-                    if (kQueue) {
-                        // the source part comes from the queue; keep the rest
-                        mask |= 1ull << (b * nn + k);
-                        I[k] = Ifg[k];
-                    } else {
-                        I[k] = Ifg[k] + source_brightness_ff(sm, ncomp, jc, ic, S.h, S.h_lo,
-                                                             a0 + k, b);
-                    }
+                    I[k] = Ifg[k] + source_brightness_ff(sm, ncomp, jc, ic, S.h, S.h_lo,
+                                                         a0 + k, b);
                 }
             }
 #pragma unroll
             for (int k = 0; k < G; ++k)
                 if (EXACT || a0 + k < nn) acc = fmaf(sm.w[b * nn + a0 + k], I[k], acc);
         }
+    }
+    if (kWarpQ) {
+        // the warp reserves consecutive slots for its lanes' rays (each
+        // pixel's in ray order); the pixel's first-pass sum is stored now and
+        // k_apply_ff adds the re-traced rays to it
+        const unsigned full = 0xffffffffu, lane = threadIdx.x & 31u;
+        const int n_t = __popcll(mask);
+        if (__any_sync(full, n_t != 0)) {
+            int incl = n_t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(full, incl, o);
+                if ((int)lane >= o) incl += v;
+            }
+            const int total = __shfl_sync(full, incl, 31);
+            unsigned long long base = 0ull;
+            if (lane == 31u) base = atomicAdd(fq.cnt, (unsigned long long)total);
+            base = __shfl_sync(full, base, 31);
+            const unsigned long long cap = (unsigned long long)fq.ecap;
+            unsigned long long e = base + (unsigned long long)(incl - n_t);
+            if (base + (unsigned long long)total <= cap) {
+                const unsigned lin = (unsigned)((size_t)(p - p0) * L_stride + S.pix_off + pix);
+                const unsigned sys8 = (unsigned)tb.sys << 8;
+                for (unsigned long long m = mask; m; m &= m - 1ull, ++e)
+                    fq.ent[e] = FfEntry{lin, sys8 | (unsigned)(__ffsll((long long)m) - 1)};
+            } else {
+                // the queue is full: mark this warp's slots inside it empty
+                // and re-trace the rays here, in ray order
+                for (int k = 0; k < n_t; ++k, ++e)
+                    if (e < cap) fq.ent[e] = FfEntry{kFfNone, 0u};
+                for (unsigned long long m = mask; m; m &= m - 1ull) {
+                    const int r = __ffsll((long long)m) - 1;
+                    acc = fmaf(sm.w[r],
+                               source_brightness_ff(sm, ncomp, jc, ic, S.h, S.h_lo, r % nn, r / nn),
+                               acc);
+                }
+            }
+        }
+        if (active) Lbuf[(size_t)(p - p0) * L_stride + S.pix_off + pix] = acc;
+        return;
     }
     if (kQueue) {
         // each pixel's deferred rays take consecutive slots in ray order
@@ -1043,31 +1113,6 @@ __global__ void __launch_bounds__(256)
         }
         __syncthreads();
         const int nq = min(q_n, kQCap);
-        if (fq.cnt) {
-            // hand the whole queue to the second pass when it fits there
-            if (threadIdx.x == 0) {
-                int ok = 0;
-                if (q_n > 0 && q_n <= kQCap) {
-                    const unsigned long long eb = atomicAdd(&fq.cnt[1], (unsigned long long)q_n);
-                    if (eb + (unsigned long long)q_n <= (unsigned long long)fq.ecap) {
-                        const unsigned long long hb = atomicAdd(&fq.cnt[0], 1ull);
-                        if (hb < (unsigned long long)fq.hcap) {
-                            fq.hdr[hb] = FfHeader{tb.sys, p, tb.start, q_n, (long long)eb};
-                            q_base = (long long)eb;
-                            ok = 1;
-                        }
-                    }
-                }
-                q_ok = ok;
-            }
-            __syncthreads();
-            if (q_ok) {
-                for (int e = threadIdx.x; e < nq; e += blockDim.x)
-                    fq.ent[q_base + e] = (unsigned)q_t[e] | ((unsigned)q_r[e] << 16);
-                if (active) Lbuf[(size_t)(p - p0) * L_stride + S.pix_off + pix] = acc;
-                return;
-            }
-        }
         for (int e = threadIdx.x; e < nq; e += blockDim.x) {
             const int t = q_t[e], r = q_r[e];
             const int pt = need ? need[S.need_off + tb.start + t] : tb.start + t;
@@ -1091,12 +1136,11 @@ __global__ void __launch_bounds__(256)
     if (active) Lbuf[(size_t)(p - p0) * L_stride + S.pix_off + pix] = acc;
 }
 
-// MIXED_FF second pass: the deferred float-float re-traces of the blocks
-// that handed their queue over (FfHeader per block).  Each CTA takes one
-// header at a time, stages that point's constants, re-traces the entries
-// with all its lanes (only this code runs here, so the rays of many blocks
-// fill whole warps), then adds each pixel's rays to its first-pass sum in ray
-// order -- the same arithmetic in the same order as the in-block path.
+// MIXED_FF second pass over a trace launch's global queue: one thread per
+// entry (the rays of many warps and points fill whole warps here) reads its
+// point's constants from global memory and writes the ray's source-plane
+// brightness; k_apply_ff then adds each pixel's rays to its first-pass sum in
+// ray order -- the same arithmetic in the same order as the in-block path.
 constexpr int kFfThreads = 128;
 
 // SMs of the current device, read once per model (sizes the second pass's
@@ -1105,49 +1149,75 @@ static int g_sm_count = 0;
 
 __global__ void __launch_bounds__(kFfThreads)
     k_retrace_ff(const SysDev *__restrict__ sys, const int *__restrict__ comp_type,
-                 const int *__restrict__ comp_plane, const float *__restrict__ cf,
-                 const double *__restrict__ cd, int C_total, const int *__restrict__ need,
-                 NodeTables nodes, int p0, float *__restrict__ Lbuf, long long L_stride,
-                 FfQueue fq)
+                 const int *__restrict__ comp_plane, const float *__restrict__ cf, int C_total,
+                 NodeTables nodes, int p0, unsigned L_stride, FfQueue fq)
 {
-    __shared__ __align__(16) TraceSmem sm;
-    __shared__ unsigned q_e[kQCap];
-    __shared__ float q_v[kQCap];
-    __shared__ long long h_cur;
-    const long long nh = min((long long)fq.cnt[0], fq.hcap);
-    for (;;) {
-        __syncthreads();  // the previous header is done with the shared arrays
-        if (threadIdx.x == 0) h_cur = (long long)atomicAdd(&fq.cnt[2], 1ull);
-        __syncthreads();
-        const long long h = h_cur;
-        if (h >= nh) return;
-        const FfHeader H = fq.hdr[h];
-        const SysDev &S = sys[H.sys];
-        const size_t cbase = ((size_t)H.p * C_total + S.comp_off) * kNC;
-        stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, false, false, nodes);
-        const int n = min(H.n, kQCap);
-        for (int e = threadIdx.x; e < n; e += blockDim.x) q_e[e] = fq.ent[H.base + e];
-        __syncthreads();
-        const int nn = S.nn, nx = S.nx, ncomp = S.ncomp;
-        for (int e = threadIdx.x; e < n; e += blockDim.x) {
-            const int t = (int)(q_e[e] & 0xffffu), r = (int)(q_e[e] >> 16);
-            const int pt = need ? need[S.need_off + H.start + t] : H.start + t;
-            const int it = pt / nx, jt = pt - it * nx;
-            q_v[e] = source_brightness_ff(sm, ncomp, (float)jt - S.cx, (float)it - S.cy, S.h,
-                                          S.h_lo, r % nn, r / nn);
+    const long long n = min((long long)*fq.cnt, fq.ecap);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const FfEntry E = fq.ent[e];
+        if (E.lin == kFfNone) continue;
+        const SysDev &S = sys[E.sr >> 8];
+        const int r = (int)(E.sr & 255u), nn = S.nn;
+        const unsigned q = E.lin / L_stride;
+        const int pix = (int)(E.lin - q * L_stride) - S.pix_off;
+        const int i = pix / S.nx, j = pix - i * S.nx;
+        const int a = r % nn, b = r / nn;
+        const FfConsts K{cf + ((size_t)(p0 + (int)q) * C_total + S.comp_off) * kNC,
+                         comp_type + S.comp_off, comp_plane + S.comp_off};
+        fq.val[e] = source_brightness_ff_at(K, S.ncomp, (float)j - S.cx, (float)i - S.cy, S.h,
+                                            S.h_lo, node_pair(nodes.ud[S.node_off + a]),
+                                            node_pair(nodes.ud[S.node_off + b]));
+    }
+}
+
+// Each pixel's re-traced rays are added, in ray order, to the sum the trace
+// kernel stored.  A warp takes 32 consecutive entries; the lane at the first
+// entry of a pixel walks its run through the warp's registers (shuffles, no
+// dependent global loads) and, for the run that goes on past the warp's
+// entries, through global memory.  The run begun before the warp's first
+// entry belongs to the previous warp.
+__global__ void k_apply_ff(const SysDev *__restrict__ sys, NodeTables nodes,
+                           float *__restrict__ Lbuf, FfQueue fq)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long n = min((long long)*fq.cnt, fq.ecap);
+    const long long wpb = blockDim.x / 32;
+    for (long long e0 = (blockIdx.x * wpb + threadIdx.x / 32) * 32; e0 < n;
+         e0 += (long long)gridDim.x * wpb * 32) {
+        const long long e = e0 + lane;
+        unsigned lin = kFfNone;
+        float w = 0.f, v = 0.f;
+        if (e < n) {
+            const FfEntry E = fq.ent[e];
+            lin = E.lin;
+            if (lin != kFfNone) {
+                w = nodes.w[sys[E.sr >> 8].w2_off + (int)(E.sr & 255u)];
+                v = fq.val[e];
+            }
         }
-        __syncthreads();
-        // a pixel's entries are consecutive and in ray order; the thread at
-        // the first of them adds the run
-        float *L = Lbuf + (size_t)(H.p - p0) * L_stride + S.pix_off;
-        for (int e = threadIdx.x; e < n; e += blockDim.x) {
-            const unsigned t = q_e[e] & 0xffffu;
-            if (e > 0 && (q_e[e - 1] & 0xffffu) == t) continue;
-            const int pt = need ? need[S.need_off + H.start + (int)t] : H.start + (int)t;
-            float acc = L[pt];
-            for (int k = e; k < n && (q_e[k] & 0xffffu) == t; ++k)
-                acc = fmaf(sm.w[q_e[k] >> 16], q_v[k], acc);
-            L[pt] = acc;
+        const unsigned up = __shfl_up_sync(full, lin, 1);
+        const unsigned before = lane == 0 ? (e > 0 && e < n ? fq.ent[e - 1].lin : kFfNone) : up;
+        const bool start = lin != kFfNone && before != lin;
+        float acc = start ? Lbuf[lin] : 0.f;
+        bool open = start;
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+            const unsigned lj = __shfl_sync(full, lin, j);
+            const float wj = __shfl_sync(full, w, j), vj = __shfl_sync(full, v, j);
+            if (open && j >= lane) {
+                if (lj == lin) acc = fmaf(wj, vj, acc);
+                else open = false;
+            }
+        }
+        if (start) {
+            if (open) {
+                const int w2 = sys[fq.ent[e].sr >> 8].w2_off;
+                for (long long k = e0 + 32; k < n && fq.ent[k].lin == lin; ++k)
+                    acc = fmaf(nodes.w[w2 + (int)(fq.ent[k].sr & 255u)], fq.val[k], acc);
+            }
+            Lbuf[lin] = acc;
         }
     }
 }
@@ -1184,7 +1254,7 @@ __global__ void __launch_bounds__(256)
     Lbuf[(size_t)(p - p0) * L_stride + S.pix_off + pix] = acc;
 }
 
-template <int MODE, int G, bool EXACT>
+template <int MODE, int G, bool EXACT, bool GQ>
 static void trace_rows_t(int threads, const SysDev *sys, const int *comp_type,
                          const int *comp_plane, const float *cf, const double *cd,
                          const unsigned char *valid, int P, int C_total, const TraceBlock *blocks,
@@ -1192,12 +1262,13 @@ static void trace_rows_t(int threads, const SysDev *sys, const int *comp_type,
                          void *Lbuf, long long L_stride, cudaStream_t st, FfQueue fq)
 {
     dim3 grid((unsigned)n_blocks, (unsigned)nP);
-    k_trace_rows<MODE, G, EXACT><<<grid, threads, 0, st>>>(sys, comp_type, comp_plane, cf, cd,
-                                                           valid, P, C_total, blocks, need, nodes,
-                                                           p0, (float *)Lbuf, L_stride, fq);
+    k_trace_rows<MODE, G, EXACT, GQ><<<grid, threads, 0, st>>>(
+        sys, comp_type, comp_plane, cf, cd, valid, P, C_total, blocks, need, nodes, p0,
+        (float *)Lbuf, L_stride, fq);
 }
 
-template <int MODE>
+// GQ: the launch has a global float-float queue (MIXED_FF, at most 8 nodes per row)
+template <int MODE, bool GQ>
 static void trace_rows_dispatch(int nn, int threads, const SysDev *sys, const int *comp_type,
                                 const int *comp_plane, const float *cf, const double *cd,
                                 const unsigned char *valid, int P, int C_total,
@@ -1205,19 +1276,19 @@ static void trace_rows_dispatch(int nn, int threads, const SysDev *sys, const in
                                 NodeTables nodes, int p0, int nP, void *Lbuf, long long L_stride,
                                 cudaStream_t st, FfQueue fq)
 {
-#define LENSED_ROWS(GG, EX)                                                                  \
-    trace_rows_t<MODE, GG, EX>(threads, sys, comp_type, comp_plane, cf, cd, valid, P, C_total, \
-                               blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st, fq)
+#define LENSED_ROWS(GG, EX, Q)                                                                  \
+    trace_rows_t<MODE, GG, EX, Q>(threads, sys, comp_type, comp_plane, cf, cd, valid, P, C_total, \
+                                  blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st, fq)
     switch (nn) {
-    case 1: LENSED_ROWS(1, true); break;
-    case 2: LENSED_ROWS(2, true); break;
-    case 3: LENSED_ROWS(3, true); break;
-    case 4: LENSED_ROWS(4, true); break;
-    case 5: LENSED_ROWS(5, true); break;
-    case 6: LENSED_ROWS(6, true); break;
-    case 7: LENSED_ROWS(7, true); break;
-    case 8: LENSED_ROWS(8, true); break;
-    default: LENSED_ROWS(4, false); break;
+    case 1: LENSED_ROWS(1, true, GQ); break;
+    case 2: LENSED_ROWS(2, true, GQ); break;
+    case 3: LENSED_ROWS(3, true, GQ); break;
+    case 4: LENSED_ROWS(4, true, GQ); break;
+    case 5: LENSED_ROWS(5, true, GQ); break;
+    case 6: LENSED_ROWS(6, true, GQ); break;
+    case 7: LENSED_ROWS(7, true, GQ); break;
+    case 8: LENSED_ROWS(8, true, GQ); break;
+    default: LENSED_ROWS(4, false, false); break;
     }
 #undef LENSED_ROWS
 }
@@ -1235,23 +1306,29 @@ void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const
                                                          valid, P, C_total, blocks, need, nodes,
                                                          p0, (double *)Lbuf, L_stride);
     } else if (precision == LENSED_PREC_MIXED_FF) {
-        // the split needs the block-wide queue, i.e. at most 8 nodes per row
-        const bool split = cfg.ff_split && q.cnt && q.hdr && q.ent && nn >= 1 && nn <= 8;
-        if (split) cudaMemsetAsync(q.cnt, 0, 3 * sizeof(unsigned long long), st);
-        trace_rows_dispatch<LENSED_PREC_MIXED_FF>(nn, cfg.trace_threads, sys, comp_type,
-                                                  comp_plane, cf, cd, valid, P, C_total, blocks,
-                                                  n_blocks, need, nodes, p0, nP, Lbuf, L_stride,
-                                                  st, split ? q : FfQueue{});
+        // the global queue needs the deferral mask, i.e. at most 8 nodes per
+        // row, and 32-bit pixel indices into this launch's scratch
+        const bool split = cfg.ff_split && q.cnt && q.ent && q.val && nn >= 1 && nn <= 8 &&
+                           (long long)nP * L_stride < (long long)kFfNone;
         if (split) {
-            const long long want = (long long)std::max(g_sm_count, 1) * 8;
-            const unsigned grid = (unsigned)std::max(1LL, std::min(want, q.hcap));
-            k_retrace_ff<<<grid, kFfThreads, 0, st>>>(sys, comp_type, comp_plane, cf, cd, C_total,
-                                                     need, nodes, p0, (float *)Lbuf, L_stride, q);
+            cudaMemsetAsync(q.cnt, 0, sizeof(unsigned long long), st);
+            trace_rows_dispatch<LENSED_PREC_MIXED_FF, true>(
+                nn, cfg.trace_threads, sys, comp_type, comp_plane, cf, cd, valid, P, C_total,
+                blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st, q);
+            const unsigned grid = (unsigned)std::max(1, g_sm_count) * 8;
+            k_retrace_ff<<<grid, kFfThreads, 0, st>>>(sys, comp_type, comp_plane, cf, C_total,
+                                                     nodes, p0, (unsigned)L_stride, q);
+            k_apply_ff<<<grid, kFfThreads, 0, st>>>(sys, nodes, (float *)Lbuf, q);
+        } else {
+            trace_rows_dispatch<LENSED_PREC_MIXED_FF, false>(
+                nn, cfg.trace_threads, sys, comp_type, comp_plane, cf, cd, valid, P, C_total,
+                blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st, FfQueue{});
         }
     } else {
-        trace_rows_dispatch<LENSED_PREC_FP32>(nn, cfg.trace_threads, sys, comp_type, comp_plane,
-                                              cf, cd, valid, P, C_total, blocks, n_blocks, need,
-                                              nodes, p0, nP, Lbuf, L_stride, st, FfQueue{});
+        trace_rows_dispatch<LENSED_PREC_FP32, false>(nn, cfg.trace_threads, sys, comp_type,
+                                                     comp_plane, cf, cd, valid, P, C_total, blocks,
+                                                     n_blocks, need, nodes, p0, nP, Lbuf, L_stride,
+                                                     st, FfQueue{});
     }
 }
 

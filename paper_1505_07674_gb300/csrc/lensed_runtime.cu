@@ -446,7 +446,6 @@ const Candidate kCandidates[] = {
 };
 constexpr int kAllCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
 constexpr int kBaseCandidates = 6;
-constexpr int kMinTraceItems = 64;  // smallest trace block of any candidate
 
 // Instantiated graphs kept per model (keyed by point count, buffers and
 // configuration; the least recently used is dropped beyond this).
@@ -522,8 +521,8 @@ struct lensed_model {
     int chunk_P = 0;
     // MIXED_FF second-pass queue (one trace launch at a time)
     DevBuf<unsigned long long> ffq_cnt;
-    DevBuf<FfHeader> ffq_hdr;
-    DevBuf<unsigned> ffq_ent;
+    DevBuf<FfEntry> ffq_ent;
+    DevBuf<float> ffq_val;
     // render buffers (one point)
     DevBuf<float> rcf;
     DevBuf<double> rcd;
@@ -533,6 +532,7 @@ struct lensed_model {
     DevBuf<double> stage_params, stage_out;
 
     int cfg_index = -1;  // autotuned candidate, -1 = default
+    long long ffq_limit = -1;  // test hook: entries the second pass may take (-1: all)
     cudaStream_t cap_stream = nullptr;
     std::vector<GraphEntry> graphs;
     unsigned long long graph_clock = 0;
@@ -545,7 +545,8 @@ struct lensed_model {
     FfQueue ffq() const
     {
         if (!ffq_cnt.p) return FfQueue{};
-        return {ffq_cnt.p, ffq_hdr.p, ffq_ent.p, (long long)ffq_hdr.n, (long long)ffq_ent.n};
+        const long long n = (long long)ffq_ent.n;
+        return {ffq_cnt.p, ffq_ent.p, ffq_val.p, ffq_limit >= 0 ? std::min(ffq_limit, n) : n};
     }
     size_t elem() const { return precision == LENSED_PREC_FP64 ? sizeof(double) : sizeof(float); }
     // FP32 modes with fixed lights: the chi^2 path traces without them and
@@ -637,18 +638,14 @@ int ensure_capacity(lensed_model *m, int P)
     chunk = std::min<size_t>(chunk, (size_t)P);
     if ((rc = m->Lbuf.alloc(chunk * per_point))) return rc;
     if (m->precision == LENSED_PREC_MIXED_FF) {
-        // headers: one per trace block and point of a chunk at the smallest
-        // block size; entries: every traced ray of a chunk, capped
-        long long blocks = 0, rays = 0;
-        for (int s = 0; s < m->n_sys; ++s) {
-            blocks += (m->need_count[s] + kMinTraceItems - 1) / kMinTraceItems;
+        // the second pass's queue: room for every traced ray of a chunk, capped
+        long long rays = 0;
+        for (int s = 0; s < m->n_sys; ++s)
             rays += (long long)m->need_count[s] * m->n_nodes[s] * m->n_nodes[s];
-        }
-        if ((rc = m->ffq_cnt.alloc(3))) return rc;
-        if ((rc = m->ffq_hdr.alloc((size_t)std::max(1LL, blocks * (long long)chunk)))) return rc;
-        if ((rc = m->ffq_ent.alloc(
-                 (size_t)std::max(1LL, std::min(rays * (long long)chunk, kFfEntryCap)))))
-            return rc;
+        const size_t cap = (size_t)std::max(1LL, std::min(rays * (long long)chunk, kFfEntryCap));
+        if ((rc = m->ffq_cnt.alloc(1))) return rc;
+        if ((rc = m->ffq_ent.alloc(cap))) return rc;
+        if ((rc = m->ffq_val.alloc(cap))) return rc;
     }
     m->chunk_P = (int)chunk;
     m->cap_P = P;
@@ -732,6 +729,15 @@ extern "C" long long lensed_debug_fail_alloc(long long after)
 {
     g_alloc_budget.store(after < 0 ? -1 : after);
     return g_live_buffers.load();
+}
+
+extern "C" int lensed_debug_ff_queue_cap(lensed_model *m, long long cap)
+{
+    if (check_model(m)) return LENSED_E_ARG;
+    cudaDeviceSynchronize();
+    m->clear_graphs();  // captured launches hold the queue's capacity
+    m->ffq_limit = cap < 0 ? -1 : cap;
+    return LENSED_OK;
 }
 
 // Low-rank form of a normalised, flipped PSF F [m][n] (m = 2p+1 rows):
@@ -1684,11 +1690,11 @@ extern "C" int lensed_batch_plan(lensed_model *m, int P, int *launches, int *chu
     int rc = ensure_capacity(m, P);
     if (rc) return rc;
     const int chunks = (P + m->chunk_P - 1) / m->chunk_P;
-    // a MIXED_FF second pass: one more kernel per trace group of at most 8
-    // nodes per row
+    // a MIXED_FF second pass: two more kernels (re-trace, apply) per trace
+    // group of at most 8 nodes per row
     int second = 0;
     if (m->precision == LENSED_PREC_MIXED_FF && m->cfg().ff_split && m->ffq_cnt.p)
-        for (const TraceGroup &g : m->trace_groups) second += g.nn >= 1 && g.nn <= 8;
+        for (const TraceGroup &g : m->trace_groups) second += 2 * (g.nn >= 1 && g.nn <= 8);
     *launches = 3 + chunks * ((int)m->trace_groups.size() + (int)m->psf_groups.size() +
                               (is_mixed(m->precision) ? 1 : 0) + second);
     *chunk_points = m->chunk_P;

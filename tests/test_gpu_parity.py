@@ -178,6 +178,33 @@ def test_mixed_ff_second_pass_is_bit_identical(case):
     assert np.isfinite(a).mean() > 0.5
 
 
+@pytest.mark.parametrize("case", ["c2_96x80", "c3_six_systems"])
+def test_mixed_ff_full_queue_falls_back_bit_identically(case):
+    # The second pass's global queue holds a bounded number of rays.  A warp
+    # whose rays do not fit marks its slots empty and re-traces the rays
+    # itself; the test hook caps the queue at 0, at sizes that leave a warp
+    # straddling the end, and unbounded: the same bits every time.
+    from paper_1505_07674_gb300 import _native as N
+    specs = _second_pass_cases()[case]()
+    specs = specs if isinstance(specs, list) else [specs]
+    obs = [O.mock_observation(s) for s in specs]
+    m = lensed().Model(specs if len(specs) > 1 else specs[0],
+                       obs if len(obs) > 1 else obs[0], precision="mixed_ff")
+    n_par = max(s["n_params"] for s in specs)
+    P = 40
+    pts = np.zeros((len(specs), P, n_par))
+    for k, s in enumerate(specs):
+        pts[k, :, :s["n_params"]] = np.vstack([s["truth"], W.draw_points(s, P - 1, 90 + k)])
+    m.set_config(1)
+    ref = m.loglike_batch(pts).cpu().numpy()
+    m.set_config(7)
+    for cap in (0, 1, 37, 1000, 20_000, -1):
+        assert N.lib().lensed_debug_ff_queue_cap(m._h, cap) == 0
+        got = m.loglike_batch(pts).cpu().numpy()
+        assert np.array_equal(got, ref), (case, cap, np.nanmax(np.abs(got - ref)))
+    assert np.isfinite(ref).mean() > 0.5
+
+
 def test_second_pass_configurations_are_offered_for_mixed_ff_only(c1):
     spec, obs, _ = c1
     for precision, n in (("fp32", 6), ("mixed", 6), ("mixed_ff", 12), ("fp64", 6)):
