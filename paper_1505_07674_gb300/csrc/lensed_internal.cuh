@@ -97,11 +97,19 @@ struct NodeTables {
 };
 
 // PSF-kernel block table entry: system and tile origin.
+// An output tile of the PSF kernels.  live_rows: bit r set when output row
+// i0 + r carries a weighted pixel; live_warps: bit w set when the 16 x 16
+// outputs of warp w (rows 16 (w >> 2) .., columns 16 (w & 3) ..) carry one
+// (both all-ones for render tiles).  The mask is fixed per model, so these
+// are computed once on the host.
 struct PsfBlock {
     int sys;
     int tile;  // global index into the partial-sum columns
     int i0, j0;
+    unsigned live_rows, live_warps;
 };
+static_assert(kTileH == 32 && kTileW == 64 && kPsfThreads == 256,
+              "PsfBlock masks: 32 output rows, 8 warps of 16 x 16 outputs");
 
 struct LaunchCfg {
     int trace_threads;  // threads per trace block, one pixel each

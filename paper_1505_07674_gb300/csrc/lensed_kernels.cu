@@ -1532,14 +1532,43 @@ static __host__ __device__ __forceinline__ int psf_row_stride(int q)
     return (kTileW + 2 * q + 3) & ~3;
 }
 
+// The separable kernel's strides.  Staged tile: psf_row_stride with an odd
+// number of 16-byte quads, so the two rows one 8-lane phase of its row pass
+// reads fall on different banks.  Row-pass output: 72 floats, 18 quads (2
+// mod 8), so the 4 rows x 2 interleaved quads of a column-pass phase do too.
+static __host__ __device__ __forceinline__ int psf_sep_row_stride(int q)
+{
+    return psf_row_stride(q) | 4;
+}
+constexpr int kHStride = kTileW + 8;
+
 // Row stride of the staged PSF: 2q+1 taps rounded up to a multiple of 4 so
 // each row starts 16-byte aligned.
 static __host__ __device__ __forceinline__ int psf_tap_stride(int q) { return (2 * q + 1 + 3) & ~3; }
 
+// Asynchronous global -> shared copy of one element (cp.async, cached in
+// L1: neighbouring tiles read the same halo), and the wait for all of a
+// thread's copies.
+__device__ __forceinline__ void cp_async_elem(float *dst, const float *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double *dst, const double *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
 // Stage rows x cols of an image into shared memory (row stride `stride`),
 // from image row i0 and column j0 on, indices clamped to the image (Eq. 15's
 // edge padding): one warp per row, consecutive lanes on consecutive columns
-// (coalesced), no integer division.
+// (coalesced), no integer division.  The copies are asynchronous, so every
+// load of the tile is in flight at once; the caller's barrier follows.
 template <typename T>
 __device__ __forceinline__ void stage_tile(T *s, int stride, const T *__restrict__ L, int nx,
                                            int ny, int i0, int j0, int rows, int cols)
@@ -1548,8 +1577,9 @@ __device__ __forceinline__ void stage_tile(T *s, int stride, const T *__restrict
     for (int r = warp; r < rows; r += (int)(blockDim.x >> 5)) {
         const T *src = L + (size_t)min(max(i0 + r, 0), ny - 1) * nx;
         T *dst = s + r * stride;
-        for (int c = lane; c < cols; c += 32) dst[c] = src[min(max(j0 + c, 0), nx - 1)];
+        for (int c = lane; c < cols; c += 32) cp_async_elem(dst + c, src + min(max(j0 + c, 0), nx - 1));
     }
+    cp_async_wait_all();
 }
 
 template <typename T, int Q>
@@ -1604,14 +1634,7 @@ __global__ void __launch_bounds__(kPsfThreads)
     const int jb = pb.j0 + tcol;
     // chi^2 mode: a warp none of whose outputs carries weight skips the
     // convolution (its partial is zero)
-    bool live = true;
-    if (partial) {
-        bool any = false;
-        if (i < ny)
-            for (int o = 0; o < kOutPerThread; ++o)
-                if (jb + o < nx && weight[S.pix_off + (size_t)i * nx + jb + o] > T(0)) any = true;
-        live = __any_sync(0xffffffffu, any);
-    }
+    const bool live = !partial || ((pb.live_warps >> warp) & 1u);
     T acc[kOutPerThread];
 #pragma unroll
     for (int o = 0; o < kOutPerThread; ++o) acc[o] = T(0);
@@ -1680,7 +1703,7 @@ __global__ void __launch_bounds__(kPsfThreads)
 // (2p+1) multiply-adds per term and output instead of (2p+1)(2q+1).  The
 // output mapping, the warp skip and the chi^2 reduction are those of k_psf.
 template <int Q>
-__global__ void __launch_bounds__(kPsfThreads)
+__global__ void __launch_bounds__(kPsfThreads, 4)
     k_psf_sep(const SysDev *__restrict__ sys, const float *__restrict__ psf,
               const float *__restrict__ data, const float *__restrict__ weight,
               const unsigned char *__restrict__ valid, int P, const PsfBlock *__restrict__ blocks,
@@ -1696,11 +1719,11 @@ __global__ void __launch_bounds__(kPsfThreads)
     const bool ok = valid[(size_t)pb.sys * P + p] != 0;
     const int Ph = S.psf_p, R = S.psf_rank;
     const int rows = kTileH + 2 * Ph;
-    const int stride = psf_row_stride(Q);
+    const int stride = psf_sep_row_stride(Q);
     const int nx = S.nx, ny = S.ny;
     float *s_L = reinterpret_cast<float *>(smem_raw);
-    float *s_H = s_L + (size_t)rows * stride;        // [R][rows][kTileW]
-    float *s_c = s_H + (size_t)R * rows * kTileW;    // [R][2p+1]
+    float *s_H = s_L + (size_t)rows * stride;        // [R][rows][kHStride]
+    float *s_c = s_H + (size_t)R * rows * kHStride;  // [R][2p+1]
     float *s_r = s_c + R * (2 * Ph + 1);             // [R][WS]
 
     if (!ok) {
@@ -1722,40 +1745,25 @@ __global__ void __launch_bounds__(kPsfThreads)
     }
     const float *L = Lbuf + (size_t)(p - p0) * L_stride + S.pix_off;
     stage_tile(s_L, stride, L, nx, ny, pb.i0 - Ph, pb.j0 - Q, rows, kTileW + 2 * Q);
-    // chi^2 mode: output rows of the tile with a weighted pixel; the row pass
-    // is needed only within p rows of one
-    __shared__ unsigned char s_live[kTileH + 2 * LENSED_MAX_PSF_HALF];
-    if (partial) {
-        __shared__ unsigned char s_orow[kTileH];
-        const int warp0 = threadIdx.x >> 5, lane0 = threadIdx.x & 31;
-        for (int r = warp0; r < kTileH; r += kPsfThreads / 32) {
-            const int i = pb.i0 + r;
-            bool any = false;
-            if (i < ny)
-                for (int c = lane0; c < kTileW; c += 32) {
-                    const int j = pb.j0 + c;
-                    any = any || (j < nx && weight[S.pix_off + (size_t)i * nx + j] > 0.f);
-                }
-            any = __any_sync(0xffffffffu, any);
-            if (lane0 == 0) s_orow[r] = any ? 1 : 0;
-        }
-        __syncthreads();
-        for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-            bool need = false;
-            for (int o = max(0, r - 2 * Ph); o <= min(kTileH - 1, r); ++o) need = need || s_orow[o];
-            s_live[r] = need ? 1 : 0;
-        }
-    }
     __syncthreads();
 
-    // pass 1: rows, kOutPerThread outputs per item (the kSeg segments of a row
-    // on kSeg consecutive threads)
+    // pass 1: rows, kOutPerThread outputs per item.  A warp takes 4 rows x 8
+    // segments; each 8-lane phase 2 adjacent rows x 4 segments.
     constexpr int kSeg = kTileW / kOutPerThread;
-    static_assert(kPsfThreads % kSeg == 0, "row-pass mapping");
-    const int seg = threadIdx.x & (kSeg - 1), rgrp = threadIdx.x / kSeg;
+    static_assert(kSeg == 8 && kPsfThreads == 256, "row-pass mapping");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int phase = lane >> 3;
+    const int seg = 4 * (phase >> 1) + (lane & 3);
+    const int rgrp = warp * 4 + 2 * (phase & 1) + ((lane >> 2) & 1);
     for (int t = 0; t < R; ++t)
     for (int r = rgrp; r < rows; r += kPsfThreads / kSeg) {
-        if (partial && !s_live[r]) continue;
+        if (partial) {
+            // chi^2 mode: staged row r feeds output rows r - 2p .. r; skip it
+            // when none of them carries a weighted pixel
+            const int lo = max(0, r - 2 * Ph), n = min(kTileH - 1, r) - lo + 1;
+            const unsigned win = n >= 32 ? ~0u : (1u << n) - 1u;
+            if (n <= 0 || ((pb.live_rows >> lo) & win) == 0u) continue;
+        }
         const int j0 = seg * kOutPerThread;
         const float *srow = s_L + r * stride + j0;
         float lv[kOutPerThread + 2 * Q];
@@ -1770,25 +1778,29 @@ __global__ void __launch_bounds__(kPsfThreads)
 #pragma unroll
             for (int o = 0; o < kOutPerThread; ++o) acc[o] = fmaf(f, lv[o + l], acc[o]);
         }
-        float *h = s_H + ((size_t)t * rows + r) * kTileW + j0;
-#pragma unroll
-        for (int o = 0; o < kOutPerThread; ++o) h[o] = acc[o];
+        float4 *h = reinterpret_cast<float4 *>(s_H + ((size_t)t * rows + r) * kHStride + j0);
+        h[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        h[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
     }
     __syncthreads();
 
-    // pass 2: columns, with the output mapping of k_psf
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // pass 2: columns.  Warp w owns the 16 x 16 outputs of k_psf's warp w;
+    // a lane 8 outputs of one row, in two quads 8 columns apart (columns
+    // jb + 0..3 and jb + 8..11)
     const int tr = (warp >> 2) * 16 + (lane >> 1);
-    const int tcol = (warp & 3) * 16 + (lane & 1) * kOutPerThread;
+    const int tq = (warp & 3) * 16 + (lane & 1) * 4;
     const int i = pb.i0 + tr;
-    const int jb = pb.j0 + tcol;
-    bool live = true;
-    if (partial) {
-        bool any = false;
-        if (i < ny)
-            for (int o = 0; o < kOutPerThread; ++o)
-                if (jb + o < nx && weight[S.pix_off + (size_t)i * nx + jb + o] > 0.f) any = true;
-        live = __any_sync(0xffffffffu, any);
+    const int jb = pb.j0 + tq;
+    const bool live = !partial || ((pb.live_warps >> warp) & 1u);
+    // chi^2 mode: the epilogue's data and weights, loaded before the sums
+    float dv[kOutPerThread], wv[kOutPerThread];
+#pragma unroll
+    for (int o = 0; o < kOutPerThread; ++o) {
+        const int j = jb + (o & 3) + 8 * (o >> 2);
+        const bool in = partial && live && i < ny && j < nx;
+        const size_t pix = S.pix_off + (size_t)i * nx + j;
+        wv[o] = in ? weight[pix] : 0.f;
+        dv[o] = in ? data[pix] : 0.f;
     }
     float acc[kOutPerThread];
 #pragma unroll
@@ -1796,9 +1808,9 @@ __global__ void __launch_bounds__(kPsfThreads)
     for (int t = 0; live && t < R; ++t) {
         for (int m = 0; m <= 2 * Ph; ++m) {
             const float c = s_c[t * (2 * Ph + 1) + m];
-            const float4 *h4 = reinterpret_cast<const float4 *>(
-                s_H + ((size_t)t * rows + tr + m) * kTileW + tcol);
-            const float4 a = h4[0], b = h4[1];
+            const float *hr = s_H + ((size_t)t * rows + tr + m) * kHStride + tq;
+            const float4 a = *reinterpret_cast<const float4 *>(hr);
+            const float4 b = *reinterpret_cast<const float4 *>(hr + 8);
             acc[0] = fmaf(c, a.x, acc[0]);
             acc[1] = fmaf(c, a.y, acc[1]);
             acc[2] = fmaf(c, a.z, acc[2]);
@@ -1812,18 +1824,11 @@ __global__ void __launch_bounds__(kPsfThreads)
 
     if (partial) {
         double chi = 0.0;
-        if (live && i < ny) {
 #pragma unroll
-            for (int o = 0; o < kOutPerThread; ++o) {
-                const int j = jb + o;
-                if (j < nx) {
-                    const size_t pix = S.pix_off + (size_t)i * nx + j;
-                    const float w = weight[pix];
-                    if (w > 0.f) {
-                        const float r = data[pix] - acc[o];
-                        chi += (double)(w * r * r);
-                    }
-                }
+        for (int o = 0; o < kOutPerThread; ++o) {
+            if (wv[o] > 0.f) {
+                const float r = dv[o] - acc[o];
+                chi += (double)(wv[o] * r * r);
             }
         }
         __shared__ double s_red[kPsfThreads / 32];
@@ -1838,7 +1843,7 @@ __global__ void __launch_bounds__(kPsfThreads)
     } else if (out && i < ny) {
 #pragma unroll
         for (int o = 0; o < kOutPerThread; ++o) {
-            const int j = jb + o;
+            const int j = jb + (o & 3) + 8 * (o >> 2);
             if (j < nx) out[(size_t)i * nx + j] = acc[o];
         }
     }
@@ -1846,8 +1851,8 @@ __global__ void __launch_bounds__(kPsfThreads)
 
 // Largest dynamic shared memory of a k_psf_sep instance (P = Q = 15, rank 3).
 static constexpr int kPsfSepSmemMax =
-    ((kTileH + 2 * LENSED_MAX_PSF_HALF) * ((kTileW + 2 * LENSED_MAX_PSF_HALF + 3) & ~3) +
-     3 * (kTileH + 2 * LENSED_MAX_PSF_HALF) * kTileW + 3 * (2 * LENSED_MAX_PSF_HALF + 1) +
+    ((kTileH + 2 * LENSED_MAX_PSF_HALF) * (((kTileW + 2 * LENSED_MAX_PSF_HALF + 3) & ~3) | 4) +
+     3 * (kTileH + 2 * LENSED_MAX_PSF_HALF) * kHStride + 3 * (2 * LENSED_MAX_PSF_HALF + 1) +
      3 * ((2 * LENSED_MAX_PSF_HALF + 1 + 3) & ~3)) *
     (int)sizeof(float);
 
@@ -1915,7 +1920,7 @@ static void psf_sep_launch_t(int p_max, int r_max, const SysDev *sys, const floa
                              float *out, cudaStream_t st)
 {
     const int rows = kTileH + 2 * p_max;
-    const size_t smem = ((size_t)rows * psf_row_stride(Q) + (size_t)r_max * rows * kTileW +
+    const size_t smem = ((size_t)rows * psf_sep_row_stride(Q) + (size_t)r_max * rows * kHStride +
                          (size_t)r_max * (2 * p_max + 1) + (size_t)r_max * psf_tap_stride(Q)) *
                         sizeof(float);
     dim3 grid((unsigned)n_blocks, (unsigned)nP);

@@ -1179,16 +1179,22 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         S.tile_off = T_total;
         for (int ty = 0; ty < S.tiles_y; ++ty)
             for (int tx = 0; tx < S.tiles_x; ++tx) {
-                bool any = false;
-                for (int i = ty * kTileH; i < std::min(ny, (ty + 1) * kTileH) && !any; ++i)
-                    for (int j = tx * kTileW; j < std::min(nx, (tx + 1) * kTileW); ++j)
+                unsigned live_rows = 0u, live_warps = 0u;
+                for (int r = 0; r < kTileH; ++r) {
+                    const int i = ty * kTileH + r;
+                    if (i >= ny) break;
+                    for (int c = 0; c < kTileW; ++c) {
+                        const int j = tx * kTileW + c;
+                        if (j >= nx) break;
                         if (w[(size_t)i * nx + j] > 0.0) {
-                            any = true;
-                            break;
+                            live_rows |= 1u << r;
+                            live_warps |= 1u << ((r / 16) * 4 + c / 16);
                         }
-                if (any)
+                    }
+                }
+                if (live_rows)
                     chi_tiles[s].push_back({s, T_total + (int)chi_tiles[s].size(), ty * kTileH,
-                                            tx * kTileW});
+                                            tx * kTileW, live_rows, live_warps});
             }
         S.n_tiles = (int)chi_tiles[s].size();
         T_total += S.n_tiles;
@@ -1293,7 +1299,7 @@ extern "C" int lensed_create_model(const lensed_system_desc *systems, int n_syst
         m->render_psf_off[s] = (int)m->render_psf_h.size();
         for (int ty = 0; ty < sh[s].tiles_y; ++ty)
             for (int tx = 0; tx < sh[s].tiles_x; ++tx)
-                m->render_psf_h.push_back({s, 0, ty * kTileH, tx * kTileW});
+                m->render_psf_h.push_back({s, 0, ty * kTileH, tx * kTileW, ~0u, ~0u});
         m->render_psf_cnt[s] = (int)m->render_psf_h.size() - m->render_psf_off[s];
     }
 
