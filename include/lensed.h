@@ -300,13 +300,15 @@ int lensed_loglike_batch_noalloc(lensed_model *m, const double *params, int P,
 
 /* Time the candidate launch configurations (trace block size; PSF applied
  * directly or, where the PSF has numerical rank <= 3, as separable passes;
+ * the trace as one CTA per (trace block, point) or as a persistent,
+ * work-queued launch whose resident CTAs take those items from a counter;
  * for LENSED_PREC_MIXED_FF also whether the float-float re-traces run inside
  * the trace blocks or in a second kernel) on a batch of P points drawn
  * inside the given DEVICE parameter array (same layout as
  * lensed_loglike_batch) and keep the fastest for later calls.  The trace
- * block size and the place of the re-traces never change a result; the PSF
- * mode changes the FP32 summation order of Eq. 15 (differences at the float
- * rounding level).  Synchronous. */
+ * block size, the launch form and the place of the re-traces never change a
+ * result; the PSF mode changes the FP32 summation order of Eq. 15
+ * (differences at the float rounding level).  Synchronous. */
 int lensed_autotune(lensed_model *m, const double *params, int P, void *stream);
 
 /* Index of the configuration in use (-1: default) and its description, for
@@ -333,9 +335,12 @@ int lensed_eval_sie_trig(const float *n, const float *d, long long count, float 
 
 /* Use configuration `index` (0 .. n-1 as lensed_tuned_config numbers them,
  * -1 = default) instead of the autotuner's choice; returns the number of
- * configurations n (6, and 12 for LENSED_PREC_MIXED_FF, whose configurations
- * 6 + k run configuration k with the float-float re-traces in a second
- * kernel), or LENSED_E_ARG for an index out of range. */
+ * configurations n, or LENSED_E_ARG for an index out of range.  n = 12:
+ * 0-5 = trace blocks of 128, 256, 64 pixels with the direct PSF, then the
+ * same three with separable passes; 6-11 = 0-5 with the trace as a
+ * persistent, work-queued launch.  LENSED_PREC_MIXED_FF: n = 24, and
+ * 12 + k runs configuration k with the float-float re-traces in a second
+ * kernel. */
 int lensed_set_config(lensed_model *m, int index);
 
 /* Launch plan of one lensed_loglike_batch call with P points: number of

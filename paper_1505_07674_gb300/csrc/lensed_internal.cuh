@@ -115,6 +115,7 @@ struct LaunchCfg {
     int trace_threads;  // threads per trace block, one pixel each
     int psf_sep;        // 1: PSFs of low rank run as separable passes
     int ff_split;       // 1 (MIXED_FF): float-float re-traces in a second kernel
+    int persistent;     // 1: the trace runs as a persistent, work-queued launch
 };
 
 // One deferred float-float ray of a trace launch: lin = the pixel's index in
@@ -167,7 +168,8 @@ void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const
                   const int *comp_plane, const float *cf, const double *cd,
                   const unsigned char *valid, int P, int C_total, const TraceBlock *blocks,
                   int n_blocks, const int *need, NodeTables nodes, int p0, int nP, void *Lbuf,
-                  long long L_stride, cudaStream_t st, FfQueue q = FfQueue{});
+                  long long L_stride, cudaStream_t st, FfQueue q = FfQueue{},
+                  unsigned long long *work = nullptr);
 
 // One-time kernel attributes (dynamic shared memory limits); call before
 // any launch or capture.

@@ -909,18 +909,23 @@ constexpr int kQCap = 2048;       // deferred float-float rays per trace block
 // parallelism.  EXACT: the rule has exactly G nodes per row (no guards).
 // GQ (MIXED_FF, EXACT): the float-float re-traces go to the launch's global
 // queue, appended warp by warp, for k_retrace_ff and k_apply_ff.
+// The work of one trace block tb at point p (every thread of the CTA calls
+// it; it returns to the caller, which may take another item).  stage = false:
+// the shared constants already hold tb's system at point p.
 template <int MODE, int G, bool EXACT, bool GQ>
-__global__ void __launch_bounds__(256)
-    k_trace_rows(const SysDev *__restrict__ sys, const int *__restrict__ comp_type,
-                 const int *__restrict__ comp_plane, const float *__restrict__ cf,
-                 const double *__restrict__ cd, const unsigned char *__restrict__ valid, int P,
-                 int C_total, const TraceBlock *__restrict__ blocks, const int *__restrict__ need,
-                 NodeTables nodes, int p0, float *__restrict__ Lbuf, long long L_stride,
-                 FfQueue fq)
+__device__ __forceinline__ void trace_item(const SysDev *__restrict__ sys,
+                                           const int *__restrict__ comp_type,
+                                           const int *__restrict__ comp_plane,
+                                           const float *__restrict__ cf,
+                                           const double *__restrict__ cd,
+                                           const unsigned char *__restrict__ valid, int P,
+                                           int C_total, const int *__restrict__ need,
+                                           const NodeTables &nodes, int p0,
+                                           float *__restrict__ Lbuf, long long L_stride,
+                                           const FfQueue &fq, const TraceBlock tb, const int p,
+                                           const bool stage = true)
 {
     __shared__ __align__(16) TraceSmem sm;
-    const TraceBlock tb = blocks[blockIdx.x];
-    const int p = p0 + blockIdx.y;
     if (!valid[(size_t)tb.sys * P + p]) return;
     const SysDev &S = sys[tb.sys];
     const size_t cbase = ((size_t)p * C_total + S.comp_off) * kNC;
@@ -935,7 +940,7 @@ __global__ void __launch_bounds__(256)
     __shared__ unsigned short q_t[kQueue ? kQCap : 1];
     __shared__ unsigned char q_r[kQueue ? kQCap : 1];
     __shared__ float q_v[kQueue ? kQCap : 1];
-    stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, false, false, nodes);
+    if (stage) stage_point(sm, S, comp_type, comp_plane, cf, cd, cbase, false, false, nodes);
     if (kQueue && threadIdx.x == 0) q_n = 0;
     __syncthreads();
 
@@ -1136,6 +1141,59 @@ __global__ void __launch_bounds__(256)
     if (active) Lbuf[(size_t)(p - p0) * L_stride + S.pix_off + pix] = acc;
 }
 
+template <int MODE, int G, bool EXACT, bool GQ>
+__global__ void __launch_bounds__(256)
+    k_trace_rows(const SysDev *__restrict__ sys, const int *__restrict__ comp_type,
+                 const int *__restrict__ comp_plane, const float *__restrict__ cf,
+                 const double *__restrict__ cd, const unsigned char *__restrict__ valid, int P,
+                 int C_total, const TraceBlock *__restrict__ blocks, const int *__restrict__ need,
+                 NodeTables nodes, int p0, float *__restrict__ Lbuf, long long L_stride,
+                 FfQueue fq)
+{
+    trace_item<MODE, G, EXACT, GQ>(sys, comp_type, comp_plane, cf, cd, valid, P, C_total, need,
+                                   nodes, p0, Lbuf, L_stride, fq, blocks[blockIdx.x],
+                                   p0 + (int)blockIdx.y);
+}
+
+// The same work as a persistent, work-queued launch: a grid sized to the
+// resident CTAs of the GPU takes (trace block, point) items, point-major,
+// kPqGrab at a time from the counter *work (zeroed before the launch) until
+// n_items are done, staging a point's constants only when the system or the
+// point changes.
+constexpr int kPqGrab = 4;
+template <int MODE, int G, bool EXACT, bool GQ>
+__global__ void __launch_bounds__(256)
+    k_trace_rows_pq(const SysDev *__restrict__ sys, const int *__restrict__ comp_type,
+                    const int *__restrict__ comp_plane, const float *__restrict__ cf,
+                    const double *__restrict__ cd, const unsigned char *__restrict__ valid, int P,
+                    int C_total, const TraceBlock *__restrict__ blocks,
+                    const int *__restrict__ need, NodeTables nodes, int p0,
+                    float *__restrict__ Lbuf, long long L_stride, FfQueue fq, int n_blocks,
+                    long long n_items, unsigned long long *__restrict__ work)
+{
+    __shared__ long long s_item;
+    int cur_sys = -1, cur_p = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(work, (unsigned long long)kPqGrab);
+        __syncthreads();
+        const long long first = s_item;
+        __syncthreads();  // read by all before thread 0 takes the next ones
+        if (first >= n_items) return;
+        const long long last = min(first + kPqGrab, n_items);
+        for (long long item = first; item < last; ++item) {
+            const int q = (int)(item / n_blocks);
+            const TraceBlock tb = blocks[item - (long long)q * n_blocks];
+            const int p = p0 + q;
+            trace_item<MODE, G, EXACT, GQ>(sys, comp_type, comp_plane, cf, cd, valid, P, C_total,
+                                           need, nodes, p0, Lbuf, L_stride, fq, tb, p,
+                                           tb.sys != cur_sys || p != cur_p);
+            cur_sys = tb.sys;
+            cur_p = p;
+            __syncthreads();  // the item is done with the shared arrays
+        }
+    }
+}
+
 // MIXED_FF second pass over a trace launch's global queue: one thread per
 // entry (the rays of many warps and points fill whole warps here) reads its
 // point's constants from global memory and writes the ray's source-plane
@@ -1254,17 +1312,33 @@ __global__ void __launch_bounds__(256)
     Lbuf[(size_t)(p - p0) * L_stride + S.pix_off + pix] = acc;
 }
 
+// work == nullptr: one CTA per (trace block, point); else a persistent grid
+// of as many CTAs as fit on the GPU at once, fed by the counter *work
 template <int MODE, int G, bool EXACT, bool GQ>
 static void trace_rows_t(int threads, const SysDev *sys, const int *comp_type,
                          const int *comp_plane, const float *cf, const double *cd,
                          const unsigned char *valid, int P, int C_total, const TraceBlock *blocks,
                          int n_blocks, const int *need, NodeTables nodes, int p0, int nP,
-                         void *Lbuf, long long L_stride, cudaStream_t st, FfQueue fq)
+                         void *Lbuf, long long L_stride, cudaStream_t st, FfQueue fq,
+                         unsigned long long *work)
 {
-    dim3 grid((unsigned)n_blocks, (unsigned)nP);
-    k_trace_rows<MODE, G, EXACT, GQ><<<grid, threads, 0, st>>>(
+    if (!work) {
+        dim3 grid((unsigned)n_blocks, (unsigned)nP);
+        k_trace_rows<MODE, G, EXACT, GQ><<<grid, threads, 0, st>>>(
+            sys, comp_type, comp_plane, cf, cd, valid, P, C_total, blocks, need, nodes, p0,
+            (float *)Lbuf, L_stride, fq);
+        return;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trace_rows_pq<MODE, G, EXACT, GQ>,
+                                                  threads, 0);
+    const long long n_items = (long long)n_blocks * nP;
+    const long long want = (long long)std::max(g_sm_count, 1) * std::max(per_sm, 1);
+    const unsigned grid = (unsigned)std::max(1LL, std::min(want, n_items));
+    cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
+    k_trace_rows_pq<MODE, G, EXACT, GQ><<<grid, threads, 0, st>>>(
         sys, comp_type, comp_plane, cf, cd, valid, P, C_total, blocks, need, nodes, p0,
-        (float *)Lbuf, L_stride, fq);
+        (float *)Lbuf, L_stride, fq, n_blocks, n_items, work);
 }
 
 // GQ: the launch has a global float-float queue (MIXED_FF, at most 8 nodes per row)
@@ -1274,11 +1348,12 @@ static void trace_rows_dispatch(int nn, int threads, const SysDev *sys, const in
                                 const unsigned char *valid, int P, int C_total,
                                 const TraceBlock *blocks, int n_blocks, const int *need,
                                 NodeTables nodes, int p0, int nP, void *Lbuf, long long L_stride,
-                                cudaStream_t st, FfQueue fq)
+                                cudaStream_t st, FfQueue fq, unsigned long long *work)
 {
 #define LENSED_ROWS(GG, EX, Q)                                                                  \
     trace_rows_t<MODE, GG, EX, Q>(threads, sys, comp_type, comp_plane, cf, cd, valid, P, C_total, \
-                                  blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st, fq)
+                                  blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st, fq, \
+                                  work)
     switch (nn) {
     case 1: LENSED_ROWS(1, true, GQ); break;
     case 2: LENSED_ROWS(2, true, GQ); break;
@@ -1297,9 +1372,10 @@ void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const
                   const int *comp_plane, const float *cf, const double *cd,
                   const unsigned char *valid, int P, int C_total, const TraceBlock *blocks,
                   int n_blocks, const int *need, NodeTables nodes, int p0, int nP, void *Lbuf,
-                  long long L_stride, cudaStream_t st, FfQueue q)
+                  long long L_stride, cudaStream_t st, FfQueue q, unsigned long long *work)
 {
     if (n_blocks <= 0 || nP <= 0) return;
+    if (!cfg.persistent) work = nullptr;
     if (precision == LENSED_PREC_FP64) {
         dim3 grid((unsigned)n_blocks, (unsigned)nP);
         k_trace_f64<<<grid, cfg.trace_threads, 0, st>>>(sys, comp_type, comp_plane, cf, cd,
@@ -1314,7 +1390,7 @@ void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const
             cudaMemsetAsync(q.cnt, 0, sizeof(unsigned long long), st);
             trace_rows_dispatch<LENSED_PREC_MIXED_FF, true>(
                 nn, cfg.trace_threads, sys, comp_type, comp_plane, cf, cd, valid, P, C_total,
-                blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st, q);
+                blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st, q, work);
             const unsigned grid = (unsigned)std::max(1, g_sm_count) * 8;
             k_retrace_ff<<<grid, kFfThreads, 0, st>>>(sys, comp_type, comp_plane, cf, C_total,
                                                      nodes, p0, (unsigned)L_stride, q);
@@ -1322,13 +1398,13 @@ void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const
         } else {
             trace_rows_dispatch<LENSED_PREC_MIXED_FF, false>(
                 nn, cfg.trace_threads, sys, comp_type, comp_plane, cf, cd, valid, P, C_total,
-                blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st, FfQueue{});
+                blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st, FfQueue{}, work);
         }
     } else {
         trace_rows_dispatch<LENSED_PREC_FP32, false>(nn, cfg.trace_threads, sys, comp_type,
                                                      comp_plane, cf, cd, valid, P, C_total, blocks,
                                                      n_blocks, need, nodes, p0, nP, Lbuf, L_stride,
-                                                     st, FfQueue{});
+                                                     st, FfQueue{}, work);
     }
 }
 

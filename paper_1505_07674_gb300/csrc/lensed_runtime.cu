@@ -424,28 +424,35 @@ struct Candidate {
     const char *name;
 };
 
-// The first kBaseCandidates apply to every precision; the rest only change
-// MIXED_FF (its float-float re-traces in a second kernel) and are offered
-// for that mode alone.
-const Candidate kCandidates[] = {
-    {{128, 0, 0}, "trace blocks of 128 pixels, direct PSF"},
-    {{256, 0, 0}, "trace blocks of 256 pixels, direct PSF"},
-    {{64, 0, 0}, "trace blocks of 64 pixels, direct PSF"},
-    {{128, 1, 0}, "trace blocks of 128 pixels, separable PSF where its rank allows"},
-    {{256, 1, 0}, "trace blocks of 256 pixels, separable PSF where its rank allows"},
-    {{64, 1, 0}, "trace blocks of 64 pixels, separable PSF where its rank allows"},
-    {{128, 0, 1}, "trace blocks of 128 pixels, direct PSF, float-float re-trace as a second pass"},
-    {{256, 0, 1}, "trace blocks of 256 pixels, direct PSF, float-float re-trace as a second pass"},
-    {{64, 0, 1}, "trace blocks of 64 pixels, direct PSF, float-float re-trace as a second pass"},
-    {{128, 1, 1}, "trace blocks of 128 pixels, separable PSF where its rank allows, "
-                  "float-float re-trace as a second pass"},
-    {{256, 1, 1}, "trace blocks of 256 pixels, separable PSF where its rank allows, "
-                  "float-float re-trace as a second pass"},
-    {{64, 1, 1}, "trace blocks of 64 pixels, separable PSF where its rank allows, "
-                 "float-float re-trace as a second pass"},
+// Launch configurations the autotuner tries: trace block size x PSF form
+// (0-5), the same with the trace as a persistent, work-queued launch (6-11);
+// for MIXED_FF also 0-11 with the float-float re-traces in a second kernel
+// (12-23).  The first kBaseCandidates apply to every precision.
+struct CandidateTable {
+    Candidate c[24];
+    char names[24][160];
 };
-constexpr int kAllCandidates = sizeof(kCandidates) / sizeof(kCandidates[0]);
-constexpr int kBaseCandidates = 6;
+static CandidateTable make_candidates()
+{
+    CandidateTable t{};
+    const int threads[3] = {128, 256, 64};
+    for (int split = 0; split < 2; ++split)
+        for (int pq = 0; pq < 2; ++pq)
+            for (int sep = 0; sep < 2; ++sep)
+                for (int b = 0; b < 3; ++b) {
+                    const int k = split * 12 + pq * 6 + sep * 3 + b;
+                    snprintf(t.names[k], sizeof(t.names[k]), "trace blocks of %d pixels%s, %s%s",
+                             threads[b], pq ? " (persistent, work-queued launch)" : "",
+                             sep ? "separable PSF where its rank allows" : "direct PSF",
+                             split ? ", float-float re-trace as a second pass" : "");
+                    t.c[k] = Candidate{LaunchCfg{threads[b], sep, split, pq}, t.names[k]};
+                }
+    return t;
+}
+static const CandidateTable g_candidates = make_candidates();
+static const Candidate *const kCandidates = g_candidates.c;
+constexpr int kAllCandidates = 24;
+constexpr int kBaseCandidates = 12;
 
 // Instantiated graphs kept per model (keyed by point count, buffers and
 // configuration; the least recently used is dropped beyond this).
@@ -523,6 +530,7 @@ struct lensed_model {
     DevBuf<unsigned long long> ffq_cnt;
     DevBuf<FfEntry> ffq_ent;
     DevBuf<float> ffq_val;
+    DevBuf<unsigned long long> work;  // item counter of a persistent trace launch
     // render buffers (one point)
     DevBuf<float> rcf;
     DevBuf<double> rcd;
@@ -637,6 +645,7 @@ int ensure_capacity(lensed_model *m, int P)
     size_t chunk = std::max<size_t>(1, m->scratch_budget / std::max<size_t>(per_point, 1));
     chunk = std::min<size_t>(chunk, (size_t)P);
     if ((rc = m->Lbuf.alloc(chunk * per_point))) return rc;
+    if ((rc = m->work.alloc(1))) return rc;
     if (m->precision == LENSED_PREC_MIXED_FF) {
         // the second pass's queue: room for every traced ray of a chunk, capped
         long long rays = 0;
@@ -693,7 +702,7 @@ void enqueue_batch(lensed_model *m, const double *params, int P, double *out, La
             launch_trace(m->precision, cfg, g.nn, m->sys.p, m->comp_type.p, m->comp_plane.p,
                          m->cf.p, m->cd.p, m->valid.p, P, m->C_total, m->trace_blocks.p + g.off,
                          g.count, m->need.p, m->nodes_chi(), p0, nP, m->Lbuf.p, m->total_pix, st,
-                         m->ffq());
+                         m->ffq(), m->work.p);
         if (is_mixed(m->precision))
             launch_fix64(cfg, m->sys.p, 0, m->n_sys, m->comp_type.p, m->comp_plane.p, m->cf.p,
                          m->cd.p, m->valid.p, P, m->C_total, m->need.p, m->nodes_chi(), p0, nP,

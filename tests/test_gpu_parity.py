@@ -164,12 +164,12 @@ def test_mixed_ff_second_pass_is_bit_identical(case):
     for k, s in enumerate(specs):
         pts[k, :, :s["n_params"]] = np.vstack([s["truth"], W.draw_points(s, P - 1, 70 + k)])
     n_cfg = m.set_config(0)
-    assert n_cfg == 12
-    for i in range(6):
+    assert n_cfg == 24
+    for i in range(12):
         m.set_config(i)
         a = m.loglike_batch(pts).cpu().numpy()
         launches_a, _ = m.batch_plan(P)
-        m.set_config(i + 6)
+        m.set_config(i + 12)
         b = m.loglike_batch(pts).cpu().numpy()
         launches_b, _ = m.batch_plan(P)
         assert launches_b > launches_a
@@ -197,7 +197,7 @@ def test_mixed_ff_full_queue_falls_back_bit_identically(case):
         pts[k, :, :s["n_params"]] = np.vstack([s["truth"], W.draw_points(s, P - 1, 90 + k)])
     m.set_config(1)
     ref = m.loglike_batch(pts).cpu().numpy()
-    m.set_config(7)
+    m.set_config(13)  # configuration 1 with the second pass
     for cap in (0, 1, 37, 1000, 20_000, -1):
         assert N.lib().lensed_debug_ff_queue_cap(m._h, cap) == 0
         got = m.loglike_batch(pts).cpu().numpy()
@@ -205,9 +205,36 @@ def test_mixed_ff_full_queue_falls_back_bit_identically(case):
     assert np.isfinite(ref).mean() > 0.5
 
 
+@pytest.mark.parametrize("case", ["c1", "c3_six_systems"])
+@pytest.mark.parametrize("precision", ["fp32", "mixed", "mixed_ff", "fp64"])
+def test_persistent_trace_launch_is_bit_identical(case, precision):
+    # Configurations 6-11 run 0-5 with the trace as a persistent, work-queued
+    # launch: the same work per (trace block, point) item, scheduled by a
+    # counter instead of the grid, so the same bits.
+    specs = _second_pass_cases()[case]()
+    specs = specs if isinstance(specs, list) else [specs]
+    obs = [O.mock_observation(s) for s in specs]
+    m = lensed().Model(specs if len(specs) > 1 else specs[0],
+                       obs if len(obs) > 1 else obs[0], precision=precision)
+    n_par = max(s["n_params"] for s in specs)
+    P = 33
+    pts = np.zeros((len(specs), P, n_par))
+    for k, s in enumerate(specs):
+        pts[k, :, :s["n_params"]] = np.vstack([s["truth"], W.draw_points(s, P - 1, 120 + k)])
+    offsets = (0, 12) if precision == "mixed_ff" else (0,)
+    for off in offsets:
+        for i in (0, 4):
+            m.set_config(off + i)
+            a = m.loglike_batch(pts).cpu().numpy()
+            m.set_config(off + i + 6)
+            b = m.loglike_batch(pts).cpu().numpy()
+            assert np.array_equal(a, b), (case, precision, off + i)
+    assert np.isfinite(a).mean() > 0.5
+
+
 def test_second_pass_configurations_are_offered_for_mixed_ff_only(c1):
     spec, obs, _ = c1
-    for precision, n in (("fp32", 6), ("mixed", 6), ("mixed_ff", 12), ("fp64", 6)):
+    for precision, n in (("fp32", 12), ("mixed", 12), ("mixed_ff", 24), ("fp64", 12)):
         m = lensed().Model(spec, obs, precision=precision)
         assert m.set_config(-1) == n
         with pytest.raises(Exception):

@@ -44,8 +44,8 @@ def _noalloc(m, params, out):
 
 @pytest.mark.parametrize("which,P,precision,config", [
     ("c1", 96, "fp32", None), ("c1", 96, "mixed", None), ("c1", 96, "fp64", None),
-    ("c1", 96, "mixed_ff", None), ("c1", 96, "mixed_ff", 7),
-    ("c2", 256, "mixed", None), ("c2", 256, "mixed_ff", 7),
+    ("c1", 96, "mixed_ff", None), ("c1", 96, "mixed_ff", 13),
+    ("c2", 256, "mixed", None), ("c2", 256, "mixed_ff", 13), ("c2", 256, "mixed_ff", 19),
 ])
 def test_noalloc_equals_batched_on_two_calls(which, P, precision, config):
     from paper_1505_07674_gb300 import lensed as LZ
@@ -53,7 +53,9 @@ def test_noalloc_equals_batched_on_two_calls(which, P, precision, config):
     obs = O.mock_observation(spec)
     m = LZ.Model(spec, obs, precision=precision)
     if config is not None:
-        m.set_config(config)  # 7: trace blocks of 256, re-traces in a second kernel
+        # 13: trace blocks of 256, re-traces in a second kernel; 19: the same
+        # with the persistent, work-queued trace launch
+        m.set_config(config)
     pts = W.draw_points(spec, P, 99)
     pts[3, spec["param_names"].index("q_L")] = 1.5  # one point outside the domain
     params = m.pack_params(pts)
