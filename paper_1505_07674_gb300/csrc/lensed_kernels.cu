@@ -1014,12 +1014,14 @@ __device__ __forceinline__ void trace_item(const SysDev *__restrict__ sys,
                     }
                 }
             }
-            float Ifg[G];
-            bool near[G];
+            // rmin: (R/r)^2 of the ray at the nearest Sersic-type source,
+            // capped at the re-trace threshold (a float minimum per source,
+            // the comparison once per ray)
+            float Ifg[G], rmin[G];
 #pragma unroll
             for (int k = 0; k < G; ++k) {
                 Ifg[k] = I[k];
-                near[k] = false;
+                rmin[k] = kCuspRho2;
             }
             for (int c = 0; c < ncomp; ++c) {
                 if (sm.plane[c] != LENSED_PLANE_SOURCE) continue;
@@ -1032,7 +1034,7 @@ __device__ __forceinline__ void trace_item(const SysDev *__restrict__ sys,
                     for (int k = 0; k < G; ++k) {
                         float r2;
                         I[k] += light_f32_rho(L, xk[k] - ax[k], y - ay[k], r2);
-                        near[k] = near[k] || r2 < kCuspRho2;
+                        rmin[k] = fminf(rmin[k], r2);
                     }
                 } else {
 #pragma unroll
@@ -1045,14 +1047,15 @@ __device__ __forceinline__ void trace_item(const SysDev *__restrict__ sys,
                 unsigned row = 0u;
 #pragma unroll
                 for (int k = 0; k < G; ++k) {
-                    row |= near[k] ? 1u << k : 0u;
-                    I[k] = near[k] ? Ifg[k] : I[k];
+                    const bool nk = rmin[k] < kCuspRho2;
+                    row |= nk ? 1u << k : 0u;
+                    I[k] = nk ? Ifg[k] : I[k];
                 }
                 mask |= (unsigned long long)row << (b * nn);
             } else if (MODE == LENSED_PREC_MIXED_FF) {
 #pragma unroll
                 for (int k = 0; k < G; ++k) {
-                    if (!near[k] || !(EXACT || a0 + k < nn)) continue;
+                    if (!(rmin[k] < kCuspRho2) || !(EXACT || a0 + k < nn)) continue;
                     I[k] = Ifg[k] + source_brightness_ff(sm, ncomp, jc, ic, S.h, S.h_lo,
                                                          a0 + k, b);
                 }
