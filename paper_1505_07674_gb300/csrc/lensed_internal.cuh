@@ -128,15 +128,20 @@ struct FfEntry {
 };
 constexpr unsigned kFfNone = 0xffffffffu;
 
-// MIXED_FF second-pass queue of one trace launch: *cnt = entries reserved
-// (zeroed before the launch), ent[ecap] the entries, val[ecap] their
-// source-plane brightness (written by the second pass).  cnt == nullptr:
-// every block re-traces its own rays (no second pass).
+// MIXED_FF second-pass queues of one trace launch.  cnt[0] = ray entries
+// reserved, cnt[1] = pixel records reserved (both zeroed before the launch).
+// pix[pcap]: the pixels with a ray near a source centre (FfEntry with
+// sr = system), recomputed by k_refine_ff, which puts their rays in
+// ent[ecap]; val[ecap] is their source-plane brightness (k_retrace_ff).
+// cnt == nullptr: every block re-traces its own rays (no second pass).
 struct FfQueue {
     unsigned long long *cnt;
     FfEntry *ent;
     float *val;
     long long ecap;
+    FfEntry *pix;
+    long long pcap;
+    uint2 *prun;  // [pcap]: each pixel record's rays in ent (first, count; count 0: none queued)
 };
 
 // True when the test hook lensed_debug_fail_alloc says the next device

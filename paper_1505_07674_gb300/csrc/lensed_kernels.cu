@@ -909,6 +909,165 @@ constexpr int kQCap = 2048;       // deferred float-float rays per trace block
 // parallelism.  EXACT: the rule has exactly G nodes per row (no guards).
 // GQ (MIXED_FF, EXACT): the float-float re-traces go to the launch's global
 // queue, appended warp by warp, for k_retrace_ff and k_apply_ff.
+// What a pixel's ray loop does with rays near the centre of a Sersic-type
+// source (MIXED_FF): nothing (other modes), record the smallest (R/r)^2 of
+// all rays in pmin, defer the rays' source light to the queue (their bits in
+// mask; the rest of the light summed now), or re-trace them in place.
+constexpr int kNearIgnore = 0, kNearFlag = 1, kNearDefer = 2, kNearInPlace = 3;
+
+// Where a pixel's ray loop reads its point's constants: the trace block's
+// staged copy in shared memory, or global memory (a pixel of any point).
+struct SmemConsts {
+    const TraceSmem &sm;
+    __device__ const float *cf(int c) const { return sm.cf + c * kNC; }
+    __device__ int plane(int c) const { return sm.plane[c]; }
+    __device__ int type(int c) const { return sm.type[c]; }
+    __device__ float u(int a) const { return sm.u[a]; }
+    __device__ float w(int r) const { return sm.w[r]; }
+    __device__ float ff(int ncomp, float jc, float ic, float h, float h_lo, int a, int b) const
+    {
+        return source_brightness_ff(sm, ncomp, jc, ic, h, h_lo, a, b);
+    }
+};
+struct GlobalConsts {
+    const float *cfp;
+    const int *typ, *pln;
+    const float *uu, *ww;
+    const double *ud;
+    __device__ const float *cf(int c) const { return cfp + c * kNC; }
+    __device__ int plane(int c) const { return pln[c]; }
+    __device__ int type(int c) const { return typ[c]; }
+    __device__ float u(int a) const { return uu[a]; }
+    __device__ float w(int r) const { return ww[r]; }
+    __device__ float ff(int ncomp, float jc, float ic, float h, float h_lo, int a, int b) const
+    {
+        return source_brightness_ff_at(FfConsts{cfp, typ, pln}, ncomp, jc, ic, h, h_lo,
+                                       node_pair(ud[a]), node_pair(ud[b]));
+    }
+};
+
+// a2-a5 for one pixel (centre (jc, ic) in pixels from the image centre): for
+// every row of the rule's node grid, G rays traced together component by
+// component (each component's constants read once per G rays; the G
+// independent rays give the scheduler instruction-level parallelism), each
+// ray's brightness added to acc with its weight in ray order.  EXACT: the
+// rule has exactly G nodes per row.
+template <int MODE, int G, bool EXACT, int NEAR, class KC>
+__device__ __forceinline__ float pixel_rays(const KC &kc, const SysDev &S, int ncomp, int nn,
+                                            float jc, float ic, float acc,
+                                            unsigned long long &mask, float &pmin)
+{
+    // pixel centre (j - cx) h with h as a float pair: one rounding, no
+    // coherent scale error
+    const float xc = fmaf(jc, S.h, jc * S.h_lo);
+    const float yc = fmaf(ic, S.h, ic * S.h_lo);
+    for (int b = 0; b < nn; ++b) {
+        const float y = yc + kc.u(b);
+        for (int a0 = 0; a0 < nn; a0 += G) {
+            float xk[G], ax[G], ay[G], I[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const int a = EXACT ? k : min(a0 + k, nn - 1);
+                xk[k] = xc + kc.u(a);
+                ax[k] = 0.f;
+                ay[k] = 0.f;
+                I[k] = 0.f;
+            }
+            for (int c = 0; c < ncomp; ++c) {
+                const int pl = kc.plane(c);
+                const float *cc = kc.cf(c);
+                if (pl == LENSED_PLANE_FOREGROUND) {
+                    const LightF L = load_light(cc);
+                    if (L.kind == (float)kKindFlat) {
+#pragma unroll
+                        for (int k = 0; k < G; ++k) I[k] += L.A;
+                    } else {
+                        const RowTerms R = row_terms(y, L.y0, L.cs, L.sn, L.csl, L.snl);
+#pragma unroll
+                        for (int k = 0; k < G; ++k) I[k] += light_f32_row(L, R, xk[k]);
+                    }
+                } else if (pl == LENSED_PLANE_LENS) {
+                    const int t = kc.type(c);
+                    if (t == LENSED_SIE) {
+                        const SieF K = load_sie(cc);
+                        const RowTerms R = row_terms(y, K.y0, K.cs, K.sn, K.csl, K.snl);
+#pragma unroll
+                        for (int k = 0; k < G; ++k) sie_f32_row(K, R, xk[k], ax[k], ay[k]);
+                    } else if (t == LENSED_SHEAR) {
+                        const float x0 = cc[0], y0 = cc[1], g1 = cc[2], g2 = cc[3];
+#pragma unroll
+                        for (int k = 0; k < G; ++k) {
+                            const float dx = xk[k] - x0, dy = y - y0;
+                            ax[k] += fmaf(g1, dx, g2 * dy);
+                            ay[k] += fmaf(g2, dx, -g1 * dy);
+                        }
+                    } else {  // point mass
+                        const float x0 = cc[0], y0 = cc[1], te2 = cc[2];
+#pragma unroll
+                        for (int k = 0; k < G; ++k) {
+                            const float dx = xk[k] - x0, dy = y - y0;
+                            const float r2 = fmaf(dx, dx, dy * dy);
+                            const float f = r2 > 0.f ? __fdividef(te2, r2) : 0.f;
+                            ax[k] = fmaf(f, dx, ax[k]);
+                            ay[k] = fmaf(f, dy, ay[k]);
+                        }
+                    }
+                }
+            }
+            // rmin: (R/r)^2 of the ray at the nearest Sersic-type source,
+            // capped at the re-trace threshold (a float minimum per source,
+            // the comparison once per ray)
+            float Ifg[G], rmin[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                Ifg[k] = I[k];
+                rmin[k] = kCuspRho2;
+            }
+            for (int c = 0; c < ncomp; ++c) {
+                if (kc.plane(c) != LENSED_PLANE_SOURCE) continue;
+                const LightF L = load_light(kc.cf(c));
+                if (L.kind == (float)kKindFlat) {
+#pragma unroll
+                    for (int k = 0; k < G; ++k) I[k] += L.A;
+                } else if (NEAR != kNearIgnore && L.kind == (float)kKindPower) {
+#pragma unroll
+                    for (int k = 0; k < G; ++k) {
+                        float r2;
+                        I[k] += light_f32_rho(L, xk[k] - ax[k], y - ay[k], r2);
+                        if (NEAR == kNearFlag) pmin = fminf(pmin, r2);
+                        else rmin[k] = fminf(rmin[k], r2);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < G; ++k) I[k] += light_f32(L, xk[k] - ax[k], y - ay[k]);
+                }
+            }
+            if (NEAR == kNearDefer) {
+                // the source part comes from the queue; keep the rest (the
+                // row's flags gathered first, one shift into the mask per row)
+                unsigned row = 0u;
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    const bool nk = rmin[k] < kCuspRho2;
+                    row |= nk ? 1u << k : 0u;
+                    I[k] = nk ? Ifg[k] : I[k];
+                }
+                mask |= (unsigned long long)row << (b * nn);
+            } else if (NEAR == kNearInPlace) {
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    if (!(rmin[k] < kCuspRho2) || !(EXACT || a0 + k < nn)) continue;
+                    I[k] = Ifg[k] + kc.ff(ncomp, jc, ic, S.h, S.h_lo, a0 + k, b);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+                if (EXACT || a0 + k < nn) acc = fmaf(kc.w(b * nn + a0 + k), I[k], acc);
+        }
+    }
+    return acc;
+}
+
 // The work of one trace block tb at point p (every thread of the CTA calls
 // it; it returns to the caller, which may take another item).  stage = false:
 // the shared constants already hold tb's system at point p.
@@ -953,156 +1112,37 @@ __device__ __forceinline__ void trace_item(const SysDev *__restrict__ sys,
     const int nx = S.nx;
     const int pix = active ? (need ? need[S.need_off + idx] : idx) : 0;
     const int i = pix / nx, j = pix - (pix / nx) * nx;
-    // pixel centre (j - cx) h with h as a float pair: one rounding, no
-    // coherent scale error
     const float jc = (float)j - S.cx, ic = (float)i - S.cy;
-    const float xc = fmaf(jc, S.h, jc * S.h_lo);
-    const float yc = fmaf(ic, S.h, ic * S.h_lo);
 
     float acc = (nodes.pre_f && S.pre_off >= 0 && active) ? nodes.pre_f[S.pre_off + pix] : 0.f;
     unsigned long long mask = 0ull;  // rays deferred to the queue
-    for (int b = 0; active && b < nn; ++b) {
-        const float y = yc + sm.u[b];
-        for (int a0 = 0; a0 < nn; a0 += G) {
-            float xk[G], ax[G], ay[G], I[G];
-#pragma unroll
-            for (int k = 0; k < G; ++k) {
-                const int a = EXACT ? k : min(a0 + k, nn - 1);
-                xk[k] = xc + sm.u[a];
-                ax[k] = 0.f;
-                ay[k] = 0.f;
-                I[k] = 0.f;
-            }
-            for (int c = 0; c < ncomp; ++c) {
-                const int pl = sm.plane[c];
-                const float *cc = sm.cf + c * kNC;
-                if (pl == LENSED_PLANE_FOREGROUND) {
-                    const LightF L = load_light(cc);
-                    if (L.kind == (float)kKindFlat) {
-#pragma unroll
-                        for (int k = 0; k < G; ++k) I[k] += L.A;
-                    } else {
-                        const RowTerms R = row_terms(y, L.y0, L.cs, L.sn, L.csl, L.snl);
-#pragma unroll
-                        for (int k = 0; k < G; ++k) I[k] += light_f32_row(L, R, xk[k]);
-                    }
-                } else if (pl == LENSED_PLANE_LENS) {
-                    const int t = sm.type[c];
-                    if (t == LENSED_SIE) {
-                        const SieF K = load_sie(cc);
-                        const RowTerms R = row_terms(y, K.y0, K.cs, K.sn, K.csl, K.snl);
-#pragma unroll
-                        for (int k = 0; k < G; ++k) sie_f32_row(K, R, xk[k], ax[k], ay[k]);
-                    } else if (t == LENSED_SHEAR) {
-                        const float x0 = cc[0], y0 = cc[1], g1 = cc[2], g2 = cc[3];
-#pragma unroll
-                        for (int k = 0; k < G; ++k) {
-                            const float dx = xk[k] - x0, dy = y - y0;
-                            ax[k] += fmaf(g1, dx, g2 * dy);
-                            ay[k] += fmaf(g2, dx, -g1 * dy);
-                        }
-                    } else {  // point mass
-                        const float x0 = cc[0], y0 = cc[1], te2 = cc[2];
-#pragma unroll
-                        for (int k = 0; k < G; ++k) {
-                            const float dx = xk[k] - x0, dy = y - y0;
-                            const float r2 = fmaf(dx, dx, dy * dy);
-                            const float f = r2 > 0.f ? __fdividef(te2, r2) : 0.f;
-                            ax[k] = fmaf(f, dx, ax[k]);
-                            ay[k] = fmaf(f, dy, ay[k]);
-                        }
-                    }
-                }
-            }
-            // rmin: (R/r)^2 of the ray at the nearest Sersic-type source,
-            // capped at the re-trace threshold (a float minimum per source,
-            // the comparison once per ray)
-            float Ifg[G], rmin[G];
-#pragma unroll
-            for (int k = 0; k < G; ++k) {
-                Ifg[k] = I[k];
-                rmin[k] = kCuspRho2;
-            }
-            for (int c = 0; c < ncomp; ++c) {
-                if (sm.plane[c] != LENSED_PLANE_SOURCE) continue;
-                const LightF L = load_light(sm.cf + c * kNC);
-                if (L.kind == (float)kKindFlat) {
-#pragma unroll
-                    for (int k = 0; k < G; ++k) I[k] += L.A;
-                } else if (MODE == LENSED_PREC_MIXED_FF && L.kind == (float)kKindPower) {
-#pragma unroll
-                    for (int k = 0; k < G; ++k) {
-                        float r2;
-                        I[k] += light_f32_rho(L, xk[k] - ax[k], y - ay[k], r2);
-                        rmin[k] = fminf(rmin[k], r2);
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < G; ++k) I[k] += light_f32(L, xk[k] - ax[k], y - ay[k]);
-                }
-            }
-            if (kFfDefer) {
-                // the source part comes from the queue; keep the rest (the
-                // row's flags gathered first, one shift into the mask per row)
-                unsigned row = 0u;
-#pragma unroll
-                for (int k = 0; k < G; ++k) {
-                    const bool nk = rmin[k] < kCuspRho2;
-                    row |= nk ? 1u << k : 0u;
-                    I[k] = nk ? Ifg[k] : I[k];
-                }
-                mask |= (unsigned long long)row << (b * nn);
-            } else if (MODE == LENSED_PREC_MIXED_FF) {
-#pragma unroll
-                for (int k = 0; k < G; ++k) {
-                    if (!(rmin[k] < kCuspRho2) || !(EXACT || a0 + k < nn)) continue;
-                    I[k] = Ifg[k] + source_brightness_ff(sm, ncomp, jc, ic, S.h, S.h_lo,
-                                                         a0 + k, b);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < G; ++k)
-                if (EXACT || a0 + k < nn) acc = fmaf(sm.w[b * nn + a0 + k], I[k], acc);
-        }
-    }
+    float pmin = kCuspRho2;          // smallest (R/r)^2 of the pixel's rays
+    constexpr int kNear = MODE != LENSED_PREC_MIXED_FF ? kNearIgnore
+                        : !EXACT                     ? kNearInPlace
+                        : GQ                         ? kNearFlag
+                                                     : kNearDefer;
+    if (active)
+        acc = pixel_rays<MODE, G, EXACT, kNear>(SmemConsts{sm}, S, ncomp, nn, jc, ic, acc, mask,
+                                                pmin);
     if (kWarpQ) {
-        // the warp reserves consecutive slots for its lanes' rays (each
-        // pixel's in ray order); the pixel's first-pass sum is stored now and
-        // k_apply_ff adds the re-traced rays to it
+        // a pixel with a ray inside half an effective radius of a source
+        // centre goes to the pixel queue (one atomic per warp): k_refine_ff
+        // recomputes it with those rays deferred.  Every other pixel's sum is
+        // final here (the same arithmetic as the deferring loop, which leaves
+        // a pixel without such rays unchanged).
         const unsigned full = 0xffffffffu, lane = threadIdx.x & 31u;
-        const int n_t = __popcll(mask);
-        if (__any_sync(full, n_t != 0)) {
-            int incl = n_t;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(full, incl, o);
-                if ((int)lane >= o) incl += v;
-            }
-            const int total = __shfl_sync(full, incl, 31);
+        const bool flag = active && pmin < kCuspRho2;
+        const unsigned ball = __ballot_sync(full, flag);
+        const size_t lin = (size_t)(p - p0) * L_stride + S.pix_off + pix;
+        if (ball) {
             unsigned long long base = 0ull;
-            if (lane == 31u) base = atomicAdd(fq.cnt, (unsigned long long)total);
-            base = __shfl_sync(full, base, 31);
-            const unsigned long long cap = (unsigned long long)fq.ecap;
-            unsigned long long e = base + (unsigned long long)(incl - n_t);
-            if (base + (unsigned long long)total <= cap) {
-                const unsigned lin = (unsigned)((size_t)(p - p0) * L_stride + S.pix_off + pix);
-                const unsigned sys8 = (unsigned)tb.sys << 8;
-                for (unsigned long long m = mask; m; m &= m - 1ull, ++e)
-                    fq.ent[e] = FfEntry{lin, sys8 | (unsigned)(__ffsll((long long)m) - 1)};
-            } else {
-                // the queue is full: mark this warp's slots inside it empty
-                // and re-trace the rays here, in ray order
-                for (int k = 0; k < n_t; ++k, ++e)
-                    if (e < cap) fq.ent[e] = FfEntry{kFfNone, 0u};
-                for (unsigned long long m = mask; m; m &= m - 1ull) {
-                    const int r = __ffsll((long long)m) - 1;
-                    acc = fmaf(sm.w[r],
-                               source_brightness_ff(sm, ncomp, jc, ic, S.h, S.h_lo, r % nn, r / nn),
-                               acc);
-                }
-            }
+            if (lane == 0u) base = atomicAdd(fq.cnt + 1, (unsigned long long)__popc(ball));
+            base = __shfl_sync(full, base, 0);
+            const unsigned long long e = base + (unsigned long long)__popc(ball & ((1u << lane) - 1u));
+            if (flag && e < (unsigned long long)fq.pcap)
+                fq.pix[e] = FfEntry{(unsigned)lin, (unsigned)tb.sys};
         }
-        if (active) Lbuf[(size_t)(p - p0) * L_stride + S.pix_off + pix] = acc;
+        if (active) Lbuf[lin] = acc;
         return;
     }
     if (kQueue) {
@@ -1197,12 +1237,93 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+constexpr int kFfThreads = 128;  // threads per CTA of the second-pass kernels
+
+// MIXED_FF second pass, part 1: the pixels the trace kernel flagged.  One
+// thread per pixel record (records of any system and point share a warp; the
+// constants come from global memory) recomputes the pixel's sum with the rays
+// near a source centre deferred -- the same loop and arithmetic as the
+// in-block form -- and the warp reserves consecutive slots of the ray queue
+// for its lanes' deferred rays (each pixel's in ray order), or, when they do
+// not fit, marks its slots inside the queue empty and re-traces the rays
+// itself, in ray order.
+template <int G>
+__global__ void __launch_bounds__(kFfThreads)
+    k_refine_ff(const SysDev *__restrict__ sys, const int *__restrict__ comp_type,
+                const int *__restrict__ comp_plane, const float *__restrict__ cf, int C_total,
+                NodeTables nodes, int p0, unsigned L_stride, float *__restrict__ Lbuf, FfQueue fq)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const long long n = min((long long)fq.cnt[1], fq.pcap);
+    const long long wpb = blockDim.x / 32;
+    for (long long e0 = (blockIdx.x * wpb + threadIdx.x / 32) * 32; e0 < n;
+         e0 += (long long)gridDim.x * wpb * 32) {
+        const long long e = e0 + lane;
+        const bool active = e < n;
+        unsigned lin = 0u, s = 0u;
+        int pix = 0, p = p0;
+        if (active) {
+            const FfEntry R = fq.pix[e];
+            lin = R.lin;
+            s = R.sr;
+            const unsigned q = lin / L_stride;
+            pix = (int)(lin - q * L_stride) - sys[s].pix_off;
+            p = p0 + (int)q;
+        }
+        const SysDev &S = sys[s];
+        const int j = pix - (pix / S.nx) * S.nx, i = pix / S.nx;
+        const float jc = (float)j - S.cx, ic = (float)i - S.cy;
+        const GlobalConsts K{cf + ((size_t)p * C_total + S.comp_off) * kNC,
+                             comp_type + S.comp_off, comp_plane + S.comp_off,
+                             nodes.u + S.node_off, nodes.w + S.w2_off, nodes.ud + S.node_off};
+        unsigned long long mask = 0ull;
+        float acc = 0.f, pmin = kCuspRho2;
+        if (active) {
+            acc = (nodes.pre_f && S.pre_off >= 0) ? nodes.pre_f[S.pre_off + pix] : 0.f;
+            acc = pixel_rays<LENSED_PREC_MIXED_FF, G, true, kNearDefer>(K, S, S.ncomp, G, jc, ic,
+                                                                       acc, mask, pmin);
+        }
+        const int n_t = __popcll(mask);
+        if (__any_sync(full, n_t != 0)) {
+            int incl = n_t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(full, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int total = __shfl_sync(full, incl, 31);
+            unsigned long long base = 0ull;
+            if (lane == 31) base = atomicAdd(fq.cnt, (unsigned long long)total);
+            base = __shfl_sync(full, base, 31);
+            const unsigned long long cap = (unsigned long long)fq.ecap;
+            unsigned long long q = base + (unsigned long long)(incl - n_t);
+            if (base + (unsigned long long)total <= cap) {
+                if (active) fq.prun[e] = make_uint2((unsigned)q, (unsigned)n_t);
+                const unsigned sys8 = s << 8;
+                for (unsigned long long m = mask; m; m &= m - 1ull, ++q)
+                    fq.ent[q] = FfEntry{lin, sys8 | (unsigned)(__ffsll((long long)m) - 1)};
+            } else {
+                if (active) fq.prun[e] = make_uint2(0u, 0u);
+                for (int k = 0; k < n_t; ++k, ++q)
+                    if (q < cap) fq.ent[q] = FfEntry{kFfNone, 0u};
+                for (unsigned long long m = mask; m; m &= m - 1ull) {
+                    const int r = __ffsll((long long)m) - 1;
+                    acc = fmaf(K.w(r), K.ff(S.ncomp, jc, ic, S.h, S.h_lo, r % G, r / G), acc);
+                }
+            }
+        } else if (active) {
+            fq.prun[e] = make_uint2(0u, 0u);
+        }
+        if (active) Lbuf[lin] = acc;
+    }
+}
+
 // MIXED_FF second pass over a trace launch's global queue: one thread per
 // entry (the rays of many warps and points fill whole warps here) reads its
 // point's constants from global memory and writes the ray's source-plane
 // brightness; k_apply_ff then adds each pixel's rays to its first-pass sum in
 // ray order -- the same arithmetic in the same order as the in-block path.
-constexpr int kFfThreads = 128;
 
 // SMs of the current device, read once per model (sizes the second pass's
 // persistent grid outside any stream capture)
@@ -1232,54 +1353,23 @@ __global__ void __launch_bounds__(kFfThreads)
     }
 }
 
-// Each pixel's re-traced rays are added, in ray order, to the sum the trace
-// kernel stored.  A warp takes 32 consecutive entries; the lane at the first
-// entry of a pixel walks its run through the warp's registers (shuffles, no
-// dependent global loads) and, for the run that goes on past the warp's
-// entries, through global memory.  The run begun before the warp's first
-// entry belongs to the previous warp.
+// Each refined pixel's re-traced rays are added, in ray order, to the sum
+// k_refine_ff stored: one thread per pixel record, its rays a contiguous
+// slice of the queue.
 __global__ void k_apply_ff(const SysDev *__restrict__ sys, NodeTables nodes,
                            float *__restrict__ Lbuf, FfQueue fq)
 {
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const long long n = min((long long)*fq.cnt, fq.ecap);
-    const long long wpb = blockDim.x / 32;
-    for (long long e0 = (blockIdx.x * wpb + threadIdx.x / 32) * 32; e0 < n;
-         e0 += (long long)gridDim.x * wpb * 32) {
-        const long long e = e0 + lane;
-        unsigned lin = kFfNone;
-        float w = 0.f, v = 0.f;
-        if (e < n) {
-            const FfEntry E = fq.ent[e];
-            lin = E.lin;
-            if (lin != kFfNone) {
-                w = nodes.w[sys[E.sr >> 8].w2_off + (int)(E.sr & 255u)];
-                v = fq.val[e];
-            }
-        }
-        const unsigned up = __shfl_up_sync(full, lin, 1);
-        const unsigned before = lane == 0 ? (e > 0 && e < n ? fq.ent[e - 1].lin : kFfNone) : up;
-        const bool start = lin != kFfNone && before != lin;
-        float acc = start ? Lbuf[lin] : 0.f;
-        bool open = start;
-#pragma unroll 4
-        for (int j = 0; j < 32; ++j) {
-            const unsigned lj = __shfl_sync(full, lin, j);
-            const float wj = __shfl_sync(full, w, j), vj = __shfl_sync(full, v, j);
-            if (open && j >= lane) {
-                if (lj == lin) acc = fmaf(wj, vj, acc);
-                else open = false;
-            }
-        }
-        if (start) {
-            if (open) {
-                const int w2 = sys[fq.ent[e].sr >> 8].w2_off;
-                for (long long k = e0 + 32; k < n && fq.ent[k].lin == lin; ++k)
-                    acc = fmaf(nodes.w[w2 + (int)(fq.ent[k].sr & 255u)], fq.val[k], acc);
-            }
-            Lbuf[lin] = acc;
-        }
+    const long long n = min((long long)fq.cnt[1], fq.pcap);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const uint2 run = fq.prun[e];
+        if (run.y == 0u) continue;
+        const FfEntry R = fq.pix[e];
+        const int w2 = sys[R.sr].w2_off;
+        float acc = Lbuf[R.lin];
+        for (unsigned k = 0; k < run.y; ++k)
+            acc = fmaf(nodes.w[w2 + (int)(fq.ent[run.x + k].sr & 255u)], fq.val[run.x + k], acc);
+        Lbuf[R.lin] = acc;
     }
 }
 
@@ -1387,14 +1477,29 @@ void launch_trace(int precision, LaunchCfg cfg, int nn, const SysDev *sys, const
     } else if (precision == LENSED_PREC_MIXED_FF) {
         // the global queue needs the deferral mask, i.e. at most 8 nodes per
         // row, and 32-bit pixel indices into this launch's scratch
-        const bool split = cfg.ff_split && q.cnt && q.ent && q.val && nn >= 1 && nn <= 8 &&
+        const bool split = cfg.ff_split && q.cnt && q.ent && q.val && q.pix && q.prun && nn >= 1 &&
+                           nn <= 8 &&
                            (long long)nP * L_stride < (long long)kFfNone;
         if (split) {
-            cudaMemsetAsync(q.cnt, 0, sizeof(unsigned long long), st);
+            cudaMemsetAsync(q.cnt, 0, 2 * sizeof(unsigned long long), st);
             trace_rows_dispatch<LENSED_PREC_MIXED_FF, true>(
                 nn, cfg.trace_threads, sys, comp_type, comp_plane, cf, cd, valid, P, C_total,
                 blocks, n_blocks, need, nodes, p0, nP, Lbuf, L_stride, st, q, work);
             const unsigned grid = (unsigned)std::max(1, g_sm_count) * 8;
+#define LENSED_REFINE(GG)                                                                     \
+    k_refine_ff<GG><<<grid, kFfThreads, 0, st>>>(sys, comp_type, comp_plane, cf, C_total, nodes, \
+                                                 p0, (unsigned)L_stride, (float *)Lbuf, q)
+            switch (nn) {
+            case 1: LENSED_REFINE(1); break;
+            case 2: LENSED_REFINE(2); break;
+            case 3: LENSED_REFINE(3); break;
+            case 4: LENSED_REFINE(4); break;
+            case 5: LENSED_REFINE(5); break;
+            case 6: LENSED_REFINE(6); break;
+            case 7: LENSED_REFINE(7); break;
+            default: LENSED_REFINE(8); break;
+            }
+#undef LENSED_REFINE
             k_retrace_ff<<<grid, kFfThreads, 0, st>>>(sys, comp_type, comp_plane, cf, C_total,
                                                      nodes, p0, (unsigned)L_stride, q);
             k_apply_ff<<<grid, kFfThreads, 0, st>>>(sys, nodes, (float *)Lbuf, q);

@@ -472,7 +472,7 @@ struct lensed_model {
     int C_total = 0;
     long long total_pix = 0;
     int T_total = 0;  // active (chi^2) tiles over all systems
-    size_t scratch_budget = (size_t)1 << 30;  // bytes of per-point image scratch
+    size_t scratch_budget = (size_t)2 << 30;  // bytes of per-point image scratch
 
     std::vector<SysDev> sys_h;
     std::vector<SysDev> sys_gauss_h;  // per system: its embedded Gauss rule (GK systems)
@@ -530,6 +530,8 @@ struct lensed_model {
     DevBuf<unsigned long long> ffq_cnt;
     DevBuf<FfEntry> ffq_ent;
     DevBuf<float> ffq_val;
+    DevBuf<FfEntry> ffq_pix;
+    DevBuf<uint2> ffq_prun;
     DevBuf<unsigned long long> work;  // item counter of a persistent trace launch
     // render buffers (one point)
     DevBuf<float> rcf;
@@ -554,7 +556,8 @@ struct lensed_model {
     {
         if (!ffq_cnt.p) return FfQueue{};
         const long long n = (long long)ffq_ent.n;
-        return {ffq_cnt.p, ffq_ent.p, ffq_val.p, ffq_limit >= 0 ? std::min(ffq_limit, n) : n};
+        return {ffq_cnt.p, ffq_ent.p, ffq_val.p, ffq_limit >= 0 ? std::min(ffq_limit, n) : n,
+                ffq_pix.p, (long long)ffq_pix.n, ffq_prun.p};
     }
     size_t elem() const { return precision == LENSED_PREC_FP64 ? sizeof(double) : sizeof(float); }
     // FP32 modes with fixed lights: the chi^2 path traces without them and
@@ -641,10 +644,17 @@ int ensure_capacity(lensed_model *m, int P)
     if ((rc = m->valid.alloc((size_t)P * m->n_sys))) return rc;
     if ((rc = m->cvalid.alloc((size_t)P * m->C_total))) return rc;
     if ((rc = m->partial.alloc((size_t)P * std::max(m->T_total, 1)))) return rc;
-    const size_t per_point = (size_t)m->total_pix * m->elem();
+    // per point: its pixel luminosities, and in MIXED_FF room for every
+    // needed pixel in the second pass's pixel queue
+    long long need_total = 0;
+    for (int s = 0; s < m->n_sys; ++s) need_total += m->need_count[s];
+    const size_t per_point =
+        (size_t)m->total_pix * m->elem() +
+        (m->precision == LENSED_PREC_MIXED_FF ? (size_t)need_total * (sizeof(FfEntry) + sizeof(uint2))
+                                               : 0);
     size_t chunk = std::max<size_t>(1, m->scratch_budget / std::max<size_t>(per_point, 1));
     chunk = std::min<size_t>(chunk, (size_t)P);
-    if ((rc = m->Lbuf.alloc(chunk * per_point))) return rc;
+    if ((rc = m->Lbuf.alloc(chunk * (size_t)m->total_pix * m->elem()))) return rc;
     if ((rc = m->work.alloc(1))) return rc;
     if (m->precision == LENSED_PREC_MIXED_FF) {
         // the second pass's queue: room for every traced ray of a chunk, capped
@@ -652,9 +662,12 @@ int ensure_capacity(lensed_model *m, int P)
         for (int s = 0; s < m->n_sys; ++s)
             rays += (long long)m->need_count[s] * m->n_nodes[s] * m->n_nodes[s];
         const size_t cap = (size_t)std::max(1LL, std::min(rays * (long long)chunk, kFfEntryCap));
-        if ((rc = m->ffq_cnt.alloc(1))) return rc;
+        if ((rc = m->ffq_cnt.alloc(2))) return rc;
         if ((rc = m->ffq_ent.alloc(cap))) return rc;
         if ((rc = m->ffq_val.alloc(cap))) return rc;
+        const size_t pcap = (size_t)std::max(1LL, need_total * (long long)chunk);
+        if ((rc = m->ffq_pix.alloc(pcap))) return rc;
+        if ((rc = m->ffq_prun.alloc(pcap))) return rc;
     }
     m->chunk_P = (int)chunk;
     m->cap_P = P;
@@ -1705,11 +1718,11 @@ extern "C" int lensed_batch_plan(lensed_model *m, int P, int *launches, int *chu
     int rc = ensure_capacity(m, P);
     if (rc) return rc;
     const int chunks = (P + m->chunk_P - 1) / m->chunk_P;
-    // a MIXED_FF second pass: two more kernels (re-trace, apply) per trace
-    // group of at most 8 nodes per row
+    // a MIXED_FF second pass: three more kernels (pixel refinement, re-trace,
+    // apply) per trace group of at most 8 nodes per row
     int second = 0;
     if (m->precision == LENSED_PREC_MIXED_FF && m->cfg().ff_split && m->ffq_cnt.p)
-        for (const TraceGroup &g : m->trace_groups) second += 2 * (g.nn >= 1 && g.nn <= 8);
+        for (const TraceGroup &g : m->trace_groups) second += 3 * (g.nn >= 1 && g.nn <= 8);
     *launches = 3 + chunks * ((int)m->trace_groups.size() + (int)m->psf_groups.size() +
                               (is_mixed(m->precision) ? 1 : 0) + second);
     *chunk_points = m->chunk_P;
