@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--config", type=int, default=None,
                     help="pin launch configuration N (lensed_set_config numbering) instead "
                          "of autotuning (profiling of one configuration)")
+    ap.add_argument("--chunk-points", type=int, default=None,
+                    help="with --config: at most N points per scratch chunk "
+                         "(lensed_set_chunk_points; 0 = whole chunks)")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
                     help="c2 (default, the benchmark), c1 or c3 (other configurations), "
                          "c4 (posterior run), c5 (surrogate pre-screen vs plain), j0808 "
@@ -688,6 +691,8 @@ def main():
             m.autotune(params, stream=stream)
         else:
             m.set_config(args.config)
+            if args.chunk_points is not None:
+                m.set_chunk_points(args.chunk_points)
         tuned = m.tuned_config()
         launches, chunk = m.batch_plan(npts)
         for _ in range(max(3, args.warmup)):
@@ -704,11 +709,14 @@ def main():
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         t_wall = time.perf_counter()
+        # an NVTX range marks the timed launches (ncu --nvtx-include "timed_steps/")
+        torch.cuda.nvtx.range_push("timed_steps")
         for k in range(args.steps):
             flush.zero_()
             starts[k].record(stream)
             m.loglike_batch(params, out=out, stream=stream)
             ends[k].record(stream)
+        torch.cuda.nvtx.range_pop()
         stream.synchronize()
         t_wall = time.perf_counter() - t_wall
         clocks = sampler.stop()
@@ -798,7 +806,7 @@ def main():
                    "precision_mode": args.precision,
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"independent points per rank x{world}",
-                   "tuned": tuned[1], "chunk_points": chunk},
+                   "tuned": tuned[1], "tuned_index": tuned[0], "chunk_points": chunk},
         "grays_per_s": grays,
         "traced_rays_per_step": npts * rays_traced,
         "plain": None if plain_ms is None else {

@@ -311,8 +311,8 @@ int lensed_loglike_batch_noalloc(lensed_model *m, const double *params, int P,
  * (differences at the float rounding level).  Synchronous. */
 int lensed_autotune(lensed_model *m, const double *params, int P, void *stream);
 
-/* Index of the configuration in use (-1: default) and its description, for
- * reports. */
+/* Index of the configuration in use (-1: default) and its description (with
+ * the chunk limit, if one is set), for reports. */
 int lensed_tuned_config(const lensed_model *m, char *buf, int buflen);
 
 /* Measured FP32 throughput of this GPU for the roofline (the paper has no
@@ -342,6 +342,18 @@ int lensed_eval_sie_trig(const float *n, const float *d, long long count, float 
  * 12 + k runs configuration k with the float-float re-traces in a second
  * kernel. */
 int lensed_set_config(lensed_model *m, int index);
+
+/* Points per scratch chunk of the batched schedule (a8; the paper has no
+ * counterpart).  lensed_loglike_batch runs the trace and PSF passes over
+ * chunks of points whose pixel luminosities fit the model's scratch; with
+ * points > 0 a chunk holds at most that many points, so that a chunk's
+ * luminosities can stay in L2 between the trace pass that writes them and
+ * the PSF pass that reads them; points = 0 lifts the limit.  Chunks are
+ * independent ranges of points, so the limit never changes a result, only
+ * the number of launches and the DRAM traffic.  lensed_autotune sets it too
+ * (no limit, or half or a quarter of L2 over one point's luminosities);
+ * lensed_set_config leaves it as it is.  LENSED_E_ARG for points < 0. */
+int lensed_set_chunk_points(lensed_model *m, int points);
 
 /* Launch plan of one lensed_loglike_batch call with P points: number of
  * kernels it launches (*launches) and the number of points per scratch

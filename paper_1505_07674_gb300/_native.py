@@ -26,7 +26,7 @@ MAX_KRONROD_ORDER = 7
 
 # the C entry points, by name (the ABI symbol list the tests check)
 EXPORTS = ("lensed_create_model", "lensed_destroy", "lensed_model_info_get", "lensed_render",
-           "lensed_render_error", "lensed_rule_nodes", "lensed_set_config",
+           "lensed_render_error", "lensed_rule_nodes", "lensed_set_config", "lensed_set_chunk_points",
            "lensed_measure_alu_peaks", "lensed_eval_sie_trig",
            "lensed_loglike_batch", "lensed_loglike_plain", "lensed_loglike_batch_host",
            "lensed_autotune", "lensed_tuned_config", "lensed_last_error", "lensed_batch_plan",
@@ -87,6 +87,7 @@ def lib():
         L.lensed_render_error.argtypes = [vp, C.c_int, vp, vp, vp]
         L.lensed_rule_nodes.argtypes = [C.c_int, C.c_int, vp, vp, vp]
         L.lensed_set_config.argtypes = [vp, C.c_int]
+        L.lensed_set_chunk_points.argtypes = [vp, C.c_int]
         L.lensed_measure_alu_peaks.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
         L.lensed_eval_sie_trig.argtypes = [vp, vp, C.c_longlong, vp, vp]
         for name in ("lensed_loglike_batch", "lensed_loglike_plain", "lensed_loglike_batch_host",

@@ -415,6 +415,7 @@ struct GraphEntry {
     const void *params;
     void *out;
     int cfg;
+    int chunk;  // points per scratch chunk the graph was captured with
     cudaGraphExec_t exec;
     unsigned long long age;
 };
@@ -525,7 +526,8 @@ struct lensed_model {
     DevBuf<unsigned char> valid, cvalid;
     DevBuf<double> partial;
     DevBuf<unsigned char> Lbuf;
-    int chunk_P = 0;
+    int chunk_P = 0;      // points per chunk that the scratch budget holds
+    int chunk_limit = 0;  // if > 0, at most this many points per chunk
     // MIXED_FF second-pass queue (one trace launch at a time)
     DevBuf<unsigned long long> ffq_cnt;
     DevBuf<FfEntry> ffq_ent;
@@ -548,6 +550,8 @@ struct lensed_model {
     unsigned long long graph_clock = 0;
 
     LaunchCfg cfg() const { return kCandidates[cfg_index < 0 ? 0 : cfg_index].cfg; }
+    // points per chunk of the batched schedule (after ensure_capacity)
+    int chunk() const { return chunk_limit > 0 ? std::min(chunk_P, chunk_limit) : chunk_P; }
     int n_candidates() const
     {
         return precision == LENSED_PREC_MIXED_FF ? kAllCandidates : kBaseCandidates;
@@ -706,8 +710,9 @@ void enqueue_batch(lensed_model *m, const double *params, int P, double *out, La
                     m->comp_free.p, m->comp_value.p, params, false, P, 0, P, m->n_par_max,
                     m->C_total, m->bn_table.p, m->cf.p, m->cd.p, m->cvalid.p, m->valid.p, st);
     if (tm) tm->end();
-    for (int p0 = 0; p0 < P; p0 += m->chunk_P) {
-        const int nP = std::min(m->chunk_P, P - p0);
+    const int chunk = m->chunk();
+    for (int p0 = 0; p0 < P; p0 += chunk) {
+        const int nP = std::min(chunk, P - p0);
         if (tm) tm->begin(1);
         // (a second pass, where launch_trace runs one, completes before the
         // MIXED fix-up overwrites its pixels: both are on stream st)
@@ -1568,7 +1573,9 @@ static int run_batch(lensed_model *m, const double *params, int P, double *out, 
     // graph cache keyed by (P, params, out, configuration)
     GraphEntry *hit = nullptr;
     for (auto &g : m->graphs)
-        if (g.P == P && g.params == params && g.out == out && g.cfg == m->cfg_index) hit = &g;
+        if (g.P == P && g.params == params && g.out == out && g.cfg == m->cfg_index &&
+            g.chunk == m->chunk())
+            hit = &g;
     if (!hit) {
         if (m->graphs.size() >= kGraphCache) {
             auto old = std::min_element(m->graphs.begin(), m->graphs.end(),
@@ -1591,7 +1598,7 @@ static int run_batch(lensed_model *m, const double *params, int P, double *out, 
         cudaGraphDestroy(graph);
         if (e3 != cudaSuccess)
             return fail(LENSED_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e3));
-        m->graphs.push_back({P, params, out, m->cfg_index, exec, 0});
+        m->graphs.push_back({P, params, out, m->cfg_index, m->chunk(), exec, 0});
         hit = &m->graphs.back();
     }
     hit->age = ++m->graph_clock;
@@ -1675,36 +1682,70 @@ extern "C" int lensed_autotune(lensed_model *m, const double *params, int P, voi
     cudaStream_t st = (cudaStream_t)stream;
     DevBuf<double> tmp;
     if ((rc = tmp.alloc((size_t)m->n_sys * P))) return rc;
+    if ((rc = ensure_capacity(m, P))) return rc;
     cudaEvent_t e0, e1;
     CUDA_OK(cudaEventCreate(&e0));
     CUDA_OK(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_i = 0;
-    const int saved = m->cfg_index;
-    for (int i = 0; i < m->n_candidates(); ++i) {
-        m->cfg_index = i;
-        float t_min = 1e30f;
+    // best of 3 timed runs (each after an untimed one) of the current setting
+    auto time_batch = [&](float *t_min) -> int {
+        *t_min = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
-            if ((rc = run_batch(m, params, P, tmp.p, st, false))) {
-                m->cfg_index = saved;
-                return rc;
-            }
+            int r = run_batch(m, params, P, tmp.p, st, false);
+            if (r) return r;
             cudaEventRecord(e0, st);
             run_batch(m, params, P, tmp.p, st, false);
             cudaEventRecord(e1, st);
-            CUDA_OK(cudaEventSynchronize(e1));
+            if (cudaEventSynchronize(e1) != cudaSuccess)
+                return fail(LENSED_E_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            t_min = std::min(t_min, ms);
+            *t_min = std::min(*t_min, ms);
         }
-        if (t_min < best) {
-            best = t_min;
+        return LENSED_OK;
+    };
+    const int saved = m->cfg_index, saved_limit = m->chunk_limit;
+    // First stage: every launch configuration, each over whole scratch chunks.
+    m->chunk_limit = 0;
+    float best = 1e30f, t = 0.f;
+    int best_i = 0;
+    for (int i = 0; i < m->n_candidates() && !rc; ++i) {
+        m->cfg_index = i;
+        if ((rc = time_batch(&t))) break;
+        if (t < best) {
+            best = t;
             best_i = i;
+        }
+    }
+    // Second stage, with the chosen configuration: whole scratch chunks, or
+    // chunks whose pixel luminosities fit in half or a quarter of L2, so the
+    // PSF pass reads what the trace pass left in L2 (smaller chunks also
+    // mean more launches and more launch tails; timing decides).
+    int best_limit = 0;
+    if (!rc) {
+        m->cfg_index = best_i;
+        int l2_bytes = 0;
+        cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, m->device);
+        const size_t per_point = std::max<size_t>(1, (size_t)m->total_pix * m->elem());
+        const int limits[2] = {(int)std::max<size_t>(1, (size_t)std::max(l2_bytes, 0) / 2 / per_point),
+                               (int)std::max<size_t>(1, (size_t)std::max(l2_bytes, 0) / 4 / per_point)};
+        for (int li = 0; li < 2 && !rc && l2_bytes > 0; ++li) {
+            if (limits[li] >= std::min(m->chunk_P, P)) continue;  // one chunk already
+            m->chunk_limit = limits[li];
+            if ((rc = time_batch(&t))) break;
+            if (t < best) {
+                best = t;
+                best_limit = limits[li];
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    m->cfg_index = best_i;
+    if (rc) {
+        m->cfg_index = saved;
+        m->chunk_limit = saved_limit;
+        return rc;
+    }
+    m->chunk_limit = best_limit;
     LaunchCfg cfg = m->cfg();
     if ((rc = build_trace_tables(m, cfg.trace_threads))) return rc;
     CUDA_OK(cudaStreamSynchronize(st));
@@ -1717,7 +1758,7 @@ extern "C" int lensed_batch_plan(lensed_model *m, int P, int *launches, int *chu
     if (P < 1 || !launches || !chunk_points) return fail(LENSED_E_ARG, "bad arguments");
     int rc = ensure_capacity(m, P);
     if (rc) return rc;
-    const int chunks = (P + m->chunk_P - 1) / m->chunk_P;
+    const int chunks = (P + m->chunk() - 1) / m->chunk();
     // a MIXED_FF second pass: three more kernels (pixel refinement, re-trace,
     // apply) per trace group of at most 8 nodes per row
     int second = 0;
@@ -1725,7 +1766,7 @@ extern "C" int lensed_batch_plan(lensed_model *m, int P, int *launches, int *chu
         for (const TraceGroup &g : m->trace_groups) second += 3 * (g.nn >= 1 && g.nn <= 8);
     *launches = 3 + chunks * ((int)m->trace_groups.size() + (int)m->psf_groups.size() +
                               (is_mixed(m->precision) ? 1 : 0) + second);
-    *chunk_points = m->chunk_P;
+    *chunk_points = m->chunk();
     return LENSED_OK;
 }
 
@@ -1769,12 +1810,23 @@ extern "C" int lensed_set_config(lensed_model *m, int index)
     return m->n_candidates();
 }
 
+extern "C" int lensed_set_chunk_points(lensed_model *m, int points)
+{
+    if (check_model(m)) return LENSED_E_ARG;
+    if (points < 0) return fail(LENSED_E_ARG, "points per chunk = %d must be >= 0", points);
+    m->chunk_limit = points;
+    return LENSED_OK;
+}
+
 extern "C" int lensed_tuned_config(const lensed_model *m, char *buf, int buflen)
 {
     if (check_model(m)) return -1;
     if (buf && buflen > 0) {
         const char *name = kCandidates[m->cfg_index < 0 ? 0 : m->cfg_index].name;
-        snprintf(buf, (size_t)buflen, "%s%s", name, m->cfg_index < 0 ? " (default)" : "");
+        char lim[64] = "";
+        if (m->chunk_limit > 0)
+            snprintf(lim, sizeof(lim), ", at most %d points per scratch chunk", m->chunk_limit);
+        snprintf(buf, (size_t)buflen, "%s%s%s", name, lim, m->cfg_index < 0 ? " (default)" : "");
     }
     return m->cfg_index;
 }

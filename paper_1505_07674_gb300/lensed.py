@@ -230,9 +230,14 @@ class Model:
         N.check(min(n, 0))
         return n
 
+    def set_chunk_points(self, points):
+        """At most `points` points per scratch chunk of the batched schedule
+        (0: as many as the scratch holds); never changes a result."""
+        N.check(N.lib().lensed_set_chunk_points(self._h, int(points)))
+
     def tuned_config(self):
-        buf = C.create_string_buffer(128)
-        idx = N.lib().lensed_tuned_config(self._h, buf, 128)
+        buf = C.create_string_buffer(256)
+        idx = N.lib().lensed_tuned_config(self._h, buf, 256)
         return idx, buf.value.decode()
 
 

@@ -232,6 +232,62 @@ def test_persistent_trace_launch_is_bit_identical(case, precision):
     assert np.isfinite(a).mean() > 0.5
 
 
+@pytest.mark.parametrize("case", ["c2_96x80", "c3_six_systems"])
+@pytest.mark.parametrize("precision", ["fp32", "mixed", "mixed_ff", "fp64"])
+def test_chunk_limit_is_bit_identical(case, precision):
+    # A limit on the points per scratch chunk (the L2-resident schedule the
+    # autotuner may pick) splits the batch into independent point ranges:
+    # more launches, the same bits, also with the persistent trace launch and
+    # the second pass, and a limit that leaves a ragged last chunk.
+    specs = _second_pass_cases()[case]()
+    specs = specs if isinstance(specs, list) else [specs]
+    obs = [O.mock_observation(s) for s in specs]
+    m = lensed().Model(specs if len(specs) > 1 else specs[0],
+                       obs if len(obs) > 1 else obs[0], precision=precision)
+    n_par = max(s["n_params"] for s in specs)
+    P = 37
+    pts = np.zeros((len(specs), P, n_par))
+    for k, s in enumerate(specs):
+        pts[k, :, :s["n_params"]] = np.vstack([s["truth"], W.draw_points(s, P - 1, 140 + k)])
+    configs = (1, 10, 19) if precision == "mixed_ff" else (1, 10)
+    for cfg in configs:
+        m.set_config(cfg)
+        m.set_chunk_points(0)
+        ref = m.loglike_batch(pts).cpu().numpy()
+        launches_ref, chunk_ref = m.batch_plan(P)
+        assert chunk_ref == P
+        for limit in (1, 8, 36, 37, 500):
+            m.set_chunk_points(limit)
+            launches, chunk = m.batch_plan(P)
+            assert chunk == min(limit, P)
+            assert (launches > launches_ref) == (limit < P)
+            got = m.loglike_batch(pts).cpu().numpy()
+            assert np.array_equal(got, ref), (case, precision, cfg, limit)
+        assert "at most 500 points" in m.tuned_config()[1]
+    with pytest.raises(Exception):
+        m.set_chunk_points(-1)
+    assert np.isfinite(ref).mean() > 0.5
+
+
+def test_autotune_keeps_a_chunk_limit_that_changes_nothing():
+    # The autotuner's second stage times whole chunks against L2-sized ones
+    # (on the 200x200 workload a quarter of L2 holds a few hundred points'
+    # luminosities, fewer than this batch); whichever it keeps, the results
+    # are the untuned ones bit for bit.
+    spec = W.c2_hst()
+    obs = O.mock_observation(spec)
+    m = lensed().Model(spec, obs, precision="mixed_ff")
+    pts = np.vstack([spec["truth"], W.draw_points(spec, 511, 150)])
+    m.set_config(1)
+    ref = m.loglike_batch(pts).cpu().numpy()
+    idx, name = m.autotune(pts)
+    m.set_config(1)
+    got = m.loglike_batch(pts).cpu().numpy()
+    assert np.array_equal(got, ref), name
+    _, chunk = m.batch_plan(len(pts))
+    assert 1 <= chunk <= len(pts)
+
+
 def test_second_pass_configurations_are_offered_for_mixed_ff_only(c1):
     spec, obs, _ = c1
     for precision, n in (("fp32", 12), ("mixed", 12), ("mixed_ff", 24), ("fp64", 12)):
