@@ -93,6 +93,8 @@ def parse():
                     help="rules: noiseless mocks (noise model kept for the variance), so that "
                          "the errors measure the integration rule alone")
     ap.add_argument("--live", type=int, default=2000, help="live points (c4, c5)")
+    ap.add_argument("--c5-runs", default="plain,online,audit,global",
+                    help="c5: which runs (plain is always run; online, audit, global)")
     ap.add_argument("--oracle-points", type=int, default=384,
                     help="posterior points the CPU oracle re-evaluates (c4)")
     return ap.parse_args()
@@ -406,6 +408,7 @@ def run_mlp(args):
     sampler.start()
     time.sleep(0.3)
     fwd, trn = [], []
+    torch.cuda.nvtx.range_push("timed_steps")  # ncu --nvtx-include "timed_steps/"
     for _ in range(args.steps):
         flush.zero_()
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -416,6 +419,7 @@ def run_mlp(args):
         e2.record()
         fwd.append((e0, e1))
         trn.append((e1, e2))
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clocks = sampler.stop()
     f_ms = sum(a.elapsed_time(b) for a, b in fwd) / args.steps
@@ -570,7 +574,10 @@ def run_surrogate(args):
     like = GpuLikelihood(m, spec)
     res = nested_sampling(like, like.ndim, args.live, seed=12, dlogz=0.1, max_evals=8_000_000)
     runs["plain"] = summary(res, like)
+    want = set(args.c5_runs.split(","))
     for audit in (False, True):
+        if ("audit" if audit else "online") not in want:
+            continue
         rec = GpuLikelihood(m, spec, record=True)
         online = OnlineSurrogate(rec, rec.ndim, forward_batch=65536)
         ell = None if audit else EllipsoidSampler(rec, rec.ndim, screen=online, seed=12)
@@ -588,42 +595,54 @@ def run_surrogate(args):
                          ellipsoid_exact=ell.n_exact, candidates=ell.n_candidates,
                          ellipsoid_draw_s=ell.draw_s, audited=ell.n_audit, missed=ell.missed)
             runs["online_surrogate"] = summary(res, rec, extra)
-    # global surrogate from an earlier run's evaluations (seed 11)
-    gen = GpuLikelihood(m, spec, record=True)
-    t0 = time.perf_counter()
-    nested_sampling(gen, gen.ndim, args.live, seed=11, dlogz=0.1, max_evals=8_000_000)
-    gen_s = time.perf_counter() - t0
-    U = np.concatenate(gen.U)[-2_000_000:]
-    L = np.concatenate(gen.L)[-2_000_000:]
-    screen = SurrogateScreen(gen.ndim, 256, 8192).fit(U, L, epochs=20, margin_sigmas=4.0)
-    like = GpuLikelihood(m, spec)
-    res = nested_sampling(like, like.ndim, args.live, seed=12, dlogz=0.1, prescreen=screen,
-                          on_round=screen.on_round, max_evals=8_000_000)
-    runs["global_surrogate"] = summary(res, like, {
-        "pairs": int(screen.n_train), "generation_s": gen_s, "train_s": screen.train_s,
-        "holdout_rms_y": screen.val_rms, "margin_y": screen.margin})
-    # network inference throughput on 65,536 proposals
-    X = torch.rand((65536, gen.ndim), device="cuda")
-    y = torch.empty(65536, device="cuda")
-    for _ in range(3):
-        screen.net.forward(X, out=y)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(20):
-        screen.net.forward(X, out=y)
-    e1.record()
-    torch.cuda.synchronize()
-    fwd_ms = e0.elapsed_time(e1) / 20
-    flops = 2 * 65536 * (32 * 256 + 2 * 256 * 256 + 256)
-    a = runs["plain"]
-    for k in ("online_surrogate", "global_surrogate"):
-        b = runs[k]
-        b["speedup_wall_vs_plain"] = a["wall_s"] / b["wall_s"]
-        b["exact_evals_vs_plain"] = b["n_evals"] / a["n_evals"]
-        b["logz_diff_in_sigma"] = (b["logz"] - a["logz"]) / math.hypot(a["logz_err"], b["logz_err"])
+    def compare():
+        a = runs["plain"]
+        for k in ("online_surrogate", "global_surrogate"):
+            if k not in runs:
+                continue
+            b = runs[k]
+            b["speedup_wall_vs_plain"] = a["wall_s"] / b["wall_s"]
+            b["exact_evals_vs_plain"] = b["n_evals"] / a["n_evals"]
+            b["logz_diff_in_sigma"] = ((b["logz"] - a["logz"])
+                                       / math.hypot(a["logz_err"], b["logz_err"]))
+
+    compare()
+    # the runs so far, in case the global-surrogate runs below do not finish
+    print(json.dumps({"partial": True, "runs": runs}), flush=True)
+    fwd = None
+    if "global" in want:
+        # global surrogate from an earlier run's evaluations (seed 11)
+        gen = GpuLikelihood(m, spec, record=True)
+        t0 = time.perf_counter()
+        nested_sampling(gen, gen.ndim, args.live, seed=11, dlogz=0.1, max_evals=8_000_000)
+        gen_s = time.perf_counter() - t0
+        U = np.concatenate(gen.U)[-2_000_000:]
+        L = np.concatenate(gen.L)[-2_000_000:]
+        screen = SurrogateScreen(gen.ndim, 256, 8192).fit(U, L, epochs=20, margin_sigmas=4.0)
+        like = GpuLikelihood(m, spec)
+        res = nested_sampling(like, like.ndim, args.live, seed=12, dlogz=0.1, prescreen=screen,
+                              on_round=screen.on_round, max_evals=8_000_000)
+        runs["global_surrogate"] = summary(res, like, {
+            "pairs": int(screen.n_train), "generation_s": gen_s, "train_s": screen.train_s,
+            "holdout_rms_y": screen.val_rms, "margin_y": screen.margin})
+        # network inference throughput on 65,536 proposals
+        X = torch.rand((65536, gen.ndim), device="cuda")
+        y = torch.empty(65536, device="cuda")
+        for _ in range(3):
+            screen.net.forward(X, out=y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            screen.net.forward(X, out=y)
+        e1.record()
+        torch.cuda.synchronize()
+        fwd_ms = e0.elapsed_time(e1) / 20
+        flops = 2 * 65536 * (32 * 256 + 2 * 256 * 256 + 256)
+        fwd = {"ms": fwd_ms, "tflops": flops / (fwd_ms * 1e-3) / 1e12}
+        compare()
     line = {"metric": "wall time to the evidence estimate, surrogate vs plain batched run",
             "workload": WORKLOADS["c5"][0], "n_live": args.live, "runs": runs,
-            "mlp_forward_65536": {"ms": fwd_ms, "tflops": flops / (fwd_ms * 1e-3) / 1e12},
+            "mlp_forward_65536": fwd,
             "data": "synthetic"}
     print(json.dumps(line), flush=True)
     return 0
