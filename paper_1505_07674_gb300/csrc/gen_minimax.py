@@ -74,17 +74,21 @@ def render(coefs):
     out = [
         "// Generated by gen_minimax.py (Lawson minimax fits; do not edit).",
         "// atan(t) = t + t^3 Qa(t^2) on [0, 1]; atanh(z) = z + z^3 Qh(z^2) on [0, 1/2].",
-        "// Each function evaluates Q(u) by Horner's rule in fused multiply-adds.",
+        "// Each function evaluates Q(u) by Horner's rule in fused multiply-adds, for",
+        "// one ray (V = float) or a pair of rays (V = float2, packed instructions).",
         "#pragma once",
+        "",
+        '#include "lensed_vec2.cuh"',
         "",
         "namespace lensed {",
     ]
     for name, c in coefs.items():
-        out.append(f"__device__ __forceinline__ float {FUNCS[name]}(float u)")
+        out.append("template <class V>")
+        out.append(f"__device__ __forceinline__ V {FUNCS[name]}(V u)")
         out.append("{")
-        out.append(f"    float q = {float(c[-1]):.9e}f;")
+        out.append(f"    V q = vsplat<V>({float(c[-1]):.9e}f);")
         for v in c[-2::-1]:
-            out.append(f"    q = fmaf(q, u, {float(v):.9e}f);")
+            out.append(f"    q = vfma(q, u, vsplat<V>({float(v):.9e}f));")
         out.append("    return q;")
         out.append("}")
     out += ["}  // namespace lensed", ""]
@@ -95,14 +99,18 @@ def parse(path=HEADER):
     """Coefficients as written in the header (constant term first)."""
     coefs, name, cur = {}, None, []
     inv = {v: k for k, v in FUNCS.items()}
+
+    def number(text):
+        return float(text.strip().rstrip(";").rstrip(")").rstrip(")").rstrip("f"))
+
     for line in open(path):
         line = line.strip()
         if line.startswith("__device__"):
-            name, cur = inv[line.split("float ")[1].split("(")[0]], []
-        elif line.startswith("float q = "):
-            cur.append(float(line.split("=")[1].strip().rstrip(";").rstrip("f")))
-        elif line.startswith("q = fmaf("):
-            cur.append(float(line.split(",")[2].strip().rstrip(");").rstrip("f")))
+            name, cur = inv[line.split("(")[0].split()[-1]], []
+        elif line.startswith("V q = vsplat<V>("):
+            cur.append(number(line.split("vsplat<V>(")[1]))
+        elif line.startswith("q = vfma("):
+            cur.append(number(line.split("vsplat<V>(")[1]))
         elif line.startswith("return q;") and name:
             coefs[name] = np.array(cur[::-1], np.float32)
     return coefs

@@ -31,6 +31,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <utility>
 
 #include "lensed_internal.cuh"
@@ -437,47 +438,85 @@ __device__ __forceinline__ RowTerms row_terms(float y, float y0, float cs, float
     return {fmaf(dy, sn, dy * snl), fmaf(dy, cs, dy * csl)};
 }
 
-// sie_f32 for a ray of the row whose terms are R (same arithmetic, the row's
-// products computed once)
-__device__ __forceinline__ void sie_f32_row(const SieF &k, const RowTerms &R, float x, float &ax,
-                                            float &ay)
+// sie_f32 for the rays of a node row whose terms are R (the row's products
+// computed once), one ray (V = float) or a pair (V = float2): the same
+// formulas, every operation rounded once (lensed_vec2.cuh), the products with
+// -sin taken as products with the negated constant (exact).
+template <class V>
+__device__ __forceinline__ void sie_row_v(const SieF &k, const RowTerms &R, V x, V &ax, V &ay)
 {
-    const float dx = x - k.x0;
-    const float u = fmaf(dx, k.cs, fmaf(dx, k.csl, R.du));
-    const float v = fmaf(-dx, k.sn, fmaf(-dx, k.snl, R.dv));
-    const float w = fmaf(u, u, k.s2);
-    const float psi2 = fmaf(k.q2, w, fmaf(k.q2l, w, v * v));
-    const float psi = psi2 > 0.f ? psi2 * rsqrtf(psi2) : 0.f;
-    const float du = psi + k.s, dv = psi + k.q2s;
-    float A1, A2;
+    const V dx = vsub(x, vsplat<V>(k.x0));
+    const V u = vfma(dx, vsplat<V>(k.cs), vfma(dx, vsplat<V>(k.csl), vsplat<V>(R.du)));
+    const V v = vfma(dx, vsplat<V>(-k.sn), vfma(dx, vsplat<V>(-k.snl), vsplat<V>(R.dv)));
+    const V w = vfma(u, u, vsplat<V>(k.s2));
+    const V psi2 = vfma(vsplat<V>(k.q2), w, vfma(vsplat<V>(k.q2l), w, vmul(v, v)));
+    const V psi = vmul(psi2, vmap(psi2, [](float a) { return a > 0.f ? rsqrtf(a) : 0.f; }));
+    const V du = vadd(psi, vsplat<V>(k.s)), dv = vadd(psi, vsplat<V>(k.q2s));
+    V A1, A2;
     if (k.series != 0.f) {
-        const float zu = du > 0.f ? __fdividef(u, du) : 0.f;
-        const float zv = du > 0.f ? __fdividef(v, dv) : 0.f;
-        const float zu2 = zu * zu, zv2 = zv * zv;
-        A1 = zu * (1.f - k.e2 * zu2 * (1.f / 3.f) + k.e2 * k.e2 * zu2 * zu2 * 0.2f);
-        A2 = zv * (1.f + k.e2 * zv2 * (1.f / 3.f) + k.e2 * k.e2 * zv2 * zv2 * 0.2f);
+        // q -> 1: atan(e z)/e and atanh(e z)/e by their series in e z
+        const float e2 = k.e2, e4 = __fmul_rn(e2, e2);
+        A1 = vmap(u, du, [=](float uu, float d) {
+            const float z = d > 0.f ? __fdividef(uu, d) : 0.f, z2 = __fmul_rn(z, z);
+            return __fmul_rn(z, __fadd_rn(__fsub_rn(1.f, __fmul_rn(__fmul_rn(e2, z2), 1.f / 3.f)),
+                                          __fmul_rn(__fmul_rn(__fmul_rn(e4, z2), z2), 0.2f)));
+        });
+        A2 = vmap(v, dv, du, du, [=](float vv, float d, float dd, float) {
+            const float z = dd > 0.f ? __fdividef(vv, d) : 0.f, z2 = __fmul_rn(z, z);
+            return __fmul_rn(z, __fadd_rn(__fadd_rn(1.f, __fmul_rn(__fmul_rn(e2, z2), 1.f / 3.f)),
+                                          __fmul_rn(__fmul_rn(__fmul_rn(e4, z2), z2), 0.2f)));
+        });
     } else {
-        A1 = atan_ratio(fmaf(k.e, u, k.el * u), du);
-        A2 = atanh_ratio(fmaf(k.e, v, k.el * v), dv);
+        A1 = atan_ratio(vfma(vsplat<V>(k.e), u, vmul(vsplat<V>(k.el), u)), du);
+        A2 = atanh_ratio(vfma(vsplat<V>(k.e), v, vmul(vsplat<V>(k.el), v)), dv);
     }
-    const float au = fmaf(k.pref, A1, k.prefl * A1);
-    const float av = fmaf(k.pref, A2, k.prefl * A2);
-    ax += fmaf(au, k.cs, fmaf(-av, k.sn, fmaf(au, k.csl, -av * k.snl)));
-    ay += fmaf(au, k.sn, fmaf(av, k.cs, fmaf(au, k.snl, av * k.csl)));
+    const V au = vfma(vsplat<V>(k.pref), A1, vmul(vsplat<V>(k.prefl), A1));
+    const V av = vfma(vsplat<V>(k.pref), A2, vmul(vsplat<V>(k.prefl), A2));
+    ax = vadd(ax, vfma(au, vsplat<V>(k.cs),
+                       vfma(av, vsplat<V>(-k.sn), vfma(au, vsplat<V>(k.csl), vmul(av, vsplat<V>(-k.snl))))));
+    ay = vadd(ay, vfma(au, vsplat<V>(k.sn),
+                       vfma(av, vsplat<V>(k.cs), vfma(au, vsplat<V>(k.snl), vmul(av, vsplat<V>(k.csl))))));
 }
 
-// light_f32 for a ray of the row whose terms are R
-__device__ __forceinline__ float light_f32_row(const LightF &k, const RowTerms &R, float x)
+// A light profile at frame coordinates (u, v) (major axis along u), one ray
+// or a pair; with rho2 != nullptr also (R / r)^2 of each ray.
+template <class V>
+__device__ __forceinline__ V light_uv_v(const LightF &k, V u, V v, V *rho2_out)
 {
-    const float dx = x - k.x0;
-    const float u = fmaf(dx, k.cs, fmaf(dx, k.csl, R.du));
-    const float v = fmaf(-dx, k.sn, fmaf(-dx, k.snl, R.dv));
-    const float uu = u * u, vv = v * v;
-    const float rho2 = fmaf(k.qr, uu, fmaf(k.iqr, vv, fmaf(k.qrl, uu, k.iqrl * vv)));
-    const float f = (k.kind == (float)kKindGauss) ? rho2 : ex2f(k.p2 * lg2f(rho2));
-    const float t = fmaf(k.B, f, k.Bl * f);
-    const float g = ex2f(-t);
-    return fmaf(k.A, g, k.Al * g);
+    const V uu = vmul(u, u), vv = vmul(v, v);
+    const V rho2 = vfma(vsplat<V>(k.qr), uu,
+                        vfma(vsplat<V>(k.iqr), vv, vfma(vsplat<V>(k.qrl), uu, vmul(vsplat<V>(k.iqrl), vv))));
+    if (rho2_out) *rho2_out = rho2;
+    V f = rho2;
+    if (k.kind != (float)kKindGauss)
+        f = vmap(vmul(vsplat<V>(k.p2), vmap(rho2, [](float a) { return lg2f(a); })),
+                 [](float a) { return ex2f(a); });
+    const V t = vfma(vsplat<V>(k.B), f, vmul(vsplat<V>(k.Bl), f));
+    const V g = vmap(t, [](float a) { return ex2f(-a); });
+    return vfma(vsplat<V>(k.A), g, vmul(vsplat<V>(k.Al), g));
+}
+
+// light_f32 for the rays of a node row whose terms are R
+template <class V>
+__device__ __forceinline__ V light_row_v(const LightF &k, const RowTerms &R, V x)
+{
+    const V dx = vsub(x, vsplat<V>(k.x0));
+    const V u = vfma(dx, vsplat<V>(k.cs), vfma(dx, vsplat<V>(k.csl), vsplat<V>(R.du)));
+    const V v = vfma(dx, vsplat<V>(-k.sn), vfma(dx, vsplat<V>(-k.snl), vsplat<V>(R.dv)));
+    return light_uv_v(k, u, v, (V *)nullptr);
+}
+
+// light_f32 (and (R / r)^2 with rho2 != nullptr) at source-plane positions
+// (x, y), one ray or a pair
+template <class V>
+__device__ __forceinline__ V light_at_v(const LightF &k, V x, V y, V *rho2)
+{
+    const V dx = vsub(x, vsplat<V>(k.x0)), dy = vsub(y, vsplat<V>(k.y0));
+    const V u = vfma(dx, vsplat<V>(k.cs),
+                     vfma(dy, vsplat<V>(k.sn), vfma(dx, vsplat<V>(k.csl), vmul(dy, vsplat<V>(k.snl)))));
+    const V v = vfma(dy, vsplat<V>(k.cs),
+                     vfma(dx, vsplat<V>(-k.sn), vfma(dy, vsplat<V>(k.csl), vmul(dx, vsplat<V>(-k.snl)))));
+    return light_uv_v(k, u, v, rho2);
 }
 
 // FP64 SIE of one ray in a MIXED evaluation.  Out of line, so that none of
@@ -964,82 +1003,88 @@ __device__ __forceinline__ float pixel_rays(const KC &kc, const SysDev &S, int n
     for (int b = 0; b < nn; ++b) {
         const float y = yc + kc.u(b);
         for (int a0 = 0; a0 < nn; a0 += G) {
-            float xk[G], ax[G], ay[G], I[G];
+            // the G rays of the chunk, traced in pairs (packed FP32) and, for
+            // odd G, one more alone; every value is the same bits either way
+            Rays<G> xk, ax, ay, I;
 #pragma unroll
             for (int k = 0; k < G; ++k) {
                 const int a = EXACT ? k : min(a0 + k, nn - 1);
-                xk[k] = xc + kc.u(a);
-                ax[k] = 0.f;
-                ay[k] = 0.f;
-                I[k] = 0.f;
+                xk.set(k, xc + kc.u(a));
             }
+            ax.fill(0.f);
+            ay.fill(0.f);
+            I.fill(0.f);
             for (int c = 0; c < ncomp; ++c) {
                 const int pl = kc.plane(c);
                 const float *cc = kc.cf(c);
                 if (pl == LENSED_PLANE_FOREGROUND) {
                     const LightF L = load_light(cc);
                     if (L.kind == (float)kKindFlat) {
-#pragma unroll
-                        for (int k = 0; k < G; ++k) I[k] += L.A;
+                        for_rays<G>([&](auto &i) {
+                            using V = std::remove_reference_t<decltype(i)>;
+                            i = vadd(i, vsplat<V>(L.A));
+                        }, I);
                     } else {
                         const RowTerms R = row_terms(y, L.y0, L.cs, L.sn, L.csl, L.snl);
-#pragma unroll
-                        for (int k = 0; k < G; ++k) I[k] += light_f32_row(L, R, xk[k]);
+                        for_rays<G>([&](auto &x, auto &i) { i = vadd(i, light_row_v(L, R, x)); },
+                                    xk, I);
                     }
                 } else if (pl == LENSED_PLANE_LENS) {
                     const int t = kc.type(c);
                     if (t == LENSED_SIE) {
                         const SieF K = load_sie(cc);
                         const RowTerms R = row_terms(y, K.y0, K.cs, K.sn, K.csl, K.snl);
-#pragma unroll
-                        for (int k = 0; k < G; ++k) sie_f32_row(K, R, xk[k], ax[k], ay[k]);
+                        for_rays<G>([&](auto &x, auto &dx, auto &dy) { sie_row_v(K, R, x, dx, dy); },
+                                    xk, ax, ay);
                     } else if (t == LENSED_SHEAR) {
                         const float x0 = cc[0], y0 = cc[1], g1 = cc[2], g2 = cc[3];
-#pragma unroll
-                        for (int k = 0; k < G; ++k) {
-                            const float dx = xk[k] - x0, dy = y - y0;
-                            ax[k] += fmaf(g1, dx, g2 * dy);
-                            ay[k] += fmaf(g2, dx, -g1 * dy);
-                        }
+                        const float dy = y - y0, g2dy = g2 * dy, g1dy = -g1 * dy;
+                        for_rays<G>([&](auto &x, auto &dx_, auto &dy_) {
+                            using V = std::remove_reference_t<decltype(x)>;
+                            const V dx = vsub(x, vsplat<V>(x0));
+                            dx_ = vadd(dx_, vfma(vsplat<V>(g1), dx, vsplat<V>(g2dy)));
+                            dy_ = vadd(dy_, vfma(vsplat<V>(g2), dx, vsplat<V>(g1dy)));
+                        }, xk, ax, ay);
                     } else {  // point mass
                         const float x0 = cc[0], y0 = cc[1], te2 = cc[2];
-#pragma unroll
-                        for (int k = 0; k < G; ++k) {
-                            const float dx = xk[k] - x0, dy = y - y0;
-                            const float r2 = fmaf(dx, dx, dy * dy);
-                            const float f = r2 > 0.f ? __fdividef(te2, r2) : 0.f;
-                            ax[k] = fmaf(f, dx, ax[k]);
-                            ay[k] = fmaf(f, dy, ay[k]);
-                        }
+                        const float dy = y - y0, dy2 = dy * dy;
+                        for_rays<G>([&](auto &x, auto &dx_, auto &dy_) {
+                            using V = std::remove_reference_t<decltype(x)>;
+                            const V dx = vsub(x, vsplat<V>(x0));
+                            const V r2 = vfma(dx, dx, vsplat<V>(dy2));
+                            const V f = vmap(r2, [=](float r) { return r > 0.f ? __fdividef(te2, r) : 0.f; });
+                            dx_ = vfma(f, dx, dx_);
+                            dy_ = vfma(f, vsplat<V>(dy), dy_);
+                        }, xk, ax, ay);
                     }
                 }
             }
             // rmin: (R/r)^2 of the ray at the nearest Sersic-type source,
             // capped at the re-trace threshold (a float minimum per source,
             // the comparison once per ray)
-            float Ifg[G], rmin[G];
-#pragma unroll
-            for (int k = 0; k < G; ++k) {
-                Ifg[k] = I[k];
-                rmin[k] = kCuspRho2;
-            }
+            Rays<G> Ifg = I, rmin;
+            rmin.fill(kCuspRho2);
             for (int c = 0; c < ncomp; ++c) {
                 if (kc.plane(c) != LENSED_PLANE_SOURCE) continue;
                 const LightF L = load_light(kc.cf(c));
                 if (L.kind == (float)kKindFlat) {
-#pragma unroll
-                    for (int k = 0; k < G; ++k) I[k] += L.A;
+                    for_rays<G>([&](auto &i) {
+                        using V = std::remove_reference_t<decltype(i)>;
+                        i = vadd(i, vsplat<V>(L.A));
+                    }, I);
                 } else if (NEAR != kNearIgnore && L.kind == (float)kKindPower) {
-#pragma unroll
-                    for (int k = 0; k < G; ++k) {
-                        float r2;
-                        I[k] += light_f32_rho(L, xk[k] - ax[k], y - ay[k], r2);
-                        if (NEAR == kNearFlag) pmin = fminf(pmin, r2);
-                        else rmin[k] = fminf(rmin[k], r2);
-                    }
+                    for_rays<G>([&](auto &x, auto &dx, auto &dy, auto &i, auto &rm) {
+                        using V = std::remove_reference_t<decltype(x)>;
+                        V r2;
+                        i = vadd(i, light_at_v(L, vsub(x, dx), vsub(vsplat<V>(y), dy), &r2));
+                        if (NEAR == kNearFlag) pmin = fminf(pmin, vminlane(r2));
+                        else rm = vmap(rm, r2, [](float p, float q) { return fminf(p, q); });
+                    }, xk, ax, ay, I, rmin);
                 } else {
-#pragma unroll
-                    for (int k = 0; k < G; ++k) I[k] += light_f32(L, xk[k] - ax[k], y - ay[k]);
+                    for_rays<G>([&](auto &x, auto &dx, auto &dy, auto &i) {
+                        using V = std::remove_reference_t<decltype(x)>;
+                        i = vadd(i, light_at_v(L, vsub(x, dx), vsub(vsplat<V>(y), dy), (V *)nullptr));
+                    }, xk, ax, ay, I);
                 }
             }
             if (NEAR == kNearDefer) {
@@ -1048,21 +1093,21 @@ __device__ __forceinline__ float pixel_rays(const KC &kc, const SysDev &S, int n
                 unsigned row = 0u;
 #pragma unroll
                 for (int k = 0; k < G; ++k) {
-                    const bool nk = rmin[k] < kCuspRho2;
+                    const bool nk = rmin.get(k) < kCuspRho2;
                     row |= nk ? 1u << k : 0u;
-                    I[k] = nk ? Ifg[k] : I[k];
+                    I.set(k, nk ? Ifg.get(k) : I.get(k));
                 }
                 mask |= (unsigned long long)row << (b * nn);
             } else if (NEAR == kNearInPlace) {
 #pragma unroll
                 for (int k = 0; k < G; ++k) {
-                    if (!(rmin[k] < kCuspRho2) || !(EXACT || a0 + k < nn)) continue;
-                    I[k] = Ifg[k] + kc.ff(ncomp, jc, ic, S.h, S.h_lo, a0 + k, b);
+                    if (!(rmin.get(k) < kCuspRho2) || !(EXACT || a0 + k < nn)) continue;
+                    I.set(k, Ifg.get(k) + kc.ff(ncomp, jc, ic, S.h, S.h_lo, a0 + k, b));
                 }
             }
 #pragma unroll
             for (int k = 0; k < G; ++k)
-                if (EXACT || a0 + k < nn) acc = fmaf(kc.w(b * nn + a0 + k), I[k], acc);
+                if (EXACT || a0 + k < nn) acc = fmaf(kc.w(b * nn + a0 + k), I.get(k), acc);
         }
     }
     return acc;

@@ -28,34 +28,54 @@ __device__ __forceinline__ float trig_lg2(float x)
 constexpr float kHalfPiHi = 1.57079637e+00f, kHalfPiLo = -4.37113901e-08f;
 constexpr float kHalfLn2Hi = 3.46573591e-01f, kHalfLn2Lo = -9.52327162e-10f;
 
-// atan(n / d) for d >= 0 (0 when n = d = 0).  t = min(|n|, d) / max(|n|, d)
-// lies in [0, 1]; atan(t) = t + t^3 Q(t^2), and pi/2 - atan(t) when |n| > d
-// (the subtraction from the leading float of pi/2 is exact there, since
-// atan(t) <= pi/4).  Odd in n.
-__device__ __forceinline__ float atan_ratio(float n, float d)
+// atan(n / d) for d >= 0 (0 when n = d = 0), for one ray (V = float) or a
+// pair (V = float2).  t = min(|n|, d) / max(|n|, d) lies in [0, 1];
+// atan(t) = t + t^3 Q(t^2), and pi/2 - atan(t) when |n| > d (the subtraction
+// from the leading float of pi/2 is exact there, since atan(t) <= pi/4).
+// Odd in n.
+template <class V>
+__device__ __forceinline__ V atan_ratio(V n, V d)
 {
-    const float an = fabsf(n);
-    const float hi = fmaxf(an, d), lo = fminf(an, d);
-    const float t = hi > 0.f ? lo * trig_rcp(hi) : 0.f;
-    const float u = t * t;
-    float r = fmaf(t * u, minimax_atan_q(u), t);
-    if (an > d) r = (kHalfPiHi - r) + kHalfPiLo;
-    return copysignf(r, n);
+    const V lo = vmap(n, d, [](float a, float b) { return fminf(fabsf(a), b); });
+    const V rh = vmap(n, d, [](float a, float b) {
+        const float hi = fmaxf(fabsf(a), b);
+        return hi > 0.f ? trig_rcp(hi) : 0.f;
+    });
+    const V t = vmul(lo, rh);
+    const V u = vmul(t, t);
+    const V r = vfma(vmul(t, u), minimax_atan_q(u), t);
+    const V rc = vadd(vsub(vsplat<V>(kHalfPiHi), r), vsplat<V>(kHalfPiLo));
+    return vmap(n, d, r, rc, [](float a, float b, float r0, float r1) {
+        return copysignf(fabsf(a) > b ? r1 : r0, a);
+    });
 }
 
-// atanh(n / d) for |n| < d (0 when d = 0).  z = n / d; for |z| <= 1/2,
-// atanh(z) = z + z^3 Q(z^2); beyond, (1/2) ln((d + n) / (d - n)), whose
-// value (> 0.549 in magnitude) keeps the logarithm's absolute error small
-// against it.  Odd in n.
-__device__ __forceinline__ float atanh_ratio(float n, float d)
+// atanh(n / d) for |n| < d (0 when d = 0), for one ray or a pair.  z = n / d;
+// for |z| <= 1/2, atanh(z) = z + z^3 Q(z^2); beyond, (1/2) ln((d + n) / (d - n)),
+// whose value (> 0.549 in magnitude) keeps the logarithm's absolute error
+// small against it.  Each lane takes its own form; a pair computes a form
+// only if one of its lanes needs it.  Odd in n.
+__device__ __forceinline__ bool all_le(float u, float c) { return u <= c; }
+__device__ __forceinline__ bool all_le(float2 u, float c) { return u.x <= c && u.y <= c; }
+__device__ __forceinline__ bool all_gt(float u, float c) { return u > c; }
+__device__ __forceinline__ bool all_gt(float2 u, float c) { return u.x > c && u.y > c; }
+template <class V>
+__device__ __forceinline__ V atanh_ratio(V n, V d)
 {
-    const float z = d > 0.f ? n * trig_rcp(d) : 0.f;
-    const float u = z * z;
-    if (u <= 0.25f) {
-        return fmaf(z * u, minimax_atanh_q(u), z);
+    const V rd = vmap(d, [](float b) { return b > 0.f ? trig_rcp(b) : 0.f; });
+    const V z = vmul(n, rd);
+    const V u = vmul(z, z);
+    const bool near_all = all_le(u, 0.25f), far_all = !near_all && all_gt(u, 0.25f);
+    V P = z, Lg = z;
+    if (!far_all) P = vfma(vmul(z, u), minimax_atanh_q(u), z);
+    if (!near_all) {
+        const V q = vmul(vadd(d, n), vmap(vsub(d, n), [](float b) { return trig_rcp(b); }));
+        const V L = vmap(q, [](float a) { return trig_lg2(a); });
+        Lg = vfma(vsplat<V>(kHalfLn2Hi), L, vmul(vsplat<V>(kHalfLn2Lo), L));
     }
-    const float L = trig_lg2((d + n) * trig_rcp(d - n));
-    return fmaf(kHalfLn2Hi, L, kHalfLn2Lo * L);
+    if (near_all) return P;
+    if (far_all) return Lg;
+    return vmap(u, P, Lg, u, [](float uu, float p, float l, float) { return uu <= 0.25f ? p : l; });
 }
 
 }  // namespace lensed
