@@ -305,10 +305,12 @@ int lensed_loglike_batch_noalloc(lensed_model *m, const double *params, int P,
  * for LENSED_PREC_MIXED_FF also whether the float-float re-traces run inside
  * the trace blocks or in a second kernel) on a batch of P points drawn
  * inside the given DEVICE parameter array (same layout as
- * lensed_loglike_batch) and keep the fastest for later calls.  The trace
- * block size, the launch form and the place of the re-traces never change a
- * result; the PSF mode changes the FP32 summation order of Eq. 15
- * (differences at the float rounding level).  Synchronous. */
+ * lensed_loglike_batch) and keep the fastest for later calls; then, with
+ * that configuration, time whole scratch chunks against chunks sized to half
+ * and a quarter of L2 (lensed_set_chunk_points) and keep the faster.  The
+ * trace block size, the launch form, the place of the re-traces and the
+ * chunk size never change a result; the PSF mode changes the FP32 summation
+ * order of Eq. 15 (differences at the float rounding level).  Synchronous. */
 int lensed_autotune(lensed_model *m, const double *params, int P, void *stream);
 
 /* Index of the configuration in use (-1: default) and its description (with
