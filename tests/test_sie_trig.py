@@ -67,3 +67,10 @@ def test_half_pi_and_half_ln2_pairs():
     assert abs(hl - np.log(2.0) / 2) <= np.spacing(np.float32(abs(const("kHalfLn2Lo"))))
     assert const("kHalfPiHi") == np.float32(np.pi / 2)
     assert const("kHalfLn2Hi") == np.float32(np.log(2.0) / 2)
+
+
+def test_header_is_its_own_rendering():
+    # the committed header is exactly what the generator writes for the
+    # coefficients it holds (templated over one ray or a pair of rays)
+    path = os.path.join(ROOT, "paper_1505_07674_gb300", "csrc", "lensed_minimax.cuh")
+    assert open(path).read() == G.render(G.parse())
