@@ -1730,6 +1730,7 @@ extern "C" int lensed_autotune(lensed_model *m, const double *params, int P, voi
                                (int)std::max<size_t>(1, (size_t)std::max(l2_bytes, 0) / 4 / per_point)};
         for (int li = 0; li < 2 && !rc && l2_bytes > 0; ++li) {
             if (limits[li] >= std::min(m->chunk_P, P)) continue;  // one chunk already
+            if (li > 0 && limits[li] == limits[li - 1]) continue;  // timed already
             m->chunk_limit = limits[li];
             if ((rc = time_batch(&t))) break;
             if (t < best) {
