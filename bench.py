@@ -97,7 +97,11 @@ def parse():
                     help="c5: which runs (plain is always run; online, audit, global)")
     ap.add_argument("--oracle-points", type=int, default=384,
                     help="posterior points the CPU oracle re-evaluates (c4)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.chunk_points is not None and args.config is None:
+        ap.error("--chunk-points pins a chunk size for a pinned --config; without --config "
+                 "the autotuner chooses both")
+    return args
 
 
 def dist_env():
