@@ -8,14 +8,21 @@
 //               magnitude, PA cosines, SIE prefactors) in FP64 with FP32
 //               copies; per (system, point): validity, and the image-plane
 //               priors (a source moved to theta - alpha(theta)).
-//   k_trace_rows
+//   k_trace_rows, k_trace_rows_pq
 //               a2-a5: one thread per needed pixel; for every ray of the
 //               quadrature rule: ray position (Eq. 14), deflection (Eq. 1),
 //               brightness at image and traced position (Eq. 2), weighted
 //               sum into the pixel luminosity (Eq. 3), in registers, starting
-//               from the once-per-model integral of the fixed lights.
-//               MIXED_FF re-traces the rays near a source centre in
-//               float-float through a block-wide queue.
+//               from the once-per-model integral of the fixed lights.  The
+//               rays of a node row are traced in pairs with packed FP32
+//               instructions (lensed_vec2.cuh).  _pq: the same work as a
+//               persistent grid taking (trace block, point) items from a
+//               counter.  MIXED_FF re-traces the rays near a source centre
+//               in float-float, inside the block (a block-wide queue) or in
+//               a second pass:
+//   k_refine_ff, k_retrace_ff, k_apply_ff
+//               the flagged pixels recomputed with their near rays queued,
+//               the queued rays re-traced, and added in ray order.
 //   k_trace_fix64, k_trace_f64
 //               MIXED: the pixels the FP64 SIE rule reaches; FP64 mode.
 //   k_psf, k_psf_sep
