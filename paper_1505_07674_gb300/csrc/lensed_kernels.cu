@@ -994,10 +994,9 @@ struct GlobalConsts {
 
 // a2-a5 for one pixel (centre (jc, ic) in pixels from the image centre): for
 // every row of the rule's node grid, G rays traced together component by
-// component (each component's constants read once per G rays; the G
-// independent rays give the scheduler instruction-level parallelism), each
-// ray's brightness added to acc with its weight in ray order.  EXACT: the
-// rule has exactly G nodes per row.
+// component (each component's constants read once per G rays), two at a
+// time in packed FP32 instructions, each ray's brightness added to acc with
+// its weight in ray order.  EXACT: the rule has exactly G nodes per row.
 template <int MODE, int G, bool EXACT, int NEAR, class KC>
 __device__ __forceinline__ float pixel_rays(const KC &kc, const SysDev &S, int ncomp, int nn,
                                             float jc, float ic, float acc,
