@@ -861,7 +861,7 @@ def main():
         "clocks": clocks,
         "loglike_finite_frac": float(np.isfinite(ll).mean()),
     }
-    if not args.no_cpu_baseline and n_sys == 1:
+    if not args.no_cpu_baseline and n_sys == 1 and world == 1:  # rank 0 at N = 1 only
         spec = specs[0]
         cb, obs_o, pts_o, ref = cpu_baseline(spec)
         mo = LZ.Model(spec, obs_o, precision=args.precision)
